@@ -1,0 +1,153 @@
+/*
+ * tsvd.h -- C ABI of the GB300 (sm_103a) mixed precision Gram-matrix thin SVD.
+ *
+ * Method: Algorithm 1 of Carson, Ma, Shao, "Mixed precision thin SVD
+ * algorithms based on the Gram matrix" (arXiv 2603.11953).  For a full-rank
+ * tall-and-skinny A (m >= n), with working precision u and higher precision
+ * u_h:
+ *   1. M_h = A^T A formed in the higher precision          (Alg. 1 lines 1-2)
+ *   2. M_h = V_h Sigma_h^2 V_h^T by the two-sided Jacobi   (Alg. 1 line 3, Sec. 2.1)
+ *   3. Sigma, V rounded to working precision               (Alg. 1 lines 4-5)
+ *   4. U = A (V Sigma^{-1}) in working precision           (Alg. 1 line 6)
+ *
+ * Conventions shared by every entry point:
+ *   - Matrices are column-major.  A has m rows, n columns, leading dimension
+ *     lda >= m (elements).  All A/G/sigma/V/U pointers are DEVICE pointers
+ *     owned by the caller; the library never frees them.
+ *   - Work is enqueued on the handle's stream and is asynchronous.  Argument
+ *     errors are detected on the host and returned immediately (nothing is
+ *     enqueued).  Numeric outcomes (non-finite input, rank deficiency, Jacobi
+ *     non-convergence) are only known on the device: they are written to the
+ *     optional tsvd_info (device or pinned host memory) and can be fetched
+ *     with tsvd_sync_status().
+ *   - sigma is sorted descending; each column of V is signed so that its
+ *     largest-magnitude entry is positive (lowest row index wins ties); the
+ *     columns of U follow V.
+ *   - A handle is not thread-safe: use one handle per host thread / stream.
+ *   - There is no CPU fallback: every step runs in the library's CUDA kernels.
+ *   - The handle grows device workspace on demand (cudaMalloc); the first call
+ *     at a given size allocates, later calls of the same or smaller size do
+ *     not.
+ */
+#ifndef TSVD_H
+#define TSVD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tsvd_ctx* tsvd_handle;
+
+/* Precision tags.  working in {TSVD_FP32, TSVD_FP64}; higher in {TSVD_FP64,
+ * TSVD_DD}.  TSVD_DD is a double-double (hi, lo) pair (u_h ~ 2^-104). */
+typedef enum { TSVD_FP32 = 0, TSVD_FP64 = 1, TSVD_DD = 2 } tsvd_prec;
+
+typedef enum {
+    TSVD_OK = 0,
+    TSVD_ERR_ARG = 1,            /* bad size, null pointer, bad tag */
+    TSVD_ERR_ALIGN = 2,          /* alignment the chosen path cannot handle */
+    TSVD_ERR_NONFINITE = 3,      /* A contains Inf or NaN */
+    TSVD_ERR_NOT_FULL_RANK = 4,  /* some eigenvalue of M_h is <= 0 */
+    TSVD_ERR_NO_CONVERGENCE = 5, /* Jacobi hit max_sweeps */
+    TSVD_ERR_TIMEOUT = 6,        /* a bounded device wait gave up */
+    TSVD_ERR_UNSUPPORTED = 7,    /* size / precision combination not built */
+    TSVD_ERR_CUDA = 8,           /* a CUDA runtime call failed */
+    TSVD_ERR_ALLOC = 9           /* workspace allocation failed */
+} tsvd_status;
+
+/* Options; a zero field selects the default. */
+typedef struct {
+    int slices;            /* Ozaki digit count k (default 7: 55 bits per entry) */
+    int chunk_rows;        /* rows per exact INT chunk (default 128; must be 128) */
+    int split_k;           /* CTAs over m for the Gram (default: from m and the SM count) */
+    double jacobi_tol;     /* skip test |m_pq| <= tol*sqrt(m_pp m_qq) (default n * 2^-53) */
+    int max_sweeps;        /* Jacobi sweep limit (default 40) */
+    int eig_variant;       /* 0 = two-sided Jacobi (only variant built) */
+    int autotune;          /* reserved (0) */
+    long long timeout_cycles; /* reserved: limit for device spin-waits (0 = default) */
+    int gram_variant;      /* 0 = Ozaki-BF16 tensor-core Gram, 1 = plain FP64 Gram */
+    int timing;            /* 1 = record per-stage CUDA events (tsvd_last_stage_ms) */
+} tsvd_opts;
+
+/* Per-call numeric report (written asynchronously by the device). */
+typedef struct {
+    int status;       /* tsvd_status of the numeric part */
+    int sweeps;       /* Jacobi sweeps performed */
+    double off_norm;  /* max_{p<q} |m_pq| / sqrt(m_pp m_qq) at exit */
+    double kappa_B;   /* reserved (0): kappa(B) is reported by the tests */
+} tsvd_info;
+
+/* Create a handle bound to `device` and `stream` (a cudaStream_t; NULL = the
+ * legacy default stream).  opts may be NULL.  Returns TSVD_ERR_ARG for a null
+ * h or a bad option, TSVD_ERR_CUDA if the device cannot be selected. */
+tsvd_status tsvd_create(tsvd_handle* h, int device, void* stream, const tsvd_opts* opts);
+
+/* Release the handle and its workspace (synchronises its stream). */
+tsvd_status tsvd_destroy(tsvd_handle h);
+
+/* Human-readable name of a status code (static storage; never NULL). */
+const char* tsvd_status_string(tsvd_status s);
+
+/* Alg. 1 lines 1-2 (eq. (ATA)): G = A^T A in the higher precision.
+ *   A: device, m x n, lda >= m, type per `working` (FP32 or FP64).
+ *   G: device FP64, n x n column-major, ldg >= n, both triangles written.
+ *      higher == TSVD_DD additionally writes the low parts of the
+ *      double-double result at G + ldg*n (another n x n block, same ldg).
+ * Errors: TSVD_ERR_ARG (m < 1, n < 1, lda < m, ldg < n, null pointer, bad
+ * tag), TSVD_ERR_UNSUPPORTED (n > 256 or a combination not built). */
+tsvd_status tsvd_gram(tsvd_handle h, const void* A, int64_t m, int64_t n, int64_t lda,
+                      tsvd_prec working, tsvd_prec higher, double* G, int64_t ldg);
+
+/* Alg. 1 lines 3-5 on a given symmetric positive definite M_h (Sec. 2.1,
+ * two-sided Jacobi in FP64; column scaling D = sqrt(diag M) drives the
+ * stopping test of A = B D, Sec. 3):
+ *   M: device FP64 n x n column-major (ldm >= n), read only.
+ *   lambda: device FP64 [n] eigenvalues, descending.   V: device FP64 n x n
+ *   (ldv >= n), sign-normalised eigenvectors.  info: optional.
+ * Errors: TSVD_ERR_ARG, TSVD_ERR_UNSUPPORTED (n > 256). */
+tsvd_status tsvd_eig(tsvd_handle h, const double* M, int64_t n, int64_t ldm, double* lambda,
+                     double* V, int64_t ldv, tsvd_info* info);
+
+/* Algorithm 1 end to end for one matrix.
+ *   A: device, m x n (m >= n), lda >= m, type per `working`.
+ *   sigma: device [n], working type, descending.
+ *   V: device n x n working type, ldv >= n.
+ *   U: device m x n working type, ldu >= m, or NULL to skip line 6.
+ *   info: NULL, or device / pinned-host tsvd_info written at the end.
+ * higher must be TSVD_FP64 for FP32 working and TSVD_DD for FP64 working.
+ * Errors: TSVD_ERR_ARG (m < n, n < 1, lda < m, ldv < n, ldu < m with U,
+ * null required pointer, bad tag), TSVD_ERR_UNSUPPORTED (n > 256). */
+tsvd_status tsvd_solve(tsvd_handle h, const void* A, int64_t m, int64_t n, int64_t lda,
+                       tsvd_prec working, tsvd_prec higher, void* sigma, void* V, int64_t ldv,
+                       void* U, int64_t ldu, tsvd_info* info);
+
+/* Many independent instances (ragged m and n, n <= 64) in one call.  All
+ * pointer arrays (A[count], sigma[count], V[count], U[count]) and size arrays
+ * (m, n, lda, ldv, ldu) are HOST arrays of device pointers / sizes; U (the
+ * array) may be NULL, or any U[i] may be NULL, to skip U for that instance.
+ * info: NULL or `count` entries (device or pinned host).
+ * Errors: TSVD_ERR_ARG for any bad instance (nothing is enqueued),
+ * TSVD_ERR_UNSUPPORTED for n > 64. */
+tsvd_status tsvd_batch_solve(tsvd_handle h, int32_t count, const void* const* A, const int64_t* m,
+                             const int64_t* n, const int64_t* lda, tsvd_prec working,
+                             tsvd_prec higher, void* const* sigma, void* const* V,
+                             const int64_t* ldv, void* const* U, const int64_t* ldu,
+                             tsvd_info* info);
+
+/* Synchronise the handle's stream and return the numeric status of the last
+ * call (TSVD_OK, TSVD_ERR_NONFINITE, TSVD_ERR_NOT_FULL_RANK,
+ * TSVD_ERR_NO_CONVERGENCE) or TSVD_ERR_CUDA. */
+tsvd_status tsvd_sync_status(tsvd_handle h);
+
+/* Per-stage device times of the last tsvd_solve (requires opts.timing = 1):
+ * ms[0] Gram (split + MMA + combine), ms[1] eigensolver (scaling, Jacobi,
+ * sort, cast), ms[2] compute U, ms[3] total.  Synchronises the stream.
+ * These are the components of the paper's time breakdown (Sec. 4.1.2). */
+tsvd_status tsvd_last_stage_ms(tsvd_handle h, float ms[4]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TSVD_H */

@@ -1,0 +1,274 @@
+"""Pins of the CPU oracle against things other than itself (CPU only).
+
+Each test ties one oracle function to an independent fact: exact rational
+arithmetic (Python ``fractions``), closed forms, exact root isolation
+(sympy), LAPACK's SVD, Weyl's perturbation bound, and invariants of the Gram
+matrix.  A dropped term, wrong sign, wrong index or transposed operand in the
+oracle fails at least one of them.
+"""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- helpers
+def exact_gram(A):
+    """sum_r A[r,i] A[r,j] as Fractions (independent of the oracle)."""
+    m, n = A.shape
+    F = [[Fraction(float(A[r, c])) for c in range(n)] for r in range(m)]
+    return [[sum(F[r][i] * F[r][j] for r in range(m)) for j in range(n)] for i in range(n)]
+
+
+def round_frac(x: Fraction, p: int) -> float:
+    """Round a rational to p significant bits, ties to even (exact)."""
+    if x == 0:
+        return 0.0
+    sign = -1.0 if x < 0 else 1.0
+    x = abs(x)
+    e = x.numerator.bit_length() - x.denominator.bit_length() - p
+    two = Fraction(2)
+    while x / two ** e >= 2 ** p:
+        e += 1
+    while x / two ** e < 2 ** (p - 1):
+        e -= 1
+    q = x / two ** e
+    k = q.numerator // q.denominator
+    r = q - k
+    if r > Fraction(1, 2) or (r == Fraction(1, 2) and k % 2 == 1):
+        k += 1
+    return sign * math.ldexp(k, e)
+
+
+def wide_random(m, n, seed, dtype=np.float32, erange=30):
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((m, n)) * np.exp2(rng.integers(-erange, erange, size=(m, n)))
+    return np.asfortranarray(A.astype(dtype))
+
+
+# ---------------------------------------------------------------- Gram (Alg. 1 lines 1-2)
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_gram_equals_exact_rational_sum(dtype):
+    A = wide_random(40, 4, 11, dtype)
+    A[7] = -A[3]  # exact cancellation pairs
+    Gh, Gl, Ga = oracle.gram(A)
+    S = exact_gram(A)
+    for i in range(4):
+        for j in range(4):
+            hi = round_frac(S[i][j], 53)
+            lo = round_frac(S[i][j] - Fraction(hi), 53)
+            assert Gh[i, j] == hi and Gl[i, j] == lo, (i, j)
+            assert Ga[i, j] >= abs(Gh[i, j]) * (1 - 1e-15)
+
+
+def test_gram_golden_integer_fixture():
+    rows = open(os.path.join(GOLDEN, "gram_integer_3x2.txt")).read().split("\n")
+    rows = [r for r in rows if r and not r.startswith("#")]
+    ia, im = rows.index("A"), rows.index("M")
+    A = np.array([[float(x) for x in r.split()] for r in rows[ia + 1:im]], dtype=np.float32)
+    M = np.array([[float(x) for x in r.split()] for r in rows[im + 1:]])
+    Gh, Gl, _ = oracle.gram(A)
+    assert np.array_equal(Gh, M) and not Gl.any()
+    res = oracle.svd(A, higher=1)
+    lam = [(91 + math.sqrt(8185)) / 2, (91 - math.sqrt(8185)) / 2]
+    assert res["status"] == 0
+    np.testing.assert_allclose(res["sigma_h"], np.sqrt(lam), rtol=1e-14)
+
+
+def test_gram_invariants():
+    A = wide_random(64, 5, 3)
+    Gh, Gl, _ = oracle.gram(A)
+    perm = np.random.default_rng(0).permutation(64)
+    Gp, Glp, _ = oracle.gram(np.asfortranarray(A[perm]))
+    assert np.array_equal(Gh, Gp) and np.array_equal(Gl, Glp)
+    # power-of-two column scaling is exact: G_ij -> 2^(p_i + p_j) G_ij
+    p = np.array([3, -7, 0, 12, -1])
+    As = np.asfortranarray((A * np.exp2(p)).astype(np.float32))
+    Gs, Gls, _ = oracle.gram(As)
+    scale = np.exp2(p[:, None] + p[None, :])
+    assert np.array_equal(Gs, Gh * scale) and np.array_equal(Gls, Gl * scale)
+    # stacking [A; A] doubles the exact sum (and both parts of the DD)
+    G2, Gl2, _ = oracle.gram(np.asfortranarray(np.vstack([A, A])))
+    assert np.array_equal(G2, 2 * Gh) and np.array_equal(Gl2, 2 * Gl)
+    # flipping the sign of column 2 flips row/column 2 off the diagonal
+    Af = A.copy(order="F")
+    Af[:, 2] *= -1
+    Gf, _, _ = oracle.gram(Af)
+    sgn = np.ones(5)
+    sgn[2] = -1
+    assert np.array_equal(Gf, Gh * np.outer(sgn, sgn))
+    # transposed operands would break symmetry of a non-square product: G is symmetric
+    assert np.array_equal(Gh, Gh.T)
+
+
+def test_gram_orthogonal_columns_exact():
+    # Sylvester-Hadamard H_8 / sqrt(8)-free: H^T H = 8 I exactly
+    H = np.array([[1.0]])
+    for _ in range(3):
+        H = np.block([[H, H], [H, -H]])
+    A = np.asfortranarray((H[:, :5] * 0.125).astype(np.float32))
+    Gh, Gl, _ = oracle.gram(A)
+    assert np.array_equal(Gh, 0.125 * np.eye(5)) and not Gl.any()
+    res = oracle.svd(A, higher=1)
+    np.testing.assert_array_equal(res["sigma_h"], np.full(5, math.sqrt(0.125)))
+
+
+# ---------------------------------------------------------------- rounding to working (line 6)
+def test_rows_times_is_exact_dot_rounded_once():
+    A = wide_random(30, 6, 5, erange=8)
+    W = np.asfortranarray(np.random.default_rng(9).standard_normal((6, 6)).astype(np.float32).astype(np.float64))
+    rows = np.array([0, 3, 29, 17])
+    for p in (24, 53):
+        out = oracle.rows_times(A, W, rows, p)
+        for k, r in enumerate(rows):
+            for j in range(6):
+                s = sum(Fraction(float(A[r, c])) * Fraction(float(W[c, j])) for c in range(6))
+                assert out[k, j] == round_frac(s, p), (p, r, j)
+
+
+def test_explicit_u_orthonormal_columns():
+    # A = Q diag(s) with exactly orthogonal Q (Hadamard/8): U must be Q exactly (up to signs)
+    H = np.array([[1.0]])
+    for _ in range(4):
+        H = np.block([[H, H], [H, -H]])
+    Q = H[:, :4] * 0.25  # 16 x 4, Q^T Q = I exactly
+    s = np.array([8.0, 4.0, 2.0, 0.5])
+    A = np.asfortranarray(Q * s)
+    res = oracle.svd(A, higher=1)
+    np.testing.assert_array_equal(res["sigma_h"], s)
+    np.testing.assert_array_equal(np.abs(res["V_h"]), np.eye(4))
+    uh, ul = oracle.rows_explicit_u(A, res["V_h"], None, res["sigma_h"], None, np.arange(16))
+    np.testing.assert_array_equal(np.abs(uh), np.abs(Q))
+
+
+# ---------------------------------------------------------------- Jacobi (Alg. 1 line 3)
+def test_jacobi_n1_and_2x2_closed_form():
+    lam, V, sw, st = oracle.jacobi_fp64(np.array([[7.25]]))
+    assert st == 0 and lam[0] == 7.25 and V[0, 0] == 1.0
+    from decimal import Decimal, getcontext
+    getcontext().prec = 60
+    a, b, c = 3.0, 1.25, 0.75  # SPD: det = 2.25 - 1.5625 > 0
+    lam, V, sw, st = oracle.jacobi_fp64(np.array([[a, b], [b, c]]))
+    mid = (Decimal(a) + Decimal(c)) / 2
+    rad = (((Decimal(a) - Decimal(c)) / 2) ** 2 + Decimal(b) ** 2).sqrt()
+    exact = sorted([float(mid + rad), float(mid - rad)], reverse=True)
+    rho = b / math.sqrt(a * c)  # scaled matrix [[1, rho], [rho, 1]], kappa = (1+rho)/(1-rho)
+    kC = (1 + rho) / (1 - rho)
+    np.testing.assert_allclose(sorted(lam, reverse=True), exact, rtol=16 * kC * 2.0 ** -53)
+    # eigenvector of the larger eigenvalue, from (M - lam I) v = 0: v ~ (b, lam - a)
+    i = int(np.argmax(lam))
+    v = V[:, i] * np.sign(V[0, i])
+    ref = np.array([b, exact[0] - a])
+    np.testing.assert_allclose(v, ref / np.linalg.norm(ref), rtol=1e-15)
+
+
+@pytest.mark.parametrize("n,seed", [(2, 1), (3, 2), (4, 3), (4, 4)])
+def test_brute_force_exact_eigenvalues(n, seed):
+    sympy = pytest.importorskip("sympy")
+    A = wide_random(6, n, seed, erange=3)
+    S = exact_gram(A)
+    Ms = sympy.Matrix(n, n, lambda i, j: sympy.Rational(S[i][j].numerator, S[i][j].denominator))
+    lam = sympy.Symbol("lam")
+    roots = sympy.Poly(Ms.charpoly(lam).as_expr(), lam).real_roots()
+    exact_sigma = sorted([float(sympy.sqrt(r).evalf(40)) for r in roots], reverse=True)
+    res = oracle.svd(A, higher=1)
+    assert res["status"] == 0
+    C = np.array(Ms.evalf(30).tolist(), dtype=float)
+    d = np.sqrt(np.diag(C))
+    kC = np.linalg.cond(C / np.outer(d, d))
+    np.testing.assert_allclose(res["sigma_h"], exact_sigma, rtol=64 * 2.0 ** -53 * kC)
+    res2 = oracle.svd(A, higher=2)
+    exact_hi = sorted([sympy.sqrt(r).evalf(40) for r in roots], reverse=True)
+    for k in range(n):
+        err = abs(sympy.Float(res2["sigma_h"][k], 40) + sympy.Float(res2["sigma_h_lo"][k], 40) - exact_hi[k])
+        assert float(err / exact_hi[k]) < 1e-28 * kC, (k, float(err / exact_hi[k]))
+
+
+def test_graded_matrix_relative_accuracy():
+    """M = D C D with C well conditioned and D spanning 1e+-8: Jacobi with the
+    scaled stopping test keeps every eigenvalue to high RELATIVE accuracy
+    (the property Sec. 2.1 picks two-sided Jacobi for)."""
+    sympy = pytest.importorskip("sympy")
+    C = np.array([[1.0, 0.3, -0.2], [0.3, 1.0, 0.25], [-0.2, 0.25, 1.0]])
+    D = np.array([1e8, 1.0, 1e-8])
+    M = C * np.outer(D, D)
+    Ms = sympy.Matrix(3, 3, lambda i, j: sympy.Rational(Fraction(float(M[i, j]))))
+    lam = sympy.Symbol("lam")
+    roots = sorted(sympy.Poly(Ms.charpoly(lam).as_expr(), lam).real_roots(), key=lambda r: -float(r.evalf(30)))
+    exact = np.array([float(r.evalf(40)) for r in roots])
+    lam_o, V, sw, st = oracle.jacobi_fp64(M)
+    assert st == 0
+    got = np.sort(lam_o)[::-1]
+    np.testing.assert_allclose(got, exact, rtol=1e-14)  # smallest is ~1e-16 of the largest
+
+
+def test_jacobi_residual_orthogonality_and_vs_lapack():
+    rng = np.random.default_rng(7)
+    n = 24
+    X = rng.standard_normal((200, n))
+    M = X.T @ X
+    lam, V, sw, st = oracle.jacobi_fp64(M)
+    assert st == 0 and sw < 15
+    scale = np.abs(lam).max()
+    assert np.abs(M @ V - V * lam).max() <= 8 * n * 2.0 ** -53 * scale
+    assert np.abs(V.T @ V - np.eye(n)).max() <= 8 * n * 2.0 ** -53
+    ref = np.linalg.eigvalsh(M)[::-1]
+    np.testing.assert_allclose(np.sort(lam)[::-1], ref, rtol=1e-12)
+    # full pipeline vs LAPACK SVD on the same (well-conditioned) matrix
+    A = np.asfortranarray(X)
+    res = oracle.svd(A, higher=1)
+    np.testing.assert_allclose(res["sigma_h"], np.linalg.svd(A, compute_uv=False), rtol=1e-13)
+    # sort and sign rule
+    assert np.all(np.diff(res["sigma_h"]) <= 0)
+    for j in range(n):
+        col = res["V_h"][:, j]
+        k = int(np.argmax(np.abs(col)))
+        assert col[k] > 0
+
+
+def test_known_sigma_weyl_bound():
+    """D = I: A64 = Q diag(sigma) W^T has singular values sigma (to FP64
+    rounding); rounding to FP32 moves each by at most ||A32 - A64||_2 (Weyl)."""
+    import torch
+    from paper_2603_11953_gb300 import workloads
+    A, meta = workloads.small_case(2000, 12, kappa_sigma=1e3, logd=0.0, seed=5, dtype=torch.float64)
+    A64 = workloads.to_numpy_colmajor(A, 2000)
+    A32 = np.asfortranarray(A64.astype(np.float32))
+    res = oracle.svd(A32, higher=1)
+    sig = meta["sigma"].numpy()
+    weyl = np.linalg.norm(A32.astype(np.float64) - A64, 2)
+    assert res["status"] == 0
+    assert np.all(np.abs(res["sigma_h"] - sig) <= weyl + 1e-14)
+    res64 = oracle.svd(A64, higher=2)
+    np.testing.assert_allclose(res64["sigma_h"], sig, rtol=1e-13)
+
+
+def test_not_full_rank_and_nonfinite_statuses():
+    A = np.asfortranarray(np.ones((8, 2), dtype=np.float32))  # rank 1
+    res = oracle.svd(A, higher=1)
+    assert res["status"] == oracle.NOT_FULL_RANK
+    A[3, 1] = np.inf
+    with pytest.raises(ValueError):
+        oracle.gram(A)
+
+
+def test_dd_jacobi_reaches_double_double_accuracy():
+    """FP64-working path: Gram in DD and Jacobi in DD reproduce sigma of a
+    D = I matrix far below FP64 resolution (checked against DD-exact sympy)."""
+    sympy = pytest.importorskip("sympy")
+    A = wide_random(9, 3, 21, dtype=np.float64, erange=2)
+    S = exact_gram(A)
+    Ms = sympy.Matrix(3, 3, lambda i, j: sympy.Rational(S[i][j].numerator, S[i][j].denominator))
+    lam = sympy.Symbol("lam")
+    roots = sympy.Poly(Ms.charpoly(lam).as_expr(), lam).real_roots()
+    exact = sorted([sympy.sqrt(r).evalf(45) for r in roots], reverse=True)
+    res = oracle.svd(A, higher=2)
+    for k in range(3):
+        got = sympy.Float(res["sigma_h"][k], 45) + sympy.Float(res["sigma_h_lo"][k], 45)
+        assert float(abs(got - exact[k]) / exact[k]) < 1e-29
