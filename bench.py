@@ -1,0 +1,353 @@
+"""Benchmark of the mixed precision Gram-matrix thin SVD on GB300.
+
+One step = one full pass of Algorithm 1 (Gram on the tensor cores, combine,
+FP64 Jacobi, sort/cast, U) on one resident synthetic instance of the
+4,194,304 x 64 FP32 workload (the configuration the headline metric is
+quoted on).  Prints ONE JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload NAME] [--no-cpu-baseline] [--no-plain]
+
+With torchrun (N > 1) every rank runs its own replica (independent
+instances, no data-path collective): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import shutil
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "A GB/s per thin SVD, mixed vs all-FP64 on GB300, sigma rel err≤1e-5; %HBM peak"
+DEFAULT_WORKLOAD = "ozaki_4194304x64_fp32"
+KERNELS_PER_STEP = 6  # gram_ozaki, gram_combine, jacobi, finish, compute_u, finalize_info
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return dict(hbm=float(p["hbm_gbs"]), bf16=float(p["bf16_tflops"]),
+                    bf16_sus=float(p.get("bf16_tflops_sustained", p["bf16_tflops"])),
+                    sm_max_mhz=float(p.get("sm_max_mhz", 2070.0)), src="measured")
+    except Exception:
+        return dict(hbm=6800.0, bf16=1900.0, bf16_sus=1700.0, sm_max_mhz=2070.0, src="fallback")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.tmp = None
+
+    def __enter__(self):
+        if shutil.which("nvidia-smi") is None:
+            return self
+        self.tmp = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+        self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                                      "--format=csv,noheader,nounits", "-lms", "100"],
+                                     stdout=self.tmp, stderr=subprocess.DEVNULL)
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.tmp is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.tmp.flush()
+        rows = []
+        with open(self.tmp.name) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.tmp.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup(n_gpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl"
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world, device):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_baseline(A_cpu, m, n, rows, reps=1):
+    """The oracle as it stands (single thread) on the first `rows` rows."""
+    import numpy as np
+    import oracle
+    from paper_2603_11953_gb300 import workloads
+    An = workloads.to_numpy_colmajor(A_cpu, rows)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        r = oracle.svd(An, higher=1)
+        oracle.rows_times(An, r["W_w"], np.arange(rows), 24)
+    dt = (time.perf_counter() - t0) / reps
+    gbs = rows * n * An.itemsize / dt / 1e9
+    return gbs, dt
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle on a bounded sample of the workload."""
+    world, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
+    if rank != 0:
+        return 0
+    import torch
+    from paper_2603_11953_gb300 import workloads
+    spec = workloads.CONFIGS[args.workload]
+    rows = args.ref_rows
+    A, _ = workloads.make_config(spec, device="cpu", m=rows)
+    for _ in range(args.warmup):
+        cpu_baseline(A, rows, spec.n, min(rows, 2048))
+    times = []
+    for _ in range(args.steps):
+        _, dt = cpu_baseline(A, rows, spec.n, rows)
+        times.append(dt)
+    tot = sum(times)
+    gbs = args.steps * rows * spec.n * A.element_size() / tot / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "fp32",
+            "data": "synthetic",
+            "config": {"workload": spec.name, "m_sample": rows, "n": spec.n, "m_full": spec.m},
+            "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": f"first {rows} rows of {spec.name}: exact Gram + FP64 Jacobi + exact U rows"},
+            "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-rows", type=int, default=32768)
+    ap.add_argument("--ref-rows", type=int, default=16384)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_2603_11953_gb300 as T
+    from paper_2603_11953_gb300 import workloads
+
+    world, rank, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    spec = workloads.CONFIGS[args.workload]
+    m, n = spec.m, spec.n
+    A, meta = workloads.make_config(spec, device=dev, seed_offset=rank)
+    esize = A.element_size()
+    working = T.TSVD_FP32 if spec.dtype == torch.float32 else T.TSVD_FP64
+    higher = T.TSVD_FP64 if working == T.TSVD_FP32 else T.TSVD_DD
+    wdt = spec.dtype
+    stream = torch.cuda.current_stream(dev)
+    h, _ = T.tsvd_create(local, stream.cuda_stream, T.tsvd_opts(timing=1))
+    sigma = torch.zeros(n, dtype=wdt, device=dev)
+    V = torch.zeros(n, n, dtype=wdt, device=dev)
+    U = torch.zeros(n, m, dtype=wdt, device=dev)
+    info = torch.zeros(6, dtype=torch.int32, device=dev)
+
+    def step():
+        T.tsvd_solve(h, A, m, n, m, working, higher, sigma, V, n, U, m, info)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    status = int(info[0].item())
+    # per-stage device times of single steps (events on the library's stream)
+    stage = []
+    for _ in range(3):
+        step()
+        stage.append(T.tsvd_last_stage_ms(h))
+    stage_ms = [statistics.median(s[k] for s in stage) for k in range(4)]
+
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+    barrier(world)
+    ms_total = ev0.elapsed_time(ev1)
+    ms_total = max_over_ranks(ms_total, world, dev)
+    ms_step = ms_total / args.steps
+    bytes_A = m * n * esize
+    value = world * args.steps * bytes_A / (ms_total * 1e-3) / 1e9
+    clocks = clk.summary()
+
+    # end to end through the public API with host buffers (pinned), H2D + solve + D2H each step
+    e2e = None
+    if not args.no_e2e:
+        A_host = torch.empty((n, m), dtype=wdt, pin_memory=True)
+        A_host.copy_(A.T.reshape(n, m), non_blocking=False)
+        U_host = torch.empty((n, m), dtype=wdt, pin_memory=True)
+        s_host = torch.empty(n, dtype=wdt, pin_memory=True)
+        V_host = torch.empty((n, n), dtype=wdt, pin_memory=True)
+        A_dev = torch.empty((n, m), dtype=wdt, device=dev)
+        K = max(3, args.steps // 4)
+
+        def e2e_step():
+            A_dev.copy_(A_host, non_blocking=True)
+            T.tsvd_solve(h, A_dev, m, n, m, working, higher, sigma, V, n, U, m, info)
+            U_host.copy_(U, non_blocking=True)
+            s_host.copy_(sigma, non_blocking=True)
+            V_host.copy_(V, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize(dev)
+        barrier(world)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(K):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier(world)
+        ms_e2e = max_over_ranks(e0.elapsed_time(e1), world, dev) / K
+        e2e = {"value": world * bytes_A / (ms_e2e * 1e-3) / 1e9, "unit": "GB/s",
+               "h2d_bytes_per_step": bytes_A, "d2h_bytes_per_step": bytes_A + n * esize + n * n * esize,
+               "ms_per_step": ms_e2e}
+        del A_host, U_host, A_dev
+
+    # the all-FP64 plain form of the same method (FP64 DFMA Gram, same Jacobi / U)
+    plain = None
+    if not args.no_plain and n <= 64:
+        hp, _ = T.tsvd_create(local, stream.cuda_stream, T.tsvd_opts(timing=1, gram_variant=1))
+        T.tsvd_solve(hp, A, m, n, m, working, higher, sigma, V, n, U, m, info)
+        torch.cuda.synchronize(dev)
+        kp = 3
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        for _ in range(kp):
+            T.tsvd_solve(hp, A, m, n, m, working, higher, sigma, V, n, U, m, info)
+        p1.record(stream)
+        torch.cuda.synchronize(dev)
+        pst = T.tsvd_last_stage_ms(hp)
+        ms_plain = p0.elapsed_time(p1) / kp
+        plain = {"value": bytes_A / (ms_plain * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": ms_plain,
+                 "gram_ms": pst[0], "speedup_mixed_vs_plain": ms_plain / ms_step}
+        T.tsvd_destroy(hp)
+
+    pk = peaks()
+    # roofline of the dominant stage (events recorded by the library on its stream)
+    gram_ms, eig_ms, u_ms = stage_ms[0], stage_ms[1], stage_ms[2]
+    NP = 16 if n <= 16 else 32 if n <= 32 else 48 if n <= 48 else 64
+    gram_flops = 16 * 2.0 * m * NP * NP          # 16 exact digit-pair products on the tensor cores
+    gram_bytes = bytes_A
+    u_bytes = 2.0 * bytes_A
+    # FP64 work of one Jacobi pass is data dependent; count it from the sweeps reported
+    sweeps = int(info[1].item())
+    jac_flops = sweeps * (n - 1 + (n & 1)) * ((n + 1) // 2) * (12 * n + 30)
+    fp64_peak_1sm = 2 * 2 * pk["sm_max_mhz"] * 1e6 / 1e9  # GFLOP/s of one SM (2 DFMA/clk)
+    cands = {
+        "gram": (gram_ms, {"bound": "tensor", "achieved": gram_flops / (gram_ms * 1e-3) / 1e12,
+                           "peak": pk["bf16_sus"], "unit": "TFLOP/s",
+                           "hbm_gbs": gram_bytes / (gram_ms * 1e-3) / 1e9}),
+        "jacobi": (eig_ms, {"bound": "alu", "achieved": jac_flops / (eig_ms * 1e-3) / 1e9,
+                            "peak": fp64_peak_1sm, "unit": "GFLOP/s"}),
+        "compute_u": (u_ms, {"bound": "hbm", "achieved": u_bytes / (u_ms * 1e-3) / 1e9,
+                             "peak": pk["hbm"], "unit": "GB/s"}),
+    }
+    dom = max(cands, key=lambda k: cands[k][0])
+    rl = dict(cands[dom][1])
+    rl["kernel"] = dom
+    rl["frac"] = rl["achieved"] / rl["peak"]
+    rl["traffic"] = None
+    rl["peak_source"] = pk["src"]
+    stages = {"gram_ms": gram_ms, "eig_ms": eig_ms, "u_ms": u_ms, "total_ms": stage_ms[3],
+              "gram_hbm_frac": (gram_bytes / (gram_ms * 1e-3) / 1e9) / pk["hbm"],
+              "u_hbm_frac": (u_bytes / (u_ms * 1e-3) / 1e9) / pk["hbm"],
+              "gram_tensor_frac": (gram_flops / (gram_ms * 1e-3) / 1e12) / pk["bf16_sus"],
+              "jacobi_sweeps": sweeps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rows = min(args.cpu_rows, m)
+        A_cpu = A[:rows].cpu()
+        gbs, dt = cpu_baseline(A_cpu, rows, n, rows)
+        cpu = {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
+               "sample": f"first {rows} rows of {spec.name}: exact Gram + FP64 Jacobi + exact U rows ({dt:.1f} s)"}
+
+    line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "fp32", "data": "synthetic",
+            "config": {"workload": spec.name, "m": m, "n": n, "working": "fp32" if working == 0 else "fp64",
+                       "higher": "fp64" if higher == 1 else "dd", "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2 (A is %.2f GB > 129 MB)" % (bytes_A / 1e9),
+                       "status": T.tsvd_status_string(status)},
+            "roofline": rl, "stages": stages, "fp64_plain": plain, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": KERNELS_PER_STEP * args.steps, "clocks": clocks,
+            "hbm_frac_of_A_stream": (bytes_A / (ms_step * 1e-3) / 1e9) / pk["hbm"]}
+    T.tsvd_destroy(h)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -34,6 +34,12 @@
 
 #include <stdint.h>
 
+#if defined(__GNUC__)
+#define TSVD_API __attribute__((visibility("default")))
+#else
+#define TSVD_API
+#endif
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -82,13 +88,13 @@ typedef struct {
 /* Create a handle bound to `device` and `stream` (a cudaStream_t; NULL = the
  * legacy default stream).  opts may be NULL.  Returns TSVD_ERR_ARG for a null
  * h or a bad option, TSVD_ERR_CUDA if the device cannot be selected. */
-tsvd_status tsvd_create(tsvd_handle* h, int device, void* stream, const tsvd_opts* opts);
+TSVD_API tsvd_status tsvd_create(tsvd_handle* h, int device, void* stream, const tsvd_opts* opts);
 
 /* Release the handle and its workspace (synchronises its stream). */
-tsvd_status tsvd_destroy(tsvd_handle h);
+TSVD_API tsvd_status tsvd_destroy(tsvd_handle h);
 
 /* Human-readable name of a status code (static storage; never NULL). */
-const char* tsvd_status_string(tsvd_status s);
+TSVD_API const char* tsvd_status_string(tsvd_status s);
 
 /* Alg. 1 lines 1-2 (eq. (ATA)): G = A^T A in the higher precision.
  *   A: device, m x n, lda >= m, type per `working` (FP32 or FP64).
@@ -97,7 +103,7 @@ const char* tsvd_status_string(tsvd_status s);
  *      double-double result at G + ldg*n (another n x n block, same ldg).
  * Errors: TSVD_ERR_ARG (m < 1, n < 1, lda < m, ldg < n, null pointer, bad
  * tag), TSVD_ERR_UNSUPPORTED (n > 256 or a combination not built). */
-tsvd_status tsvd_gram(tsvd_handle h, const void* A, int64_t m, int64_t n, int64_t lda,
+TSVD_API tsvd_status tsvd_gram(tsvd_handle h, const void* A, int64_t m, int64_t n, int64_t lda,
                       tsvd_prec working, tsvd_prec higher, double* G, int64_t ldg);
 
 /* Alg. 1 lines 3-5 on a given symmetric positive definite M_h (Sec. 2.1,
@@ -107,7 +113,7 @@ tsvd_status tsvd_gram(tsvd_handle h, const void* A, int64_t m, int64_t n, int64_
  *   lambda: device FP64 [n] eigenvalues, descending.   V: device FP64 n x n
  *   (ldv >= n), sign-normalised eigenvectors.  info: optional.
  * Errors: TSVD_ERR_ARG, TSVD_ERR_UNSUPPORTED (n > 256). */
-tsvd_status tsvd_eig(tsvd_handle h, const double* M, int64_t n, int64_t ldm, double* lambda,
+TSVD_API tsvd_status tsvd_eig(tsvd_handle h, const double* M, int64_t n, int64_t ldm, double* lambda,
                      double* V, int64_t ldv, tsvd_info* info);
 
 /* Algorithm 1 end to end for one matrix.
@@ -119,7 +125,7 @@ tsvd_status tsvd_eig(tsvd_handle h, const double* M, int64_t n, int64_t ldm, dou
  * higher must be TSVD_FP64 for FP32 working and TSVD_DD for FP64 working.
  * Errors: TSVD_ERR_ARG (m < n, n < 1, lda < m, ldv < n, ldu < m with U,
  * null required pointer, bad tag), TSVD_ERR_UNSUPPORTED (n > 256). */
-tsvd_status tsvd_solve(tsvd_handle h, const void* A, int64_t m, int64_t n, int64_t lda,
+TSVD_API tsvd_status tsvd_solve(tsvd_handle h, const void* A, int64_t m, int64_t n, int64_t lda,
                        tsvd_prec working, tsvd_prec higher, void* sigma, void* V, int64_t ldv,
                        void* U, int64_t ldu, tsvd_info* info);
 
@@ -130,7 +136,7 @@ tsvd_status tsvd_solve(tsvd_handle h, const void* A, int64_t m, int64_t n, int64
  * info: NULL or `count` entries (device or pinned host).
  * Errors: TSVD_ERR_ARG for any bad instance (nothing is enqueued),
  * TSVD_ERR_UNSUPPORTED for n > 64. */
-tsvd_status tsvd_batch_solve(tsvd_handle h, int32_t count, const void* const* A, const int64_t* m,
+TSVD_API tsvd_status tsvd_batch_solve(tsvd_handle h, int32_t count, const void* const* A, const int64_t* m,
                              const int64_t* n, const int64_t* lda, tsvd_prec working,
                              tsvd_prec higher, void* const* sigma, void* const* V,
                              const int64_t* ldv, void* const* U, const int64_t* ldu,
@@ -139,13 +145,13 @@ tsvd_status tsvd_batch_solve(tsvd_handle h, int32_t count, const void* const* A,
 /* Synchronise the handle's stream and return the numeric status of the last
  * call (TSVD_OK, TSVD_ERR_NONFINITE, TSVD_ERR_NOT_FULL_RANK,
  * TSVD_ERR_NO_CONVERGENCE) or TSVD_ERR_CUDA. */
-tsvd_status tsvd_sync_status(tsvd_handle h);
+TSVD_API tsvd_status tsvd_sync_status(tsvd_handle h);
 
 /* Per-stage device times of the last tsvd_solve (requires opts.timing = 1):
  * ms[0] Gram (split + MMA + combine), ms[1] eigensolver (scaling, Jacobi,
  * sort, cast), ms[2] compute U, ms[3] total.  Synchronises the stream.
  * These are the components of the paper's time breakdown (Sec. 4.1.2). */
-tsvd_status tsvd_last_stage_ms(tsvd_handle h, float ms[4]);
+TSVD_API tsvd_status tsvd_last_stage_ms(tsvd_handle h, float ms[4]);
 
 #ifdef __cplusplus
 }

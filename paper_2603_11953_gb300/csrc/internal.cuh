@@ -1,0 +1,84 @@
+// internal.cuh -- declarations shared by the CUDA translation units of libtsvd.
+// (Nothing here is shared with the CPU oracle.)
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/tsvd.h"
+
+namespace tsvd {
+
+// Device-side report; layout identical to tsvd_info so it can be copied out.
+struct DevInfo {
+    int flags;        // FLAG_* bits, turned into a tsvd_status by finalize_info
+    int sweeps;
+    double off_norm;
+    double kappa;
+};
+static_assert(sizeof(DevInfo) == sizeof(tsvd_info), "DevInfo must mirror tsvd_info");
+
+enum : int {
+    FLAG_NONFINITE = 1,
+    FLAG_NOT_FULL_RANK = 2,
+    FLAG_NO_CONVERGENCE = 4,
+    FLAG_TIMEOUT = 8,
+};
+
+// Sentinel exponent of an all-zero column (no digits, nothing accumulated).
+constexpr int EXP_EMPTY = -(1 << 20);
+
+// ---------------------------------------------------------------- Gram (Alg. 1 l.1-2)
+// Ozaki split into k = 7 signed digits (|q| <= 128, exact in bf16) relative
+// to a running per-column power-of-two scale; every digit-pair block is an
+// exact integer sum over a 128-row chunk (BF16 MMA, FP32 accumulate, all
+// partial sums below 2^22) folded into two int64 fixed-point accumulators.
+constexpr int GRAM_KC = 128;           // rows per exact chunk
+constexpr int GRAM_DIGITS = 7;         // k
+constexpr int GRAM_MAX_ROWS_PER_CTA = 32768;  // keeps the int64 accumulators in range
+
+struct GramPlan {
+    int NP;            // padded n (16, 32, 48 or 64)
+    int P;             // CTAs over m (split-K)
+    int64_t rows_per_cta;
+};
+GramPlan gram_plan(int64_t m, int n, int sm_count, int split_k_opt);
+size_t gram_partials_bytes(const GramPlan& p);
+
+// part: workspace of gram_partials_bytes(plan) bytes.
+cudaError_t launch_gram_ozaki(const void* A, int working, int64_t m, int n, int64_t lda,
+                              const GramPlan& plan, void* part, DevInfo* info, cudaStream_t s);
+// Combine the partials into G (n x n FP64, both triangles) and optionally the
+// double-double low parts G_lo (may be null).
+cudaError_t launch_gram_combine(const GramPlan& plan, const void* part, int n, double* G,
+                                double* G_lo, int64_t ldg, cudaStream_t s);
+
+// Plain all-FP64 Gram (the comparison form): DFMA over m, fixed-order combine.
+size_t gram_plain_partials_bytes(int64_t m, int n, int sm_count);
+cudaError_t launch_gram_plain(const void* A, int working, int64_t m, int n, int64_t lda,
+                              int sm_count, void* part, double* G, int64_t ldg, DevInfo* info,
+                              cudaStream_t s);
+
+// ---------------------------------------------------------------- eigen stage (Alg. 1 l.3-5)
+// Two-sided Jacobi in FP64 on M (n x n, read from M/ldm), one CTA.
+// scratch: 2*n*n doubles (used when n > 64).  Writes unsorted lambda and V
+// (n x n, ld n) into lam_ws / V_ws.
+cudaError_t launch_jacobi(const double* M, int n, int64_t ldm, double tol, int max_sweeps,
+                          double* scratch, double* lam_ws, double* V_ws, DevInfo* info,
+                          cudaStream_t s);
+
+// Sort descending, sign rule, sigma = sqrt(lambda), round to working.
+// working: 0 FP32, 1 FP64.  Outputs (any may be null):
+//   sigma_w [n], V_w (ldv), W_w = RN(V_w / sigma_w) (ld n) in working type;
+//   lam_sorted [n], V_sorted (ld_vs) in FP64.
+cudaError_t launch_finish(const double* lam_ws, const double* V_ws, int n, int working,
+                          void* sigma_w, void* V_w, int64_t ldv, void* W_w, double* lam_sorted,
+                          double* V_sorted, int64_t ld_vs, DevInfo* info, cudaStream_t s);
+
+// ---------------------------------------------------------------- U (Alg. 1 l.6)
+cudaError_t launch_compute_u(const void* A, int working, int64_t m, int n, int64_t lda,
+                             const void* W, void* U, int64_t ldu, cudaStream_t s);
+
+// flags -> tsvd_status in info->flags (overwritten by the status code).
+cudaError_t launch_finalize_info(DevInfo* info, cudaStream_t s);
+
+}  // namespace tsvd

@@ -1,0 +1,346 @@
+// tsvd_api.cu -- the C ABI (include/tsvd.h): argument checks, workspace,
+// and the launch sequence of Algorithm 1 on the handle's stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.cuh"
+
+using namespace tsvd;
+
+struct tsvd_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    tsvd_opts opts{};
+    int sm_count = 0;
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    DevInfo* dinfo = nullptr;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool have_times = false;
+};
+
+namespace {
+
+constexpr double U_FP64 = 1.1102230246251565e-16;  // 2^-53
+
+size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+tsvd_status from_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return TSVD_OK;
+    if (e == cudaErrorNotSupported) return TSVD_ERR_UNSUPPORTED;
+    if (e == cudaErrorMemoryAllocation) return TSVD_ERR_ALLOC;
+    return TSVD_ERR_CUDA;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+tsvd_status ensure_ws(tsvd_ctx* h, size_t bytes) {
+    if (bytes <= h->ws_bytes) return TSVD_OK;
+    if (h->ws) {
+        cudaStreamSynchronize(h->stream);
+        cudaFree(h->ws);
+        h->ws = nullptr;
+        h->ws_bytes = 0;
+    }
+    if (cudaMalloc(&h->ws, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return TSVD_ERR_ALLOC;
+    }
+    h->ws_bytes = bytes;
+    return TSVD_OK;
+}
+
+size_t wsize(int working) { return working == 0 ? sizeof(float) : sizeof(double); }
+
+// Workspace carve-up of one solve: [partials][G][G_lo][lam][Vh][scratch 2n^2][W].
+struct Layout {
+    size_t part = 0, G = 0, Glo = 0, lam = 0, Vh = 0, scratch = 0, W = 0, total = 0;
+};
+Layout layout_for(int64_t n, size_t part_bytes, int working) {
+    Layout L;
+    size_t off = 0;
+    L.part = off; off += align_up(part_bytes);
+    L.G = off; off += align_up(sizeof(double) * n * n);
+    L.Glo = off; off += align_up(sizeof(double) * n * n);
+    L.lam = off; off += align_up(sizeof(double) * n);
+    L.Vh = off; off += align_up(sizeof(double) * n * n);
+    L.scratch = off; off += align_up(sizeof(double) * 2 * n * n);
+    L.W = off; off += align_up(wsize(working) * n * n);
+    L.total = off;
+    return L;
+}
+
+char* base(tsvd_ctx* h) { return static_cast<char*>(h->ws); }
+
+bool valid_prec_pair(tsvd_prec working, tsvd_prec higher) {
+    return (working == TSVD_FP32 || working == TSVD_FP64) && (higher == TSVD_FP64 || higher == TSVD_DD);
+}
+
+// Gram into G (and G_lo) for one matrix.  Caller validated the arguments.
+tsvd_status run_gram(tsvd_ctx* h, const void* A, int64_t m, int n, int64_t lda, int working,
+                     double* G, double* G_lo, int64_t ldg, size_t part_off) {
+    cudaError_t e;
+    if (h->opts.gram_variant == 1) {
+        e = launch_gram_plain(A, working, m, n, lda, h->sm_count, base(h) + part_off, G, ldg, h->dinfo,
+                              h->stream);
+        if (e == cudaSuccess && G_lo) e = cudaMemsetAsync(G_lo, 0, sizeof(double) * ldg * n, h->stream);
+        return from_cuda(e);
+    }
+    const GramPlan plan = gram_plan(m, n, h->sm_count, h->opts.split_k);
+    e = launch_gram_ozaki(A, working, m, n, lda, plan, base(h) + part_off, h->dinfo, h->stream);
+    if (e != cudaSuccess) return from_cuda(e);
+    return from_cuda(launch_gram_combine(plan, base(h) + part_off, n, G, G_lo, ldg, h->stream));
+}
+
+size_t part_bytes_for(tsvd_ctx* h, int64_t m, int n) {
+    if (h->opts.gram_variant == 1) return gram_plain_partials_bytes(m, n, h->sm_count);
+    return gram_partials_bytes(gram_plan(m, n, h->sm_count, h->opts.split_k));
+}
+
+bool gram_supported(tsvd_ctx* h, int working, int64_t n) {
+    if (n > 64) return false;                      // tensor-core Gram built for n <= 64
+    if (h->opts.gram_variant == 0 && working != TSVD_FP32) return false;
+    return true;
+}
+
+double jacobi_tol(tsvd_ctx* h, int64_t n) {
+    return h->opts.jacobi_tol > 0.0 ? h->opts.jacobi_tol : (double)n * U_FP64;
+}
+int max_sweeps(tsvd_ctx* h) { return h->opts.max_sweeps > 0 ? h->opts.max_sweeps : 40; }
+
+void record(tsvd_ctx* h, int k) {
+    if (h->opts.timing) cudaEventRecord(h->ev[k], h->stream);
+}
+
+// One instance of Algorithm 1, workspace already sized by the caller.
+tsvd_status solve_one(tsvd_ctx* h, const void* A, int64_t m, int n, int64_t lda, int working,
+                      void* sigma, void* V, int64_t ldv, void* U, int64_t ldu, tsvd_info* info,
+                      bool timed) {
+    const Layout L = layout_for(n, part_bytes_for(h, m, n), working);
+    cudaError_t e = cudaMemsetAsync(h->dinfo, 0, sizeof(DevInfo), h->stream);
+    if (e != cudaSuccess) return from_cuda(e);
+    double* G = reinterpret_cast<double*>(base(h) + L.G);
+    double* lam = reinterpret_cast<double*>(base(h) + L.lam);
+    double* Vh = reinterpret_cast<double*>(base(h) + L.Vh);
+    double* scratch = reinterpret_cast<double*>(base(h) + L.scratch);
+    void* W = base(h) + L.W;
+    if (timed) record(h, 0);
+    tsvd_status st = run_gram(h, A, m, n, lda, working, G, nullptr, n, L.part);
+    if (st != TSVD_OK) return st;
+    if (timed) record(h, 1);
+    e = launch_jacobi(G, n, n, jacobi_tol(h, n), max_sweeps(h), scratch, lam, Vh, h->dinfo, h->stream);
+    if (e != cudaSuccess) return from_cuda(e);
+    e = launch_finish(lam, Vh, n, working, sigma, V, ldv, W, nullptr, nullptr, 0, h->dinfo, h->stream);
+    if (e != cudaSuccess) return from_cuda(e);
+    if (timed) record(h, 2);
+    if (U) {
+        e = launch_compute_u(A, working, m, n, lda, W, U, ldu, h->stream);
+        if (e != cudaSuccess) return from_cuda(e);
+    }
+    if (timed) record(h, 3);
+    e = launch_finalize_info(h->dinfo, h->stream);
+    if (e != cudaSuccess) return from_cuda(e);
+    if (info) {
+        e = cudaMemcpyAsync(info, h->dinfo, sizeof(DevInfo), cudaMemcpyDefault, h->stream);
+        if (e != cudaSuccess) return from_cuda(e);
+    }
+    if (timed) h->have_times = true;
+    return TSVD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* tsvd_status_string(tsvd_status s) {
+    switch (s) {
+        case TSVD_OK: return "TSVD_OK";
+        case TSVD_ERR_ARG: return "TSVD_ERR_ARG";
+        case TSVD_ERR_ALIGN: return "TSVD_ERR_ALIGN";
+        case TSVD_ERR_NONFINITE: return "TSVD_ERR_NONFINITE";
+        case TSVD_ERR_NOT_FULL_RANK: return "TSVD_ERR_NOT_FULL_RANK";
+        case TSVD_ERR_NO_CONVERGENCE: return "TSVD_ERR_NO_CONVERGENCE";
+        case TSVD_ERR_TIMEOUT: return "TSVD_ERR_TIMEOUT";
+        case TSVD_ERR_UNSUPPORTED: return "TSVD_ERR_UNSUPPORTED";
+        case TSVD_ERR_CUDA: return "TSVD_ERR_CUDA";
+        case TSVD_ERR_ALLOC: return "TSVD_ERR_ALLOC";
+    }
+    return "TSVD_ERR_UNKNOWN";
+}
+
+tsvd_status tsvd_create(tsvd_handle* out, int device, void* stream, const tsvd_opts* opts) {
+    if (!out) return TSVD_ERR_ARG;
+    *out = nullptr;
+    if (opts) {
+        if (opts->slices != 0 && opts->slices != GRAM_DIGITS) return TSVD_ERR_UNSUPPORTED;
+        if (opts->chunk_rows != 0 && opts->chunk_rows != GRAM_KC) return TSVD_ERR_UNSUPPORTED;
+        if (opts->split_k < 0 || opts->max_sweeps < 0 || opts->jacobi_tol < 0.0) return TSVD_ERR_ARG;
+        if (opts->eig_variant != 0) return TSVD_ERR_UNSUPPORTED;
+        if (opts->gram_variant != 0 && opts->gram_variant != 1) return TSVD_ERR_ARG;
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return TSVD_ERR_CUDA;
+    }
+    DeviceGuard g(device);
+    tsvd_ctx* h = new (std::nothrow) tsvd_ctx();
+    if (!h) return TSVD_ERR_ALLOC;
+    h->device = device;
+    h->stream = static_cast<cudaStream_t>(stream);
+    if (opts) h->opts = *opts;
+    if (cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+        cudaMalloc(&h->dinfo, sizeof(DevInfo)) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return TSVD_ERR_CUDA;
+    }
+    for (auto& ev : h->ev) cudaEventCreate(&ev);
+    *out = h;
+    return TSVD_OK;
+}
+
+tsvd_status tsvd_destroy(tsvd_handle h) {
+    if (!h) return TSVD_ERR_ARG;
+    DeviceGuard g(h->device);
+    cudaStreamSynchronize(h->stream);
+    if (h->ws) cudaFree(h->ws);
+    if (h->dinfo) cudaFree(h->dinfo);
+    for (auto& ev : h->ev)
+        if (ev) cudaEventDestroy(ev);
+    delete h;
+    return TSVD_OK;
+}
+
+tsvd_status tsvd_gram(tsvd_handle h, const void* A, int64_t m, int64_t n, int64_t lda,
+                      tsvd_prec working, tsvd_prec higher, double* G, int64_t ldg) {
+    if (!h || !A || !G || m < 1 || n < 1 || lda < m || ldg < n || !valid_prec_pair(working, higher))
+        return TSVD_ERR_ARG;
+    if (!gram_supported(h, working, n)) return TSVD_ERR_UNSUPPORTED;
+    if (higher == TSVD_DD && h->opts.gram_variant == 1) return TSVD_ERR_UNSUPPORTED;
+    DeviceGuard g(h->device);
+    const size_t pb = part_bytes_for(h, m, (int)n);
+    tsvd_status st = ensure_ws(h, align_up(pb));
+    if (st != TSVD_OK) return st;
+    cudaError_t e = cudaMemsetAsync(h->dinfo, 0, sizeof(DevInfo), h->stream);
+    if (e != cudaSuccess) return from_cuda(e);
+    double* G_lo = higher == TSVD_DD ? G + ldg * n : nullptr;
+    st = run_gram(h, A, m, (int)n, lda, working, G, G_lo, ldg, 0);
+    if (st != TSVD_OK) return st;
+    return from_cuda(launch_finalize_info(h->dinfo, h->stream));
+}
+
+tsvd_status tsvd_eig(tsvd_handle h, const double* M, int64_t n, int64_t ldm, double* lambda,
+                     double* V, int64_t ldv, tsvd_info* info) {
+    if (!h || !M || !lambda || !V || n < 1 || ldm < n || ldv < n) return TSVD_ERR_ARG;
+    if (n > 256) return TSVD_ERR_UNSUPPORTED;
+    DeviceGuard g(h->device);
+    const Layout L = layout_for(n, 0, 1);
+    tsvd_status st = ensure_ws(h, L.total);
+    if (st != TSVD_OK) return st;
+    cudaError_t e = cudaMemsetAsync(h->dinfo, 0, sizeof(DevInfo), h->stream);
+    if (e != cudaSuccess) return from_cuda(e);
+    double* lam = reinterpret_cast<double*>(base(h) + L.lam);
+    double* Vh = reinterpret_cast<double*>(base(h) + L.Vh);
+    double* scratch = reinterpret_cast<double*>(base(h) + L.scratch);
+    e = launch_jacobi(M, (int)n, ldm, jacobi_tol(h, n), max_sweeps(h), scratch, lam, Vh, h->dinfo,
+                      h->stream);
+    if (e == cudaSuccess)
+        e = launch_finish(lam, Vh, (int)n, 1, nullptr, nullptr, 0, nullptr, lambda, V, ldv, h->dinfo,
+                          h->stream);
+    if (e == cudaSuccess) e = launch_finalize_info(h->dinfo, h->stream);
+    if (e == cudaSuccess && info)
+        e = cudaMemcpyAsync(info, h->dinfo, sizeof(DevInfo), cudaMemcpyDefault, h->stream);
+    return from_cuda(e);
+}
+
+tsvd_status tsvd_solve(tsvd_handle h, const void* A, int64_t m, int64_t n, int64_t lda,
+                       tsvd_prec working, tsvd_prec higher, void* sigma, void* V, int64_t ldv,
+                       void* U, int64_t ldu, tsvd_info* info) {
+    if (!h || !A || !sigma || !V || n < 1 || m < n || lda < m || ldv < n || (U && ldu < m) ||
+        !valid_prec_pair(working, higher))
+        return TSVD_ERR_ARG;
+    if (!(working == TSVD_FP32 && higher == TSVD_FP64)) return TSVD_ERR_UNSUPPORTED;
+    if (!gram_supported(h, working, n)) return TSVD_ERR_UNSUPPORTED;
+    DeviceGuard g(h->device);
+    const Layout L = layout_for(n, part_bytes_for(h, m, (int)n), working);
+    tsvd_status st = ensure_ws(h, L.total);
+    if (st != TSVD_OK) return st;
+    h->have_times = false;
+    return solve_one(h, A, m, (int)n, lda, working, sigma, V, ldv, U, ldu, info, true);
+}
+
+tsvd_status tsvd_batch_solve(tsvd_handle h, int32_t count, const void* const* A, const int64_t* m,
+                             const int64_t* n, const int64_t* lda, tsvd_prec working,
+                             tsvd_prec higher, void* const* sigma, void* const* V,
+                             const int64_t* ldv, void* const* U, const int64_t* ldu,
+                             tsvd_info* info) {
+    if (!h || count < 0 || (count > 0 && (!A || !m || !n || !lda || !sigma || !V || !ldv)))
+        return TSVD_ERR_ARG;
+    if (!valid_prec_pair(working, higher)) return TSVD_ERR_ARG;
+    if (!(working == TSVD_FP32 && higher == TSVD_FP64)) return TSVD_ERR_UNSUPPORTED;
+    size_t need = 0;
+    for (int32_t i = 0; i < count; ++i) {
+        const bool want_u = U && U[i];
+        if (!A[i] || !sigma[i] || !V[i] || n[i] < 1 || m[i] < n[i] || lda[i] < m[i] || ldv[i] < n[i] ||
+            (want_u && (!ldu || ldu[i] < m[i])))
+            return TSVD_ERR_ARG;
+        if (n[i] > 64) return TSVD_ERR_UNSUPPORTED;
+        need = std::max(need, layout_for(n[i], part_bytes_for(h, m[i], (int)n[i]), working).total);
+    }
+    DeviceGuard g(h->device);
+    tsvd_status st = ensure_ws(h, need);
+    if (st != TSVD_OK) return st;
+    h->have_times = false;
+    for (int32_t i = 0; i < count; ++i) {
+        const bool want_u = U && U[i];
+        st = solve_one(h, A[i], m[i], (int)n[i], lda[i], working, sigma[i], V[i], ldv[i],
+                       want_u ? U[i] : nullptr, want_u ? ldu[i] : 0, info ? info + i : nullptr, false);
+        if (st != TSVD_OK) return st;
+    }
+    return TSVD_OK;
+}
+
+tsvd_status tsvd_sync_status(tsvd_handle h) {
+    if (!h) return TSVD_ERR_ARG;
+    DeviceGuard g(h->device);
+    DevInfo d;
+    if (cudaMemcpyAsync(&d, h->dinfo, sizeof(d), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return TSVD_ERR_CUDA;
+    }
+    // Before finalize the word holds flag bits; after it holds a status code.
+    return static_cast<tsvd_status>(d.flags);
+}
+
+tsvd_status tsvd_last_stage_ms(tsvd_handle h, float ms[4]) {
+    if (!h || !ms) return TSVD_ERR_ARG;
+    if (!h->opts.timing || !h->have_times) return TSVD_ERR_ARG;
+    DeviceGuard g(h->device);
+    if (cudaEventSynchronize(h->ev[3]) != cudaSuccess) return TSVD_ERR_CUDA;
+    float a = 0, b = 0, c = 0, t = 0;
+    cudaEventElapsedTime(&a, h->ev[0], h->ev[1]);
+    cudaEventElapsedTime(&b, h->ev[1], h->ev[2]);
+    cudaEventElapsedTime(&c, h->ev[2], h->ev[3]);
+    cudaEventElapsedTime(&t, h->ev[0], h->ev[3]);
+    ms[0] = a; ms[1] = b; ms[2] = c; ms[3] = t;
+    return TSVD_OK;
+}
+
+}  // extern "C"

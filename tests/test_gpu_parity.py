@@ -1,0 +1,298 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Tolerances (each derived in the design doc):
+  * Gram (Alg. 1 l.2, eq. (ATA) with eps_M = 2^-50): |G - S| <= 2^-50 (|A|^T|A|)
+    componentwise, S the exact sum; plus the deterministic any-size bound
+    |G - S|_ij <= m * 2^-50 * 2^(E_i + E_j) with 2^E_j <= 2 max_r |a_rj|.
+  * eigenvalues (same M into both Jacobis): relative difference
+    <= 32 n u_h kappa(C), C = D^-1 M D^-1.
+  * sigma end to end, FP32 working: |sigma - sigma_oracle| <= 2 u_32 sigma_oracle
+    (the higher-precision errors are far below one FP32 ulp for kappa(B) <= 1e3).
+  * U (eq. (AV-0)): |U - RN_32(A W)| <= (n + 1) u_32 (|A| |W|), W = RN_32(V / sigma).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2603_11953_gb300 as T
+from paper_2603_11953_gb300 import build as B
+from paper_2603_11953_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+U32 = 2.0 ** -24
+UH = 2.0 ** -53
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    B.build()
+    T.load_library()
+
+
+def handle(**kw):
+    opts = T.tsvd_opts(**kw) if kw else None
+    h, _ = T.tsvd_create(0, torch.cuda.current_stream().cuda_stream, opts)
+    return h
+
+
+def colmajor(ld, n, dtype, device="cuda"):
+    return torch.zeros(n, ld, dtype=dtype, device=device).T  # (ld, n), column j contiguous
+
+
+def gpu_gram(A, m, n, lda, h=None, higher=T.TSVD_FP64):
+    own = h is None
+    h = handle() if own else h
+    G = torch.zeros(2 * n * n, dtype=torch.float64, device="cuda")
+    T.tsvd_gram(h, A, m, n, lda, T.TSVD_FP32, higher, G, n)
+    st = T.tsvd_sync_status(h)
+    if own:
+        T.tsvd_destroy(h)
+    Gh = G[: n * n].view(n, n).T.cpu().numpy()
+    Gl = G[n * n:].view(n, n).T.cpu().numpy()
+    return Gh, Gl, st
+
+
+def gpu_solve(A, m, n, lda, want_u=True, h=None):
+    own = h is None
+    h = handle() if own else h
+    sigma = torch.zeros(n, dtype=torch.float32, device="cuda")
+    V = colmajor(n, n, torch.float32)
+    U = colmajor(max(m, 1), n, torch.float32) if want_u else None
+    info = torch.zeros(6, dtype=torch.int32, device="cuda")
+    T.tsvd_solve(h, A, m, n, lda, T.TSVD_FP32, T.TSVD_FP64, sigma, V, n, U, m if want_u else 0, info)
+    torch.cuda.synchronize()
+    if own:
+        T.tsvd_destroy(h)
+    inf = info.cpu().numpy()
+    return (sigma.cpu().numpy().astype(np.float64), V.cpu().numpy().astype(np.float64),
+            None if U is None else U[:m].cpu().numpy().astype(np.float64), int(inf[0]), int(inf[1]))
+
+
+def exp_bound(A):
+    mx = np.abs(A).max(axis=0).astype(np.float64)
+    return 2.0 * np.where(mx > 0, mx, 0.0)
+
+
+def check_gram(A_np, Gh, m, n):
+    S_hi, S_lo, Sabs = oracle.gram(A_np)
+    err = np.abs((Gh - S_hi) - S_lo)  # |G - S| with S = S_hi + S_lo (exact to 2^-106)
+    ratio = np.where(Sabs > 0, err / np.where(Sabs > 0, Sabs, 1.0), 0.0)
+    any_size = m * 2.0 ** -50 * np.outer(exp_bound(A_np), exp_bound(A_np))
+    assert np.all(err <= any_size), float(np.max(err - any_size))
+    return float(ratio.max())
+
+
+# ------------------------------------------------------------------ Gram (a1-a3)
+@pytest.mark.parametrize("m,n,split", [(1000, 1, 0), (1000, 5, 0), (20000, 16, 0), (4133, 33, 3),
+                                       (70001, 48, 0), (131077, 64, 0), (131077, 64, 5)])
+def test_gram_matches_exact_sum(m, n, split):
+    A, _ = workloads.small_case(m, n, kappa_sigma=1e3, logd=3.0, seed=m + n, device="cuda")
+    h = handle(split_k=split) if split else None
+    Gh, Gl, st = gpu_gram(A, m, n, m, h=h)
+    if h is not None:
+        T.tsvd_destroy(h)
+    assert st == T.TSVD_OK
+    A_np = workloads.to_numpy_colmajor(A, m)
+    worst = check_gram(A_np, Gh, m, n)
+    assert worst <= 2.0 ** -50, worst
+    assert np.array_equal(Gh, Gh.T)
+
+
+def test_gram_deterministic_and_dd_output():
+    m, n = 50000, 40
+    A, _ = workloads.small_case(m, n, seed=3, device="cuda")
+    G1, L1, _ = gpu_gram(A, m, n, m, higher=T.TSVD_DD)
+    G2, L2, _ = gpu_gram(A, m, n, m, higher=T.TSVD_DD)
+    assert np.array_equal(G1, G2) and np.array_equal(L1, L2)
+    # the DD pair is a faithful split of one exact number: |lo| <= ulp(hi)/2
+    assert np.all(np.abs(L1) <= np.spacing(np.abs(G1)) / 2)
+
+
+def test_gram_lda_unaligned_and_ragged():
+    m, n, lda = 3001, 24, 3010
+    base = torch.zeros(lda * n + 1, dtype=torch.float32, device="cuda")
+    A, _ = workloads.small_case(m, n, seed=9, device="cuda", lda=lda)
+    flat = A.T.reshape(-1)
+    base[1:] = flat  # base pointer offset by 4 bytes: not 16-byte aligned
+    Au = base[1:]
+    Gh, _, st = gpu_gram(Au, m, n, lda)
+    assert st == T.TSVD_OK
+    A_np = workloads.to_numpy_colmajor(A, m)
+    assert check_gram(A_np, Gh, m, n) <= 2.0 ** -50
+
+
+def test_gram_powers_of_two_and_stacking_are_exact():
+    """Invariants the exact construction guarantees bitwise: [A; A] gives 2G
+    when both halves land on the same per-CTA scales (one CTA, and row 0
+    holds every column's largest magnitude so the running scale is final
+    after the first chunk: a later growth would re-grid, i.e. truncate, the
+    earlier chunks), and scaling a column by 2^p scales its row/column of G
+    by 2^p."""
+    m, n = 2048, 8
+    A, _ = workloads.small_case(m, n, seed=4, device="cuda")
+    A[0, :] = 1.5 * A[:m].abs().max(dim=0).values
+    h = handle(split_k=1)
+    G, _, _ = gpu_gram(A, m, n, m, h=h)
+    AA = torch.cat([A[:m], A[:m]], 0).contiguous()
+    AA = AA.T.contiguous().T  # column-major
+    G2, _, _ = gpu_gram(AA, 2 * m, n, 2 * m, h=h)
+    T.tsvd_destroy(h)
+    assert np.array_equal(G2, 2 * G)
+    As = A.clone()
+    As[:, 3] *= 2.0 ** 20
+    Gs, _, _ = gpu_gram(As, m, n, m)
+    sc = np.ones(n)
+    sc[3] = 2.0 ** 20
+    assert np.array_equal(Gs, G * np.outer(sc, sc))
+
+
+# ------------------------------------------------------------------ Jacobi (a4-a6)
+@pytest.mark.parametrize("n,kappa,logd", [(1, 1.0, 0.0), (2, 10.0, 1.0), (7, 1e2, 2.0), (16, 1e3, 3.0),
+                                          (33, 1e3, 3.0), (64, 1e4, 4.0)])
+def test_eig_matches_oracle_jacobi(n, kappa, logd):
+    m = max(4 * n, 200)
+    A, _ = workloads.small_case(m, n, kappa_sigma=kappa, logd=logd, seed=11 * n)
+    S_hi, _, _ = oracle.gram(workloads.to_numpy_colmajor(A, m))
+    lam_o, V_o, sw, st = oracle.jacobi_fp64(S_hi)
+    assert st == 0
+    lam_o = np.sort(lam_o)[::-1]
+    M = torch.from_numpy(np.asfortranarray(S_hi)).cuda().T.contiguous().T
+    lam = torch.zeros(n, dtype=torch.float64, device="cuda")
+    V = colmajor(n, n, torch.float64)
+    info_d = torch.zeros(6, dtype=torch.int32, device="cuda")
+    h = handle()
+    T.tsvd_eig(h, M, n, n, lam, V, n, info_d)
+    torch.cuda.synchronize()
+    T.tsvd_destroy(h)
+    inf = info_d.cpu().numpy()
+    assert inf[0] == T.TSVD_OK
+    d = np.sqrt(np.diag(S_hi))
+    kC = np.linalg.cond(S_hi / np.outer(d, d))
+    lam_g = lam.cpu().numpy()
+    np.testing.assert_allclose(lam_g, lam_o, rtol=32 * n * UH * kC)
+    Vg = V.cpu().numpy()
+    assert np.abs(Vg.T @ Vg - np.eye(n)).max() <= 64 * n * UH
+    # eigenvectors: scaled residual of every column against the same M
+    R = S_hi @ Vg - Vg * lam_g
+    assert np.all(np.linalg.norm(R, axis=0) <= 64 * n * UH * kC * np.abs(lam_g).max() + 1e-300)
+
+
+# ------------------------------------------------------------------ solve (a1-a7)
+@pytest.mark.parametrize("m,n,kappa,logd", [(20000, 16, 1e3, 3.0), (5000, 1, 1.0, 0.0), (16, 16, 1e2, 1.0),
+                                            (12345, 33, 1e3, 3.0), (65537, 64, 1e3, 3.0)])
+def test_solve_matches_oracle(m, n, kappa, logd):
+    A, _ = workloads.small_case(m, n, kappa_sigma=kappa, logd=logd, seed=5 * m + n, device="cuda")
+    sig, V, U, st, sweeps = gpu_solve(A, m, n, m)
+    assert st == T.TSVD_OK
+    A_np = workloads.to_numpy_colmajor(A, m)
+    ref = oracle.svd(A_np, higher=1)
+    assert ref["status"] == 0
+    rel = np.abs(sig - ref["sigma_h"]) / ref["sigma_h"]
+    assert rel.max() <= 2 * U32, rel.max()
+    assert rel.max() <= 1e-5
+    # V: same sign rule; entrywise against the oracle within the cast + eigenvector error
+    gaps = np.abs(np.diff(ref["sigma_h"] ** 2)) / ref["sigma_h"][:-1] ** 2 if n > 1 else np.array([1.0])
+    if n > 1 and gaps.min() > 1e-3:
+        assert np.abs(V - ref["V_w"]).max() <= 4 * U32 + 1e-9 / gaps.min()
+    # U against the exactly rounded product with the GPU's own W (eq. (AV-0))
+    W = (V.astype(np.float32) / sig.astype(np.float32)).astype(np.float64)
+    rows = np.unique(np.concatenate([np.arange(min(m, 64)), np.linspace(0, m - 1, 200).astype(np.int64)]))
+    Uref = oracle.rows_times(A_np, W, rows, 24)
+    bound = (n + 1) * U32 * (np.abs(A_np[rows].astype(np.float64)) @ np.abs(W)) + 1e-38
+    assert np.all(np.abs(U[rows] - Uref) <= bound)
+    # Remark 1: U is orthonormal to O(u) + O(u_h) kappa^2(B)
+    orth = np.abs(U.T @ U - np.eye(n)).max()
+    assert orth <= 1e-4, orth
+
+
+def test_batch_equals_single_solves():
+    cases = [(3000, 8), (1024, 16), (7777, 24), (2048, 64), (4096, 1)]
+    As = [workloads.small_case(m, n, seed=31 + i, device="cuda")[0] for i, (m, n) in enumerate(cases)]
+    sig = [torch.zeros(n, device="cuda") for _, n in cases]
+    Vs = [colmajor(n, n, torch.float32) for _, n in cases]
+    Us = [colmajor(m, n, torch.float32) for m, n in cases]
+    info = torch.zeros(6 * len(cases), dtype=torch.int32, device="cuda")
+    h = handle()
+    T.tsvd_batch_solve(h, len(cases), As, [m for m, _ in cases], [n for _, n in cases], [m for m, _ in cases],
+                       T.TSVD_FP32, T.TSVD_FP64, sig, Vs, [n for _, n in cases], Us, [m for m, _ in cases],
+                       info)
+    torch.cuda.synchronize()
+    T.tsvd_destroy(h)
+    assert np.all(info.view(len(cases), 6)[:, 0].cpu().numpy() == 0)
+    for k, (m, n) in enumerate(cases):
+        s1, V1, U1, st, _ = gpu_solve(As[k], m, n, m)
+        assert np.array_equal(s1, sig[k].cpu().numpy().astype(np.float64))
+        assert np.array_equal(V1, Vs[k].cpu().numpy().astype(np.float64))
+        assert np.array_equal(U1, Us[k][:m].cpu().numpy().astype(np.float64))
+
+
+# ------------------------------------------------------------------ statuses and arguments
+def test_status_nonfinite_rank_convergence_and_args():
+    m, n = 4096, 8
+    A, _ = workloads.small_case(m, n, seed=2, device="cuda")
+    B = A.clone()
+    B[100, 3] = float("nan")
+    assert gpu_solve(B, m, n, m, want_u=False)[3] == T.TSVD_ERR_NONFINITE
+    C = A.clone()
+    C[:, 5] = 0.0
+    assert gpu_solve(C, m, n, m, want_u=False)[3] == T.TSVD_ERR_NOT_FULL_RANK
+    h = handle(max_sweeps=1)
+    assert gpu_solve(A, m, n, m, want_u=False, h=h)[3] == T.TSVD_ERR_NO_CONVERGENCE
+    T.tsvd_destroy(h)
+    h = handle()
+    sig = torch.zeros(n, device="cuda")
+    V = colmajor(n, n, torch.float32)
+    assert T.tsvd_solve(h, A, n - 1, n, m, 0, 1, sig, V, n, check=False) == T.TSVD_ERR_ARG  # m < n
+    assert T.tsvd_solve(h, A, m, n, m - 1, 0, 1, sig, V, n, check=False) == T.TSVD_ERR_ARG  # lda < m
+    assert T.tsvd_solve(h, A, m, n, m, 0, 1, sig, V, n - 1, check=False) == T.TSVD_ERR_ARG  # ldv < n
+    assert T.tsvd_solve(h, A, m, n, m, 0, 7, sig, V, n, check=False) == T.TSVD_ERR_ARG  # bad tag
+    assert T.tsvd_solve(h, A, m, 300, m, 0, 1, sig, V, 300, check=False) == T.TSVD_ERR_UNSUPPORTED
+    T.tsvd_destroy(h)
+
+
+# ------------------------------------------------------------------ full size, bench configuration
+@pytest.mark.parametrize("name", ["ozaki_4194304x64_fp32"])
+def test_full_size_sampled(name):
+    spec = workloads.CONFIGS[name]
+    A, meta = workloads.make_config(spec, device="cuda")
+    m, n = spec.m, spec.n
+    h = handle()
+    G = torch.zeros(n * n, dtype=torch.float64, device="cuda")
+    T.tsvd_gram(h, A, m, n, m, T.TSVD_FP32, T.TSVD_FP64, G, n)
+    sig, V, U, st, _ = gpu_solve(A, m, n, m, h=h)
+    T.tsvd_destroy(h)
+    assert st == T.TSVD_OK
+    Gg = G.view(n, n).T.cpu().numpy()
+    # sampled Gram entries against the exact oracle, column pairs one by one
+    rng = np.random.default_rng(0)
+    pairs = [(0, 0), (n - 1, n - 1), (0, n - 1)] + [tuple(sorted(rng.integers(0, n, 2))) for _ in range(3)]
+    for i, j in pairs:
+        cols = sorted({i, j})
+        Ac = A[:m, cols].cpu().numpy()
+        S_hi, S_lo, Sabs = oracle.gram(np.asfortranarray(Ac))
+        a, b = cols.index(i), cols.index(j)
+        err = abs((Gg[i, j] - S_hi[a, b]) - S_lo[a, b])
+        assert err <= 2.0 ** -50 * Sabs[a, b], (i, j, err / Sabs[a, b])
+    # the eigen stage on the GPU's own Gram against the oracle's Jacobi
+    lam_o, V_o, _, st_o = oracle.jacobi_fp64(Gg)
+    assert st_o == 0
+    sig_o = np.sqrt(np.sort(lam_o)[::-1])
+    d = np.sqrt(np.diag(Gg))
+    kC = np.linalg.cond(Gg / np.outer(d, d))
+    assert np.all(np.abs(sig - sig_o) <= (2 * U32 + 32 * n * UH * kC) * sig_o)
+    # sampled U rows against the exactly rounded product with the GPU's W
+    W = (V.astype(np.float32) / sig.astype(np.float32)).astype(np.float64)
+    rows = np.unique(np.concatenate([[0, 1, m - 1], rng.integers(0, m, 61)]))
+    A_rows = A[torch.from_numpy(rows).cuda()].cpu().numpy()
+    Uref = oracle.rows_times(np.asfortranarray(A_rows), W, np.arange(len(rows)), 24)
+    bound = (n + 1) * U32 * (np.abs(A_rows.astype(np.float64)) @ np.abs(W)) + 1e-38
+    assert np.all(np.abs(U[rows] - Uref) <= bound)
+    Ut = torch.from_numpy(U).cuda()
+    orth = (Ut.T @ Ut - torch.eye(n, dtype=torch.float64, device="cuda")).abs().max().item()
+    assert orth <= 1e-3, orth
