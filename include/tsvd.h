@@ -32,6 +32,7 @@
 #ifndef TSVD_H
 #define TSVD_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #if defined(__GNUC__)
@@ -152,6 +153,37 @@ TSVD_API tsvd_status tsvd_sync_status(tsvd_handle h);
  * sort, cast), ms[2] compute U, ms[3] total.  Synchronises the stream.
  * These are the components of the paper's time breakdown (Sec. 4.1.2). */
 TSVD_API tsvd_status tsvd_last_stage_ms(tsvd_handle h, float ms[4]);
+
+/* Size of the one device array that tsvd_gram_static works in (16 MiB). */
+#define TSVD_GRAM_STATIC_SCRATCH_BYTES ((size_t)16 << 20)
+
+/* The Gram matrix of tsvd_gram without any allocation.  The paper has no
+ * counterpart: this exists for callers that cannot call cudaMalloc
+ * (services that reserve all device memory up front and forbid allocation
+ * on the request path, plug-ins that must not own device memory, code that
+ * may not risk the implicit synchronisation of cudaMalloc / cudaFree).  It
+ * needs no handle and allocates nothing: its split-K partials and status
+ * block live in one fixed device array of TSVD_GRAM_STATIC_SCRATCH_BYTES
+ * that every GPU which loads this part of the library holds until exit.
+ *   A, m, n, lda, working, higher, G, ldg: as for tsvd_gram (working must be
+ *     TSVD_FP32, n <= 64); results are those of tsvd_gram with default
+ *     options.  info: NULL or a device / pinned-host tsvd_info.  stream: a
+ *     cudaStream_t (NULL = the legacy default stream); the work runs on the
+ *     calling thread's current device.
+ *   The first call on each device looks up the array's device address
+ *   (cudaGetSymbolAddress, with that device current) and caches it; make
+ *   that first call before any stream capture.
+ *   Every call reuses the same array and leaves its contents behind (the
+ *   status block is cleared at the start of each call); calls that overlap
+ *   on the GPU, e.g. on two streams at once, race on it.
+ * Errors: TSVD_ERR_ARG as tsvd_gram; TSVD_ERR_UNSUPPORTED when the partials
+ * would not fit the array, i.e. m > 32768 * floor((16 MiB - 512) /
+ * (16 NP^2 + 4 NP)) with NP = n rounded up to 16, 32, 48 or 64 (for n = 64:
+ * m > 8,323,072), or for FP64 working / n > 64; TSVD_ERR_CUDA if the
+ * runtime fails. */
+TSVD_API tsvd_status tsvd_gram_static(const void* A, int64_t m, int64_t n, int64_t lda,
+                                      tsvd_prec working, tsvd_prec higher, double* G, int64_t ldg,
+                                      tsvd_info* info, void* stream);
 
 #ifdef __cplusplus
 }

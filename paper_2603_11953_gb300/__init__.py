@@ -24,7 +24,8 @@ TSVD_FP32, TSVD_FP64, TSVD_DD = 0, 1, 2
  TSVD_ERR_ALLOC) = range(10)
 
 EXPORTED = ["tsvd_create", "tsvd_destroy", "tsvd_status_string", "tsvd_gram", "tsvd_eig",
-            "tsvd_solve", "tsvd_batch_solve", "tsvd_sync_status", "tsvd_last_stage_ms"]
+            "tsvd_solve", "tsvd_batch_solve", "tsvd_sync_status", "tsvd_last_stage_ms",
+            "tsvd_gram_static"]
 
 
 class tsvd_opts(ctypes.Structure):
@@ -70,6 +71,7 @@ def load_library(path: str = LIB_PATH):
         lib.tsvd_batch_solve.argtypes = [P, I32, P, P, P, P, I, I, P, P, P, P, P, P]
         lib.tsvd_sync_status.argtypes = [P]
         lib.tsvd_last_stage_ms.argtypes = [P, ctypes.POINTER(ctypes.c_float)]
+        lib.tsvd_gram_static.argtypes = [P, I64, I64, I64, I, I, P, I64, P, P]
         for name in EXPORTED:
             if name != "tsvd_status_string":
                 getattr(lib, name).restype = ctypes.c_int
@@ -148,6 +150,13 @@ def tsvd_batch_solve(h, count, A, m, n, lda, working, higher, sigma, V, ldv, U=N
     st = load_library().tsvd_batch_solve(h, int(count), cast[0], cast[1], cast[2], cast[3], int(working),
                                          int(higher), cast[4], cast[5], cast[6], cast[7], cast[8], _p(info))
     return _check("tsvd_batch_solve", st) if check else st
+
+
+def tsvd_gram_static(A, m, n, lda, working, higher, G, ldg, info=None, stream=None, check=True):
+    """Allocation-free Gram (no handle): see include/tsvd.h."""
+    st = load_library().tsvd_gram_static(_p(A), int(m), int(n), int(lda), int(working), int(higher), _p(G),
+                                         int(ldg), _p(info), None if stream is None else ctypes.c_void_p(int(stream)))
+    return _check("tsvd_gram_static", st) if check else st
 
 
 def tsvd_sync_status(h) -> int:
