@@ -71,7 +71,9 @@ typedef struct {
     int split_k;           /* CTAs over m for the Gram (default: from m and the SM count) */
     double jacobi_tol;     /* skip test |m_pq| <= tol*sqrt(m_pp m_qq) (default n * 2^-53) */
     int max_sweeps;        /* Jacobi sweep limit (default 40) */
-    int eig_variant;       /* 0 = two-sided Jacobi (only variant built) */
+    int eig_variant;       /* 0 = default (2 for n <= 64, else 1); 1 = two-sided
+                              Jacobi on M_h (Sec. 2.1); 2 = pivoted Cholesky of M_h
+                              + one-sided Jacobi on R^T, both in FP64 (n <= 64) */
     int autotune;          /* reserved (0) */
     long long timeout_cycles; /* reserved: limit for device spin-waits (0 = default) */
     int gram_variant;      /* 0 = Ozaki-BF16 tensor-core Gram, 1 = plain FP64 Gram */

@@ -105,7 +105,175 @@ cudaError_t launch_u_t(const T* A, int64_t m, int n, int64_t lda, const T* W, T*
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- v2: FP32, n <= 64
+// Persistent CTAs stream 128-row tiles of A through a 2-stage shared-memory
+// ring filled by cp.async.bulk (one contiguous copy per column) and signalled
+// by an mbarrier.  Each of the 128 threads owns an 8-row x 8-column block of
+// the U tile and accumulates with packed FP32 FMAs (fma.rn.f32x2): row pairs
+// of A times a duplicated W entry, W being stored pre-duplicated ({w, w}) in
+// shared memory so that no operand shuffles are needed.
+constexpr int U2_ROWS = 128;
+constexpr int U2_THREADS = 128;
+constexpr int U2_STAGES = 2;
+constexpr long long U2_WAIT_LIMIT = 1ll << 26;  // bounded mbarrier polls
+
+__device__ __forceinline__ uint32_t u2_smem(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void u2_mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(u2_smem(bar)), "r"(count));
+}
+__device__ __forceinline__ void u2_mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(u2_smem(bar)), "r"(bytes)
+                 : "memory");
+}
+// Wait for phase `parity` of the barrier; false if the poll limit ran out.
+__device__ __forceinline__ bool u2_mbar_wait(uint64_t* bar, unsigned parity) {
+    for (long long it = 0; it < U2_WAIT_LIMIT; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(u2_smem(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+__device__ __forceinline__ void u2_bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            u2_smem(dst)),
+        "l"(src), "r"(bytes), "r"(u2_smem(bar))
+        : "memory");
+}
+__device__ __forceinline__ unsigned long long f2pack(float lo, float hi) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2unpack(unsigned long long v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b,
+                                                    unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+__global__ void __launch_bounds__(U2_THREADS)
+    compute_u_v2_kernel(const float* __restrict__ A, int64_t m, int n, int64_t lda, const float* __restrict__ W,
+                        float* __restrict__ U, int64_t ldu, int64_t ntiles, DevInfo* info) {
+    extern __shared__ __align__(128) unsigned char u2smem[];
+    float* Ast = reinterpret_cast<float*>(u2smem);                         // [STAGES][64][128]
+    float* Wd = Ast + (size_t)U2_STAGES * 64 * U2_ROWS;                       // [64][128] = {w,w} pairs
+    __shared__ __align__(8) uint64_t full[U2_STAGES];
+    __shared__ int s_abort;
+    const int tid = threadIdx.x;
+    const int tr = tid & 15;   // rows 8 tr .. 8 tr + 7 of the tile
+    const int tc = tid >> 4;   // columns 8 tc .. 8 tc + 7
+    for (int idx = tid; idx < 64 * 64; idx += U2_THREADS) {
+        const int c = idx >> 6, j = idx & 63;
+        const float w = (c < n && j < n) ? W[c + (size_t)j * n] : 0.f;
+        Wd[c * 128 + 2 * j] = w;
+        Wd[c * 128 + 2 * j + 1] = w;
+    }
+    if (tid == 0) {
+        for (int s = 0; s < U2_STAGES; ++s) u2_mbar_init(&full[s], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_abort = 0;
+    }
+    __syncthreads();
+    // a tile is bulk-loadable when every column segment is a whole number of 16-byte units
+    auto issue = [&](int64_t tile, int stage) {
+        const int64_t r0 = tile * U2_ROWS;
+        const int rows = (int)((m - r0) < U2_ROWS ? (m - r0) : U2_ROWS);
+        const unsigned bytes = (unsigned)rows * 4u;
+        u2_mbar_expect_tx(&full[stage], bytes * (unsigned)n);
+        for (int c = 0; c < n; ++c)
+            u2_bulk_g2s(Ast + ((size_t)stage * 64 + c) * U2_ROWS, A + (size_t)c * lda + r0, bytes, &full[stage]);
+    };
+    int64_t tile = blockIdx.x;
+    if (tid == 0 && tile < ntiles) issue(tile, 0);
+    unsigned phase_bits = 0u;  // bit s: parity to wait for on full[s]
+    for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
+        const int stage = it & 1;
+        const int64_t next = tile + gridDim.x;
+        if (tid == 0 && next < ntiles) issue(next, stage ^ 1);
+        if (!u2_mbar_wait(&full[stage], (phase_bits >> stage) & 1u)) {
+            atomicOr(&info->flags, FLAG_TIMEOUT);
+            atomicExch(&s_abort, 1);
+        }
+        phase_bits ^= 1u << stage;
+        __syncthreads();
+        if (s_abort) break;
+        const float* At = Ast + (size_t)stage * 64 * U2_ROWS;
+        unsigned long long acc[4][8];  // [row pair][column]
+#pragma unroll
+        for (int rp = 0; rp < 4; ++rp)
+#pragma unroll
+            for (int k = 0; k < 8; ++k) acc[rp][k] = 0ull;
+        for (int c = 0; c < n; ++c) {
+            const ulonglong2 a01 = *reinterpret_cast<const ulonglong2*>(At + c * U2_ROWS + 8 * tr);
+            const ulonglong2 a23 = *reinterpret_cast<const ulonglong2*>(At + c * U2_ROWS + 8 * tr + 4);
+            const unsigned long long ap[4] = {a01.x, a01.y, a23.x, a23.y};
+            const ulonglong2* wv = reinterpret_cast<const ulonglong2*>(Wd + c * 128 + 16 * tc);
+            const ulonglong2 w01 = wv[0], w23 = wv[1], w45 = wv[2], w67 = wv[3];
+            const unsigned long long wp[8] = {w01.x, w01.y, w23.x, w23.y, w45.x, w45.y, w67.x, w67.y};
+#pragma unroll
+            for (int rp = 0; rp < 4; ++rp)
+#pragma unroll
+                for (int k = 0; k < 8; ++k) acc[rp][k] = ffma2(ap[rp], wp[k], acc[rp][k]);
+        }
+        const int64_t r0 = tile * U2_ROWS + 8 * tr;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int j = 8 * tc + k;
+            if (j >= n) continue;
+            float v[8];
+#pragma unroll
+            for (int rp = 0; rp < 4; ++rp) f2unpack(acc[rp][k], v[2 * rp], v[2 * rp + 1]);
+            float* dst = U + (size_t)j * ldu + r0;
+            if (r0 + 7 < m) {
+                reinterpret_cast<float4*>(dst)[0] = make_float4(v[0], v[1], v[2], v[3]);
+                reinterpret_cast<float4*>(dst)[1] = make_float4(v[4], v[5], v[6], v[7]);
+            } else {
+#pragma unroll
+                for (int r = 0; r < 8; ++r)
+                    if (r0 + r < m) dst[r] = v[r];
+            }
+        }
+        __syncthreads();  // every thread is done with this stage before it is refilled
+    }
+    if (s_abort && tid == 0) {
+        // leave no bulk copy in flight: wait (bounded) for the other stage too
+        for (int s = 0; s < U2_STAGES; ++s) (void)u2_mbar_wait(&full[s], (phase_bits >> s) & 1u);
+    }
+}
+
 }  // namespace
+
+size_t compute_u_v2_smem() { return sizeof(float) * ((size_t)U2_STAGES * 64 * U2_ROWS + 64 * 128); }
+
+cudaError_t launch_compute_u_v2(const float* A, int64_t m, int n, int64_t lda, const float* W, float* U,
+                                int64_t ldu, int sm_count, DevInfo* info, cudaStream_t s) {
+    const size_t smem = compute_u_v2_smem();
+    cudaError_t e = cudaFuncSetAttribute(compute_u_v2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t ntiles = (m + U2_ROWS - 1) / U2_ROWS;
+    int64_t grid = (int64_t)sm_count * 2;
+    if (grid > ntiles) grid = ntiles;
+    compute_u_v2_kernel<<<(unsigned)grid, U2_THREADS, smem, s>>>(A, m, n, lda, W, U, ldu, ntiles, info);
+    return cudaGetLastError();
+}
+
+bool compute_u_v2_ok(const void* A, int working, int64_t m, int n, int64_t lda, const void* U, int64_t ldu) {
+    // every column segment of every tile must be a whole number of 16-byte units
+    return working == 0 && n <= 64 && ((uintptr_t)A % 16 == 0) && (lda % 4 == 0) && (m % 4 == 0) &&
+           ((uintptr_t)U % 16 == 0) && (ldu % 4 == 0);
+}
 
 cudaError_t launch_compute_u(const void* A, int working, int64_t m, int n, int64_t lda,
                              const void* W, void* U, int64_t ldu, cudaStream_t s) {

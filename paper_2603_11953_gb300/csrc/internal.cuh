@@ -66,6 +66,16 @@ cudaError_t launch_jacobi(const double* M, int n, int64_t ldm, double tol, int m
                           double* scratch, double* lam_ws, double* V_ws, DevInfo* info,
                           cudaStream_t s);
 
+// Preconditioned one-sided Jacobi in FP64 (pivoted Cholesky, then one-sided
+// Jacobi on R^T over a thread-block cluster), n <= 64.  scratch: at least
+// n*n doubles + 256 ints.  Writes unsorted lambda and V like launch_jacobi.
+cudaError_t launch_eig_onesided(const double* M, int n, int64_t ldm, double tol, int max_sweeps,
+                                void* scratch, double* lam_ws, double* V_ws, DevInfo* info,
+                                cudaStream_t s);
+
+// Eigensolver variants (tsvd_opts.eig_variant).
+enum : int { EIG_DEFAULT = 0, EIG_TWO_SIDED = 1, EIG_ONE_SIDED = 2 };
+
 // Sort descending, sign rule, sigma = sqrt(lambda), round to working.
 // working: 0 FP32, 1 FP64.  Outputs (any may be null):
 //   sigma_w [n], V_w (ldv), W_w = RN(V_w / sigma_w) (ld n) in working type;
@@ -77,6 +87,11 @@ cudaError_t launch_finish(const double* lam_ws, const double* V_ws, int n, int w
 // ---------------------------------------------------------------- U (Alg. 1 l.6)
 cudaError_t launch_compute_u(const void* A, int working, int64_t m, int n, int64_t lda,
                              const void* W, void* U, int64_t ldu, cudaStream_t s);
+// Streaming FP32 U kernel (bulk-copy pipeline, packed FMA); requires
+// compute_u_v2_ok(): FP32, n <= 64, 16-byte aligned columns, m % 4 == 0.
+bool compute_u_v2_ok(const void* A, int working, int64_t m, int n, int64_t lda, const void* U, int64_t ldu);
+cudaError_t launch_compute_u_v2(const float* A, int64_t m, int n, int64_t lda, const float* W, float* U,
+                                int64_t ldu, int sm_count, DevInfo* info, cudaStream_t s);
 
 // flags -> tsvd_status in info->flags (overwritten by the status code).
 cudaError_t launch_finalize_info(DevInfo* info, cudaStream_t s);

@@ -179,6 +179,8 @@ __global__ void __launch_bounds__(256)
         sgn[tid] = V[best + (size_t)src * n] < 0.0 ? -1.0 : 1.0;
     }
     __syncthreads();
+    if (tid == 0 && n > 1 && sig[n - 1] < 1.1102230246251565e-16 * sig[0])
+        atomicOr(&info->flags, FLAG_NOT_FULL_RANK);  // sigma_n / sigma_1 below u_h
     for (int idx = tid; idx < n * n; idx += blockDim.x) {
         const int r = idx % n, k = idx / n;
         const int src = order[k];

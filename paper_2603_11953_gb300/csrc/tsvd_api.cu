@@ -123,6 +123,17 @@ double jacobi_tol(tsvd_ctx* h, int64_t n) {
 }
 int max_sweeps(tsvd_ctx* h) { return h->opts.max_sweeps > 0 ? h->opts.max_sweeps : 40; }
 
+// The eigen stage on M (n x n, ldm): unsorted lambda and V into lam / Vh.
+cudaError_t run_eig(tsvd_ctx* h, const double* M, int n, int64_t ldm, double* scratch, double* lam,
+                    double* Vh) {
+    const bool one_sided = h->opts.eig_variant == EIG_ONE_SIDED ||
+                           (h->opts.eig_variant == EIG_DEFAULT && n <= 64);
+    if (one_sided)
+        return launch_eig_onesided(M, n, ldm, jacobi_tol(h, n), max_sweeps(h), scratch, lam, Vh, h->dinfo,
+                                   h->stream);
+    return launch_jacobi(M, n, ldm, jacobi_tol(h, n), max_sweeps(h), scratch, lam, Vh, h->dinfo, h->stream);
+}
+
 void record(tsvd_ctx* h, int k) {
     if (h->opts.timing) cudaEventRecord(h->ev[k], h->stream);
 }
@@ -143,13 +154,17 @@ tsvd_status solve_one(tsvd_ctx* h, const void* A, int64_t m, int n, int64_t lda,
     tsvd_status st = run_gram(h, A, m, n, lda, working, G, nullptr, n, L.part);
     if (st != TSVD_OK) return st;
     if (timed) record(h, 1);
-    e = launch_jacobi(G, n, n, jacobi_tol(h, n), max_sweeps(h), scratch, lam, Vh, h->dinfo, h->stream);
+    e = run_eig(h, G, n, n, scratch, lam, Vh);
     if (e != cudaSuccess) return from_cuda(e);
     e = launch_finish(lam, Vh, n, working, sigma, V, ldv, W, nullptr, nullptr, 0, h->dinfo, h->stream);
     if (e != cudaSuccess) return from_cuda(e);
     if (timed) record(h, 2);
     if (U) {
-        e = launch_compute_u(A, working, m, n, lda, W, U, ldu, h->stream);
+        if (compute_u_v2_ok(A, working, m, n, lda, U, ldu))
+            e = launch_compute_u_v2(static_cast<const float*>(A), m, n, lda, static_cast<const float*>(W),
+                                    static_cast<float*>(U), ldu, h->sm_count, h->dinfo, h->stream);
+        else
+            e = launch_compute_u(A, working, m, n, lda, W, U, ldu, h->stream);
         if (e != cudaSuccess) return from_cuda(e);
     }
     if (timed) record(h, 3);
@@ -190,7 +205,7 @@ tsvd_status tsvd_create(tsvd_handle* out, int device, void* stream, const tsvd_o
         if (opts->slices != 0 && opts->slices != GRAM_DIGITS) return TSVD_ERR_UNSUPPORTED;
         if (opts->chunk_rows != 0 && opts->chunk_rows != GRAM_KC) return TSVD_ERR_UNSUPPORTED;
         if (opts->split_k < 0 || opts->max_sweeps < 0 || opts->jacobi_tol < 0.0) return TSVD_ERR_ARG;
-        if (opts->eig_variant != 0) return TSVD_ERR_UNSUPPORTED;
+        if (opts->eig_variant < 0 || opts->eig_variant > 2) return TSVD_ERR_UNSUPPORTED;
         if (opts->gram_variant != 0 && opts->gram_variant != 1) return TSVD_ERR_ARG;
     }
     int ndev = 0;
@@ -258,8 +273,7 @@ tsvd_status tsvd_eig(tsvd_handle h, const double* M, int64_t n, int64_t ldm, dou
     double* lam = reinterpret_cast<double*>(base(h) + L.lam);
     double* Vh = reinterpret_cast<double*>(base(h) + L.Vh);
     double* scratch = reinterpret_cast<double*>(base(h) + L.scratch);
-    e = launch_jacobi(M, (int)n, ldm, jacobi_tol(h, n), max_sweeps(h), scratch, lam, Vh, h->dinfo,
-                      h->stream);
+    e = run_eig(h, M, (int)n, ldm, scratch, lam, Vh);
     if (e == cudaSuccess)
         e = launch_finish(lam, Vh, (int)n, 1, nullptr, nullptr, 0, nullptr, lambda, V, ldv, h->dinfo,
                           h->stream);

@@ -98,19 +98,18 @@ def make_matrix(m: int, n: int, sigma: torch.Tensor, d: torch.Tensor, seed: int,
     lda = m if lda is None else lda
     gen = torch.Generator(device="cpu").manual_seed(seed)
     W = haar_orthogonal(n, gen)
-    if str(device).startswith("cuda"):
-        g_dev = torch.Generator(device=device).manual_seed(seed + 7919)
-        G = torch.randn(m, n, generator=g_dev, dtype=torch.float64, device=device)
-    else:
-        G = torch.randn(m, n, generator=gen, dtype=torch.float64)
+    # Built on the CPU (LAPACK QR) whatever the target device, so the same
+    # seed gives the same matrix everywhere; only the result is moved.
+    G = torch.randn(m, n, generator=gen, dtype=torch.float64)
     Q, _ = torch.linalg.qr(G)
     del G
-    B = Q * sigma.to(Q.device)
-    A64 = (B @ W.to(Q.device).T) * d.to(Q.device)
-    del Q, B
-    store = torch.zeros(n, lda, dtype=dtype, device=device)
+    A64 = (Q * sigma) @ W.T
+    del Q
+    A64 *= d
+    store = torch.zeros(n, lda, dtype=dtype)
     store[:, :m] = A64.T.to(dtype)
-    return store.T  # shape (lda, n), column-major storage
+    del A64
+    return store.to(device).T  # shape (lda, n), column-major storage
 
 
 def make_config(spec: Spec, device="cpu", m: int | None = None, seed_offset: int = 0):

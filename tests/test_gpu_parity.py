@@ -153,9 +153,10 @@ def test_gram_powers_of_two_and_stacking_are_exact():
 
 
 # ------------------------------------------------------------------ Jacobi (a4-a6)
+@pytest.mark.parametrize("variant", [1, 2])
 @pytest.mark.parametrize("n,kappa,logd", [(1, 1.0, 0.0), (2, 10.0, 1.0), (7, 1e2, 2.0), (16, 1e3, 3.0),
                                           (33, 1e3, 3.0), (64, 1e4, 4.0)])
-def test_eig_matches_oracle_jacobi(n, kappa, logd):
+def test_eig_matches_oracle_jacobi(n, kappa, logd, variant):
     m = max(4 * n, 200)
     A, _ = workloads.small_case(m, n, kappa_sigma=kappa, logd=logd, seed=11 * n)
     S_hi, _, _ = oracle.gram(workloads.to_numpy_colmajor(A, m))
@@ -166,7 +167,7 @@ def test_eig_matches_oracle_jacobi(n, kappa, logd):
     lam = torch.zeros(n, dtype=torch.float64, device="cuda")
     V = colmajor(n, n, torch.float64)
     info_d = torch.zeros(6, dtype=torch.int32, device="cuda")
-    h = handle()
+    h = handle(eig_variant=variant)
     T.tsvd_eig(h, M, n, n, lam, V, n, info_d)
     torch.cuda.synchronize()
     T.tsvd_destroy(h)
@@ -184,11 +185,16 @@ def test_eig_matches_oracle_jacobi(n, kappa, logd):
 
 
 # ------------------------------------------------------------------ solve (a1-a7)
+@pytest.mark.parametrize("variant", [0, 1])
 @pytest.mark.parametrize("m,n,kappa,logd", [(20000, 16, 1e3, 3.0), (5000, 1, 1.0, 0.0), (16, 16, 1e2, 1.0),
-                                            (12345, 33, 1e3, 3.0), (65537, 64, 1e3, 3.0)])
-def test_solve_matches_oracle(m, n, kappa, logd):
+                                            (12345, 33, 1e3, 3.0), (65537, 64, 1e3, 3.0),
+                                            (40964, 64, 1e3, 3.0)])
+def test_solve_matches_oracle(m, n, kappa, logd, variant):
     A, _ = workloads.small_case(m, n, kappa_sigma=kappa, logd=logd, seed=5 * m + n, device="cuda")
-    sig, V, U, st, sweeps = gpu_solve(A, m, n, m)
+    h = handle(eig_variant=variant) if variant else None
+    sig, V, U, st, sweeps = gpu_solve(A, m, n, m, h=h)
+    if h is not None:
+        T.tsvd_destroy(h)
     assert st == T.TSVD_OK
     A_np = workloads.to_numpy_colmajor(A, m)
     ref = oracle.svd(A_np, higher=1)
