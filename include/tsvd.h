@@ -76,7 +76,9 @@ typedef struct {
                               + one-sided Jacobi on R^T, both in FP64 (n <= 64) */
     int autotune;          /* reserved (0) */
     long long timeout_cycles; /* reserved: limit for device spin-waits (0 = default) */
-    int gram_variant;      /* 0 = Ozaki-BF16 tensor-core Gram, 1 = plain FP64 Gram */
+    int gram_variant;      /* 0 = Ozaki-BF16 Gram on tcgen05/TMEM (mma.sync when the
+                              input cannot be TMA-loaded), 1 = plain FP64 Gram,
+                              2 = Ozaki-BF16 Gram on mma.sync (comparison) */
     int timing;            /* 1 = record per-stage CUDA events (tsvd_last_stage_ms) */
 } tsvd_opts;
 

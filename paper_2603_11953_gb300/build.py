@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libtsvd.so")
-SOURCES = ["tsvd_api.cu", "gram_ozaki.cu", "jacobi.cu", "compute_u.cu", "gram_static.cu", "eig_onesided.cu"]
+SOURCES = ["tsvd_api.cu", "gram_ozaki.cu", "jacobi.cu", "compute_u.cu", "gram_static.cu", "eig_onesided.cu", "tma_util.cu", "gram_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ARCH + ["-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
@@ -36,8 +36,7 @@ def _compile(src: str, extra: list[str]) -> str:
 def build(force: bool = False, extra: list[str] | None = None) -> str:
     os.makedirs(OUT, exist_ok=True)
     extra = extra or []
-    srcs = [os.path.join(CSRC, s) for s in SOURCES] + [os.path.join(CSRC, "internal.cuh"),
-                                                       os.path.join(HERE, "..", "include", "tsvd.h")]
+    srcs = [os.path.join(CSRC, s) for s in os.listdir(CSRC)] + [os.path.join(HERE, "..", "include", "tsvd.h")]
     if not force and os.path.exists(LIB):
         newest = max(os.path.getmtime(s) for s in srcs)
         if os.path.getmtime(LIB) >= newest:

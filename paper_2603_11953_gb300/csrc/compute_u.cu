@@ -6,6 +6,7 @@
 // working precision (FP32 FMA for FP32 working).  A is read once per
 // 64-column block of U (once in total for n <= 64), U is written once.
 #include "internal.cuh"
+#include "tma_util.cuh"
 
 namespace tsvd {
 namespace {
@@ -106,52 +107,17 @@ cudaError_t launch_u_t(const T* A, int64_t m, int n, int64_t lda, const T* W, T*
 }
 
 // ---------------------------------------------------------------- v2: FP32, n <= 64
-// Persistent CTAs stream 128-row tiles of A through a 2-stage shared-memory
-// ring filled by cp.async.bulk (one contiguous copy per column) and signalled
-// by an mbarrier.  Each of the 128 threads owns an 8-row x 8-column block of
-// the U tile and accumulates with packed FP32 FMAs (fma.rn.f32x2): row pairs
-// of A times a duplicated W entry, W being stored pre-duplicated ({w, w}) in
-// shared memory so that no operand shuffles are needed.
+// Persistent CTAs (one per SM, 8 warps) stream 128-row x n tiles of A through
+// a 3-stage shared-memory ring, one 2-D TMA load per tile (rows past m are
+// zero-filled by the TMA unit), so two tiles are in flight while the third
+// is consumed.  Each thread owns an 8-row x 4-column block of the U tile and
+// accumulates with packed FP32 FMAs (fma.rn.f32x2): row pairs of A times a
+// duplicated W entry, W being stored pre-duplicated ({w, w}) in shared
+// memory so that no operand shuffles are needed.
 constexpr int U2_ROWS = 128;
-constexpr int U2_THREADS = 128;
-constexpr int U2_STAGES = 2;
-constexpr long long U2_WAIT_LIMIT = 1ll << 26;  // bounded mbarrier polls
+constexpr int U2_THREADS = 256;
+constexpr int U2_STAGES = 3;
 
-__device__ __forceinline__ uint32_t u2_smem(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void u2_mbar_init(uint64_t* bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(u2_smem(bar)), "r"(count));
-}
-__device__ __forceinline__ void u2_mbar_expect_tx(uint64_t* bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(u2_smem(bar)), "r"(bytes)
-                 : "memory");
-}
-// Wait for phase `parity` of the barrier; false if the poll limit ran out.
-__device__ __forceinline__ bool u2_mbar_wait(uint64_t* bar, unsigned parity) {
-    for (long long it = 0; it < U2_WAIT_LIMIT; ++it) {
-        uint32_t ok;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(ok)
-            : "r"(u2_smem(bar)), "r"(parity)
-            : "memory");
-        if (ok) return true;
-    }
-    return false;
-}
-__device__ __forceinline__ void u2_bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            u2_smem(dst)),
-        "l"(src), "r"(bytes), "r"(u2_smem(bar))
-        : "memory");
-}
-__device__ __forceinline__ unsigned long long f2pack(float lo, float hi) {
-    unsigned long long r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-    return r;
-}
 __device__ __forceinline__ void f2unpack(unsigned long long v, float& lo, float& hi) {
     asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
 }
@@ -162,74 +128,82 @@ __device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsign
     return d;
 }
 
-__global__ void __launch_bounds__(U2_THREADS)
-    compute_u_v2_kernel(const float* __restrict__ A, int64_t m, int n, int64_t lda, const float* __restrict__ W,
-                        float* __restrict__ U, int64_t ldu, int64_t ntiles, DevInfo* info) {
+__global__ void __launch_bounds__(U2_THREADS, 1)
+    compute_u_v2_kernel(const __grid_constant__ CUtensorMap tmapA, int64_t m, int n,
+                        const float* __restrict__ W, float* __restrict__ U, int64_t ldu, int64_t ntiles,
+                        DevInfo* info) {
     extern __shared__ __align__(128) unsigned char u2smem[];
-    float* Ast = reinterpret_cast<float*>(u2smem);                         // [STAGES][64][128]
-    float* Wd = Ast + (size_t)U2_STAGES * 64 * U2_ROWS;                       // [64][128] = {w,w} pairs
+    float* Ast = reinterpret_cast<float*>(u2smem);     // [STAGES][n][128] (TMA box, rows fastest)
+    float* Wd = Ast + (size_t)U2_STAGES * 64 * U2_ROWS;  // [64][128] = {w,w} pairs
     __shared__ __align__(8) uint64_t full[U2_STAGES];
     __shared__ int s_abort;
     const int tid = threadIdx.x;
     const int tr = tid & 15;   // rows 8 tr .. 8 tr + 7 of the tile
-    const int tc = tid >> 4;   // columns 8 tc .. 8 tc + 7
+    const int tc = tid >> 4;   // columns 4 tc .. 4 tc + 3
+    const unsigned tile_bytes = (unsigned)(U2_ROWS * n * sizeof(float));
+    if (tid == 0) {
+        tma_prefetch_desc(&tmapA);
+        for (int s = 0; s < U2_STAGES; ++s) mbar_init(&full[s], 1);
+        mbar_fence_init();
+        s_abort = 0;
+    }
     for (int idx = tid; idx < 64 * 64; idx += U2_THREADS) {
         const int c = idx >> 6, j = idx & 63;
         const float w = (c < n && j < n) ? W[c + (size_t)j * n] : 0.f;
         Wd[c * 128 + 2 * j] = w;
         Wd[c * 128 + 2 * j + 1] = w;
     }
-    if (tid == 0) {
-        for (int s = 0; s < U2_STAGES; ++s) u2_mbar_init(&full[s], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        s_abort = 0;
-    }
     __syncthreads();
-    // a tile is bulk-loadable when every column segment is a whole number of 16-byte units
-    auto issue = [&](int64_t tile, int stage) {
-        const int64_t r0 = tile * U2_ROWS;
-        const int rows = (int)((m - r0) < U2_ROWS ? (m - r0) : U2_ROWS);
-        const unsigned bytes = (unsigned)rows * 4u;
-        u2_mbar_expect_tx(&full[stage], bytes * (unsigned)n);
-        for (int c = 0; c < n; ++c)
-            u2_bulk_g2s(Ast + ((size_t)stage * 64 + c) * U2_ROWS, A + (size_t)c * lda + r0, bytes, &full[stage]);
-    };
-    int64_t tile = blockIdx.x;
-    if (tid == 0 && tile < ntiles) issue(tile, 0);
+    const int64_t first = blockIdx.x;
+    if (tid == 0) {
+        for (int k = 0; k < U2_STAGES - 1; ++k) {
+            const int64_t t = first + (int64_t)k * gridDim.x;
+            if (t < ntiles) {
+                mbar_expect_tx(&full[k], tile_bytes);
+                tma_load_2d(Ast + (size_t)k * 64 * U2_ROWS, &tmapA, (int)(t * U2_ROWS), 0, &full[k]);
+            }
+        }
+    }
     unsigned phase_bits = 0u;  // bit s: parity to wait for on full[s]
-    for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
-        const int stage = it & 1;
-        const int64_t next = tile + gridDim.x;
-        if (tid == 0 && next < ntiles) issue(next, stage ^ 1);
-        if (!u2_mbar_wait(&full[stage], (phase_bits >> stage) & 1u)) {
+    int stage = 0;
+    for (int64_t tile = first; tile < ntiles; tile += gridDim.x) {
+        const int64_t ahead = tile + (int64_t)(U2_STAGES - 1) * gridDim.x;
+        const int astage = (stage + U2_STAGES - 1) % U2_STAGES;
+        if (tid == 0 && ahead < ntiles) {
+            mbar_expect_tx(&full[astage], tile_bytes);
+            tma_load_2d(Ast + (size_t)astage * 64 * U2_ROWS, &tmapA, (int)(ahead * U2_ROWS), 0, &full[astage]);
+        }
+        if (!mbar_wait(&full[stage], (phase_bits >> stage) & 1u)) {
             atomicOr(&info->flags, FLAG_TIMEOUT);
             atomicExch(&s_abort, 1);
         }
         phase_bits ^= 1u << stage;
         __syncthreads();
         if (s_abort) break;
-        const float* At = Ast + (size_t)stage * 64 * U2_ROWS;
-        unsigned long long acc[4][8];  // [row pair][column]
+        const float* At = Ast + (size_t)stage * 64 * U2_ROWS + 8 * tr;
+        const float* Wt = Wd + 8 * tc;
+        unsigned long long acc[4][4];  // [row pair][column]
 #pragma unroll
         for (int rp = 0; rp < 4; ++rp)
 #pragma unroll
-            for (int k = 0; k < 8; ++k) acc[rp][k] = 0ull;
+            for (int k = 0; k < 4; ++k) acc[rp][k] = 0ull;
+#pragma unroll 4
         for (int c = 0; c < n; ++c) {
-            const ulonglong2 a01 = *reinterpret_cast<const ulonglong2*>(At + c * U2_ROWS + 8 * tr);
-            const ulonglong2 a23 = *reinterpret_cast<const ulonglong2*>(At + c * U2_ROWS + 8 * tr + 4);
+            const ulonglong2 a01 = *reinterpret_cast<const ulonglong2*>(At + c * U2_ROWS);
+            const ulonglong2 a23 = *reinterpret_cast<const ulonglong2*>(At + c * U2_ROWS + 4);
+            const ulonglong2 w01 = *reinterpret_cast<const ulonglong2*>(Wt + c * 128);
+            const ulonglong2 w23 = *reinterpret_cast<const ulonglong2*>(Wt + c * 128 + 4);
             const unsigned long long ap[4] = {a01.x, a01.y, a23.x, a23.y};
-            const ulonglong2* wv = reinterpret_cast<const ulonglong2*>(Wd + c * 128 + 16 * tc);
-            const ulonglong2 w01 = wv[0], w23 = wv[1], w45 = wv[2], w67 = wv[3];
-            const unsigned long long wp[8] = {w01.x, w01.y, w23.x, w23.y, w45.x, w45.y, w67.x, w67.y};
+            const unsigned long long wp[4] = {w01.x, w01.y, w23.x, w23.y};
 #pragma unroll
             for (int rp = 0; rp < 4; ++rp)
 #pragma unroll
-                for (int k = 0; k < 8; ++k) acc[rp][k] = ffma2(ap[rp], wp[k], acc[rp][k]);
+                for (int k = 0; k < 4; ++k) acc[rp][k] = ffma2(ap[rp], wp[k], acc[rp][k]);
         }
         const int64_t r0 = tile * U2_ROWS + 8 * tr;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int j = 8 * tc + k;
+        for (int k = 0; k < 4; ++k) {
+            const int j = 4 * tc + k;
             if (j >= n) continue;
             float v[8];
 #pragma unroll
@@ -244,11 +218,12 @@ __global__ void __launch_bounds__(U2_THREADS)
                     if (r0 + r < m) dst[r] = v[r];
             }
         }
+        stage = (stage + 1) % U2_STAGES;
         __syncthreads();  // every thread is done with this stage before it is refilled
     }
     if (s_abort && tid == 0) {
-        // leave no bulk copy in flight: wait (bounded) for the other stage too
-        for (int s = 0; s < U2_STAGES; ++s) (void)u2_mbar_wait(&full[s], (phase_bits >> s) & 1u);
+        // leave no TMA load in flight: wait (bounded) on every stage's pending phase
+        for (int s = 0; s < U2_STAGES; ++s) (void)mbar_wait(&full[s], (phase_bits >> s) & 1u);
     }
 }
 
@@ -258,20 +233,23 @@ size_t compute_u_v2_smem() { return sizeof(float) * ((size_t)U2_STAGES * 64 * U2
 
 cudaError_t launch_compute_u_v2(const float* A, int64_t m, int n, int64_t lda, const float* W, float* U,
                                 int64_t ldu, int sm_count, DevInfo* info, cudaStream_t s) {
+    CUtensorMap tmap;
+    cudaError_t e = make_tmap_2d(&tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, sizeof(float), A, (uint64_t)m,
+                                 (uint64_t)n, (uint64_t)lda, U2_ROWS, (uint32_t)n, CU_TENSOR_MAP_SWIZZLE_NONE);
+    if (e != cudaSuccess) return e;
     const size_t smem = compute_u_v2_smem();
-    cudaError_t e = cudaFuncSetAttribute(compute_u_v2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    e = cudaFuncSetAttribute(compute_u_v2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t ntiles = (m + U2_ROWS - 1) / U2_ROWS;
-    int64_t grid = (int64_t)sm_count * 2;
+    int64_t grid = (int64_t)sm_count;
     if (grid > ntiles) grid = ntiles;
-    compute_u_v2_kernel<<<(unsigned)grid, U2_THREADS, smem, s>>>(A, m, n, lda, W, U, ldu, ntiles, info);
+    compute_u_v2_kernel<<<(unsigned)grid, U2_THREADS, smem, s>>>(tmap, m, n, W, U, ldu, ntiles, info);
     return cudaGetLastError();
 }
 
 bool compute_u_v2_ok(const void* A, int working, int64_t m, int n, int64_t lda, const void* U, int64_t ldu) {
-    // every column segment of every tile must be a whole number of 16-byte units
-    return working == 0 && n <= 64 && ((uintptr_t)A % 16 == 0) && (lda % 4 == 0) && (m % 4 == 0) &&
+    // TMA: 16-byte aligned base and column stride; 128-bit stores of U
+    return working == 0 && n <= 64 && m >= 1 && ((uintptr_t)A % 16 == 0) && (lda % 4 == 0) &&
            ((uintptr_t)U % 16 == 0) && (ldu % 4 == 0);
 }
 

@@ -20,10 +20,18 @@
 //      pair); after each step one column moves to each neighbouring CTA
 //      through distributed shared memory, followed by one cluster barrier.
 //
-// Squared norms are kept incrementally within a sweep (||x_p'||^2 =
-// ||x_p||^2 - t g) and recomputed exactly at the start of every sweep and
-// whenever a norm drops below 1/16 of its previous value; the stopping test
-// of the final, rotation-free sweep therefore uses exact norms.
+// The rotation angle is estimated in FP32 while the applied rotation is kept
+// orthogonal to FP64 precision (c = rsqrt(1 + t^2) in FP64): an inexact angle
+// only leaves a residual g * O(2^-24) on a pair, which later sweeps remove,
+// whereas a non-orthogonal rotation would change the singular values.  On
+// GB300 every FP64 warp instruction occupies the thin FP64 pipe for tens of
+// cycles, so the divisions and square roots of the angle go to the FP32
+// units.  Squared norms are updated within a sweep by the exact quadratic
+// form of the rotation, recomputed at the start of every sweep and whenever
+// a norm drops below 1/16 of its previous value; the stopping test of the
+// final, rotation-free sweep therefore uses exact norms.
+#include <climits>
+
 #include <cooperative_groups.h>
 
 #include "internal.cuh"
@@ -53,18 +61,21 @@ __global__ void __launch_bounds__(256)
     bool deficient = false;
     for (int k = 0; k < n; ++k) {
         if (tid < 32) {  // pivot: largest remaining diagonal (lowest index on ties)
-            double best = -1.0;
+            // the bit patterns of non-negative doubles order like the values, and
+            // every negative value (rank deficiency) sorts below them as a signed int
+            long long best = LLONG_MIN;
             int bi = k;
             for (int i = k + tid; i < n; i += 32) {
-                const double d = sa[i + (size_t)i * n];
-                if (d > best) { best = d; bi = i; }
+                const long long d = __double_as_longlong(sa[i + (size_t)i * n]);
+                const long long key = d < 0 ? LLONG_MIN + 1 : d;
+                if (key > best) { best = key; bi = i; }
             }
             for (int o = 16; o > 0; o >>= 1) {
-                const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const long long ob = __shfl_xor_sync(0xffffffffu, best, o);
                 const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
                 if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
             }
-            if (tid == 0) { s_piv = bi; s_d = best; }
+            if (tid == 0) { s_piv = bi; s_d = sa[bi + (size_t)bi * n]; }
         }
         __syncthreads();
         const int p = s_piv;
@@ -94,9 +105,10 @@ __global__ void __launch_bounds__(256)
             if (tid == 0) { const int t = perm[k]; perm[k] = perm[p]; perm[p] = t; }
             __syncthreads();
         }
-        const double rkk = sqrt(d);
+        const double rinv = rsqrt(d);  // 1 / r_kk
         // R[k][j] = A[k][j] / r_kk for j >= k, stored as X[j][k]
-        for (int j = k + tid; j < n; j += nt) X[j + (size_t)k * n] = (j == k) ? rkk : sa[k + (size_t)j * n] / rkk;
+        for (int j = k + tid; j < n; j += nt)
+            X[j + (size_t)k * n] = (j == k) ? d * rinv : sa[k + (size_t)j * n] * rinv;
         __syncthreads();
         // trailing update A[i][j] -= R[k][i] R[k][j], i, j > k
         const int rem = n - k - 1;
@@ -144,8 +156,6 @@ __global__ void __launch_bounds__(512) onesided_jacobi_kernel(OsParams prm) {
     __shared__ unsigned long long s_off;     // bits of a non-negative double
     __shared__ int s_cnt[2];                 // used in CTA 0: per-sweep cluster totals
     __shared__ int s_total;
-    __shared__ double s_g[32], s_c[32], s_s[32], s_t[32];
-    __shared__ int s_r[32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int N = np - 1;
     const double tol2 = prm.tol * prm.tol;
@@ -183,72 +193,60 @@ __global__ void __launch_bounds__(512) onesided_jacobi_kernel(OsParams prm) {
         }
         __syncthreads();
         for (int k = 0; k < N; ++k) {
-            // (a) one warp per pair: g = x_p^T x_q
+            // one warp per pair: g = x_p^T x_q, the rotation, and its application
             if (warp < P) {
-                const double* xp = bufs + (size_t)top_buf[warp] * LD;
-                const double* xq = bufs + (size_t)bot_buf[warp] * LD;
+                double* xp = bufs + (size_t)top_buf[warp] * LD;
+                double* xq = bufs + (size_t)bot_buf[warp] * LD;
                 double g = 0.0;
                 for (int r = lane; r < n; r += 32) g += xp[r] * xq[r];
                 g = warp_sum(g);
-                if (lane == 0) s_g[warp] = g;
-            }
-            __syncthreads();
-            // (b) rotation parameters of all pairs, one lane per pair
-            if (warp == 0 && lane < P) {
-                double* xp = bufs + (size_t)top_buf[lane] * LD;
-                double* xq = bufs + (size_t)bot_buf[lane] * LD;
-                const double g = s_g[lane], app = xp[n + 1], aqq = xq[n + 1];
-                int rot = 0;
-                double cs = 1.0, sn = 0.0, t = 0.0;
-                if ((int)xp[n] < n && (int)xq[n] < n && app > 0.0 && aqq > 0.0) {
-                    const double g2 = g * g, pq = app * aqq;
-                    // largest g^2 / (a_pp a_qq) of the sweep (divide only for a new maximum)
-                    if (g2 > __longlong_as_double((long long)s_off) * pq)
-                        atomicMax(&s_off, (unsigned long long)__double_as_longlong(g2 / pq));
-                    if (g != 0.0 && g2 > tol2 * pq) {
-                        // Rutishauser: t = sgn(zeta) / (|zeta| + sqrt(1 + zeta^2)),
-                        // zeta = d / h with d = a_qq - a_pp, h = 2g; written without zeta.
-                        const double d = aqq - app, h = 2.0 * g;
-                        if (d == 0.0) {
-                            t = 1.0;
-                        } else {
-                            const double r = sqrt(d * d + h * h);
-                            t = (d > 0.0 ? h : -h) / (fabs(d) + r);
-                        }
-                        cs = rsqrt(1.0 + t * t);
-                        sn = t * cs;
-                        rot = 1;
+                const double app = xp[n + 1], aqq = xq[n + 1];
+                const bool live = (int)xp[n] < n && (int)xq[n] < n && app > 0.0 && aqq > 0.0;
+                const double g2 = g * g, pq = app * aqq;
+                if (live && lane == 0 && g2 > __longlong_as_double((long long)s_off) * pq)
+                    atomicMax(&s_off, (unsigned long long)__double_as_longlong(g2 / pq));
+                if (live && g != 0.0 && g2 > tol2 * pq) {
+                    // Rotation angle from Rutishauser's t = sgn(zeta)/(|zeta| + sqrt(1 + zeta^2)),
+                    // zeta = (a_qq - a_pp) / 2g, evaluated in FP32 (its accuracy only sets how
+                    // far g is reduced); the rotation itself is made orthogonal to FP64
+                    // precision by c = rsqrt(1 + t^2), s = t c computed in FP64.
+                    const float df = (float)(aqq - app), hf = 2.0f * (float)g;
+                    float tf;
+                    if (df == 0.0f) {
+                        tf = 1.0f;
+                    } else {
+                        const float rf = sqrtf(df * df + hf * hf);
+                        tf = (df > 0.0f ? hf : -hf) / (fabsf(df) + rf);
+                    }
+                    const double t = (double)tf;
+                    const double cs = rsqrt(1.0 + t * t);
+                    const double sn = t * cs;
+                    for (int r = lane; r < n; r += 32) {
+                        const double a = xp[r], b = xq[r];
+                        xp[r] = cs * a - sn * b;
+                        xq[r] = sn * a + cs * b;
+                    }
+                    // ||x_p'||^2 = c^2 a_pp - 2cs g + s^2 a_qq (exact for any angle)
+                    double np2 = cs * cs * app - 2.0 * cs * sn * g + sn * sn * aqq;
+                    double nq2 = sn * sn * app + 2.0 * cs * sn * g + cs * cs * aqq;
+                    __syncwarp();
+                    if (np2 < 0.0625 * app) {
+                        double s2 = 0.0;
+                        for (int r = lane; r < n; r += 32) s2 += xp[r] * xp[r];
+                        np2 = warp_sum(s2);
+                    }
+                    if (nq2 < 0.0625 * aqq) {
+                        double s2 = 0.0;
+                        for (int r = lane; r < n; r += 32) s2 += xq[r] * xq[r];
+                        nq2 = warp_sum(s2);
+                    }
+                    __syncwarp();
+                    if (lane == 0) {
+                        xp[n + 1] = np2;
+                        xq[n + 1] = nq2;
+                        atomicAdd(&s_rot, 1);
                     }
                 }
-                s_c[lane] = cs; s_s[lane] = sn; s_t[lane] = t; s_r[lane] = rot;
-                if (rot) atomicAdd(&s_rot, 1);
-            }
-            __syncthreads();
-            // (c) apply: x_p <- c x_p - s x_q, x_q <- s x_p + c x_q; norms
-            if (warp < P && s_r[warp]) {
-                double* xp = bufs + (size_t)top_buf[warp] * LD;
-                double* xq = bufs + (size_t)bot_buf[warp] * LD;
-                const double cs = s_c[warp], sn = s_s[warp], t = s_t[warp], g = s_g[warp];
-                const double app = xp[n + 1], aqq = xq[n + 1];
-                for (int r = lane; r < n; r += 32) {
-                    const double a = xp[r], b = xq[r];
-                    xp[r] = cs * a - sn * b;
-                    xq[r] = sn * a + cs * b;
-                }
-                double np2 = app - t * g, nq2 = aqq + t * g;
-                __syncwarp();
-                if (np2 < 0.0625 * app) {
-                    double s2 = 0.0;
-                    for (int r = lane; r < n; r += 32) s2 += xp[r] * xp[r];
-                    np2 = warp_sum(s2);
-                }
-                if (nq2 < 0.0625 * aqq) {
-                    double s2 = 0.0;
-                    for (int r = lane; r < n; r += 32) s2 += xq[r] * xq[r];
-                    nq2 = warp_sum(s2);
-                }
-                __syncwarp();
-                if (lane == 0) { xp[n + 1] = np2; xq[n + 1] = nq2; }
             }
             __syncthreads();
             // circle tournament move: slot j -> j+1 (1 <= j <= np-2), slot np-1 -> 1, slot 0 fixed

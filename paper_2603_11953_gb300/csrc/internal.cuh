@@ -47,6 +47,13 @@ size_t gram_partials_bytes(const GramPlan& p);
 // part: workspace of gram_partials_bytes(plan) bytes.
 cudaError_t launch_gram_ozaki(const void* A, int working, int64_t m, int n, int64_t lda,
                               const GramPlan& plan, void* part, DevInfo* info, cudaStream_t s);
+// tcgen05 / TMEM / TMA version of the same Gram (FP32, n <= 64, 16-byte
+// aligned columns).  Writes partials in the layout of launch_gram_ozaki with
+// NP = 64; plan from gram_tc_plan.
+bool gram_tc_ok(const void* A, int working, int n, int64_t lda);
+GramPlan gram_tc_plan(int64_t m, int n, int sm_count, int split_k_opt);
+cudaError_t launch_gram_tc(const void* A, int64_t m, int n, int64_t lda, const GramPlan& plan, void* part,
+                           DevInfo* info, cudaStream_t s);
 // Combine the partials into G (n x n FP64, both triangles) and optionally the
 // double-double low parts G_lo (may be null).
 cudaError_t launch_gram_combine(const GramPlan& plan, const void* part, int n, double* G,

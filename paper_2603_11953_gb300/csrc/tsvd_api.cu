@@ -91,6 +91,12 @@ bool valid_prec_pair(tsvd_prec working, tsvd_prec higher) {
     return (working == TSVD_FP32 || working == TSVD_FP64) && (higher == TSVD_FP64 || higher == TSVD_DD);
 }
 
+// tcgen05 Gram (default) when the input allows TMA; gram_variant 2 forces the
+// mma.sync version of the same Ozaki arithmetic.
+bool use_tc(tsvd_ctx* h, const void* A, int working, int n, int64_t lda) {
+    return h->opts.gram_variant == 0 && gram_tc_ok(A, working, n, lda);
+}
+
 // Gram into G (and G_lo) for one matrix.  Caller validated the arguments.
 tsvd_status run_gram(tsvd_ctx* h, const void* A, int64_t m, int n, int64_t lda, int working,
                      double* G, double* G_lo, int64_t ldg, size_t part_off) {
@@ -101,20 +107,24 @@ tsvd_status run_gram(tsvd_ctx* h, const void* A, int64_t m, int n, int64_t lda, 
         if (e == cudaSuccess && G_lo) e = cudaMemsetAsync(G_lo, 0, sizeof(double) * ldg * n, h->stream);
         return from_cuda(e);
     }
-    const GramPlan plan = gram_plan(m, n, h->sm_count, h->opts.split_k);
-    e = launch_gram_ozaki(A, working, m, n, lda, plan, base(h) + part_off, h->dinfo, h->stream);
+    const bool tc = use_tc(h, A, working, n, lda);
+    const GramPlan plan = tc ? gram_tc_plan(m, n, h->sm_count, h->opts.split_k)
+                             : gram_plan(m, n, h->sm_count, h->opts.split_k);
+    e = tc ? launch_gram_tc(A, m, n, lda, plan, base(h) + part_off, h->dinfo, h->stream)
+           : launch_gram_ozaki(A, working, m, n, lda, plan, base(h) + part_off, h->dinfo, h->stream);
     if (e != cudaSuccess) return from_cuda(e);
     return from_cuda(launch_gram_combine(plan, base(h) + part_off, n, G, G_lo, ldg, h->stream));
 }
 
-size_t part_bytes_for(tsvd_ctx* h, int64_t m, int n) {
+size_t part_bytes_for(tsvd_ctx* h, const void* A, int working, int64_t m, int n, int64_t lda) {
     if (h->opts.gram_variant == 1) return gram_plain_partials_bytes(m, n, h->sm_count);
+    if (use_tc(h, A, working, n, lda)) return gram_partials_bytes(gram_tc_plan(m, n, h->sm_count, h->opts.split_k));
     return gram_partials_bytes(gram_plan(m, n, h->sm_count, h->opts.split_k));
 }
 
 bool gram_supported(tsvd_ctx* h, int working, int64_t n) {
     if (n > 64) return false;                      // tensor-core Gram built for n <= 64
-    if (h->opts.gram_variant == 0 && working != TSVD_FP32) return false;
+    if (h->opts.gram_variant != 1 && working != TSVD_FP32) return false;
     return true;
 }
 
@@ -142,7 +152,7 @@ void record(tsvd_ctx* h, int k) {
 tsvd_status solve_one(tsvd_ctx* h, const void* A, int64_t m, int n, int64_t lda, int working,
                       void* sigma, void* V, int64_t ldv, void* U, int64_t ldu, tsvd_info* info,
                       bool timed) {
-    const Layout L = layout_for(n, part_bytes_for(h, m, n), working);
+    const Layout L = layout_for(n, part_bytes_for(h, A, working, m, n, lda), working);
     cudaError_t e = cudaMemsetAsync(h->dinfo, 0, sizeof(DevInfo), h->stream);
     if (e != cudaSuccess) return from_cuda(e);
     double* G = reinterpret_cast<double*>(base(h) + L.G);
@@ -206,7 +216,7 @@ tsvd_status tsvd_create(tsvd_handle* out, int device, void* stream, const tsvd_o
         if (opts->chunk_rows != 0 && opts->chunk_rows != GRAM_KC) return TSVD_ERR_UNSUPPORTED;
         if (opts->split_k < 0 || opts->max_sweeps < 0 || opts->jacobi_tol < 0.0) return TSVD_ERR_ARG;
         if (opts->eig_variant < 0 || opts->eig_variant > 2) return TSVD_ERR_UNSUPPORTED;
-        if (opts->gram_variant != 0 && opts->gram_variant != 1) return TSVD_ERR_ARG;
+        if (opts->gram_variant < 0 || opts->gram_variant > 2) return TSVD_ERR_ARG;
     }
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
@@ -249,7 +259,7 @@ tsvd_status tsvd_gram(tsvd_handle h, const void* A, int64_t m, int64_t n, int64_
     if (!gram_supported(h, working, n)) return TSVD_ERR_UNSUPPORTED;
     if (higher == TSVD_DD && h->opts.gram_variant == 1) return TSVD_ERR_UNSUPPORTED;
     DeviceGuard g(h->device);
-    const size_t pb = part_bytes_for(h, m, (int)n);
+    const size_t pb = part_bytes_for(h, A, working, m, (int)n, lda);
     tsvd_status st = ensure_ws(h, align_up(pb));
     if (st != TSVD_OK) return st;
     cudaError_t e = cudaMemsetAsync(h->dinfo, 0, sizeof(DevInfo), h->stream);
@@ -292,7 +302,7 @@ tsvd_status tsvd_solve(tsvd_handle h, const void* A, int64_t m, int64_t n, int64
     if (!(working == TSVD_FP32 && higher == TSVD_FP64)) return TSVD_ERR_UNSUPPORTED;
     if (!gram_supported(h, working, n)) return TSVD_ERR_UNSUPPORTED;
     DeviceGuard g(h->device);
-    const Layout L = layout_for(n, part_bytes_for(h, m, (int)n), working);
+    const Layout L = layout_for(n, part_bytes_for(h, A, working, m, (int)n, lda), working);
     tsvd_status st = ensure_ws(h, L.total);
     if (st != TSVD_OK) return st;
     h->have_times = false;
@@ -315,7 +325,7 @@ tsvd_status tsvd_batch_solve(tsvd_handle h, int32_t count, const void* const* A,
             (want_u && (!ldu || ldu[i] < m[i])))
             return TSVD_ERR_ARG;
         if (n[i] > 64) return TSVD_ERR_UNSUPPORTED;
-        need = std::max(need, layout_for(n[i], part_bytes_for(h, m[i], (int)n[i]), working).total);
+        need = std::max(need, layout_for(n[i], part_bytes_for(h, A[i], working, m[i], (int)n[i], lda[i]), working).total);
     }
     DeviceGuard g(h->device);
     tsvd_status st = ensure_ws(h, need);

@@ -142,11 +142,11 @@ def test_gram_powers_of_two_and_stacking_are_exact():
     AA = torch.cat([A[:m], A[:m]], 0).contiguous()
     AA = AA.T.contiguous().T  # column-major
     G2, _, _ = gpu_gram(AA, 2 * m, n, 2 * m, h=h)
-    T.tsvd_destroy(h)
     assert np.array_equal(G2, 2 * G)
     As = A.clone()
     As[:, 3] *= 2.0 ** 20
-    Gs, _, _ = gpu_gram(As, m, n, m)
+    Gs, _, _ = gpu_gram(As, m, n, m, h=h)  # same split, so the same per-CTA row ranges
+    T.tsvd_destroy(h)
     sc = np.ones(n)
     sc[3] = 2.0 ** 20
     assert np.array_equal(Gs, G * np.outer(sc, sc))
