@@ -107,16 +107,16 @@ cudaError_t launch_u_t(const T* A, int64_t m, int n, int64_t lda, const T* W, T*
 }
 
 // ---------------------------------------------------------------- v2: FP32, n <= 64
-// Persistent CTAs (one per SM, 8 warps) stream 128-row x n tiles of A through
-// a 3-stage shared-memory ring, one 2-D TMA load per tile (rows past m are
-// zero-filled by the TMA unit), so two tiles are in flight while the third
-// is consumed.  Each thread owns an 8-row x 4-column block of the U tile and
-// accumulates with packed FP32 FMAs (fma.rn.f32x2): row pairs of A times a
-// duplicated W entry, W being stored pre-duplicated ({w, w}) in shared
-// memory so that no operand shuffles are needed.
+// Persistent CTAs (two per SM, 4 warps each) stream 128-row x n tiles of A
+// through a 2-stage shared-memory ring, one 2-D TMA load per tile (rows past
+// m are zero-filled by the TMA unit).  Each thread owns 8 rows (4tr..4tr+3
+// and 64+4tr..64+4tr+3, so the 16-byte shared reads of consecutive lanes are
+// contiguous) by 8 columns of the U tile, and accumulates with packed FP32
+// FMAs (fma.rn.f32x2): a row pair of A times a duplicated W entry, W being
+// stored pre-duplicated ({w, w}) in shared memory.
 constexpr int U2_ROWS = 128;
-constexpr int U2_THREADS = 256;
-constexpr int U2_STAGES = 3;
+constexpr int U2_THREADS = 128;
+constexpr int U2_STAGES = 2;
 
 __device__ __forceinline__ void f2unpack(unsigned long long v, float& lo, float& hi) {
     asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
@@ -128,7 +128,7 @@ __device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsign
     return d;
 }
 
-__global__ void __launch_bounds__(U2_THREADS, 1)
+__global__ void __launch_bounds__(U2_THREADS, 2)
     compute_u_v2_kernel(const __grid_constant__ CUtensorMap tmapA, int64_t m, int n,
                         const float* __restrict__ W, float* __restrict__ U, int64_t ldu, int64_t ntiles,
                         DevInfo* info) {
@@ -138,8 +138,8 @@ __global__ void __launch_bounds__(U2_THREADS, 1)
     __shared__ __align__(8) uint64_t full[U2_STAGES];
     __shared__ int s_abort;
     const int tid = threadIdx.x;
-    const int tr = tid & 15;   // rows 8 tr .. 8 tr + 7 of the tile
-    const int tc = tid >> 4;   // columns 4 tc .. 4 tc + 3
+    const int tr = tid & 15;   // rows 4 tr .. 4 tr + 3 and 64 + 4 tr .. 64 + 4 tr + 3
+    const int tc = tid >> 4;   // columns 8 tc .. 8 tc + 7
     const unsigned tile_bytes = (unsigned)(U2_ROWS * n * sizeof(float));
     if (tid == 0) {
         tma_prefetch_desc(&tmapA);
@@ -155,23 +155,17 @@ __global__ void __launch_bounds__(U2_THREADS, 1)
     }
     __syncthreads();
     const int64_t first = blockIdx.x;
-    if (tid == 0) {
-        for (int k = 0; k < U2_STAGES - 1; ++k) {
-            const int64_t t = first + (int64_t)k * gridDim.x;
-            if (t < ntiles) {
-                mbar_expect_tx(&full[k], tile_bytes);
-                tma_load_2d(Ast + (size_t)k * 64 * U2_ROWS, &tmapA, (int)(t * U2_ROWS), 0, &full[k]);
-            }
-        }
+    if (tid == 0 && first < ntiles) {
+        mbar_expect_tx(&full[0], tile_bytes);
+        tma_load_2d(Ast, &tmapA, (int)(first * U2_ROWS), 0, &full[0]);
     }
     unsigned phase_bits = 0u;  // bit s: parity to wait for on full[s]
     int stage = 0;
     for (int64_t tile = first; tile < ntiles; tile += gridDim.x) {
-        const int64_t ahead = tile + (int64_t)(U2_STAGES - 1) * gridDim.x;
-        const int astage = (stage + U2_STAGES - 1) % U2_STAGES;
-        if (tid == 0 && ahead < ntiles) {
-            mbar_expect_tx(&full[astage], tile_bytes);
-            tma_load_2d(Ast + (size_t)astage * 64 * U2_ROWS, &tmapA, (int)(ahead * U2_ROWS), 0, &full[astage]);
+        const int64_t next = tile + gridDim.x;
+        if (tid == 0 && next < ntiles) {
+            mbar_expect_tx(&full[stage ^ 1], tile_bytes);
+            tma_load_2d(Ast + (size_t)(stage ^ 1) * 64 * U2_ROWS, &tmapA, (int)(next * U2_ROWS), 0, &full[stage ^ 1]);
         }
         if (!mbar_wait(&full[stage], (phase_bits >> stage) & 1u)) {
             atomicOr(&info->flags, FLAG_TIMEOUT);
@@ -180,45 +174,48 @@ __global__ void __launch_bounds__(U2_THREADS, 1)
         phase_bits ^= 1u << stage;
         __syncthreads();
         if (s_abort) break;
-        const float* At = Ast + (size_t)stage * 64 * U2_ROWS + 8 * tr;
-        const float* Wt = Wd + 8 * tc;
-        unsigned long long acc[4][4];  // [row pair][column]
+        const float* At = Ast + (size_t)stage * 64 * U2_ROWS + 4 * tr;
+        const float* Wt = Wd + 16 * tc;
+        unsigned long long acc[4][8];  // [row pair][column]
 #pragma unroll
         for (int rp = 0; rp < 4; ++rp)
 #pragma unroll
-            for (int k = 0; k < 4; ++k) acc[rp][k] = 0ull;
-#pragma unroll 4
+            for (int k = 0; k < 8; ++k) acc[rp][k] = 0ull;
+#pragma unroll 2
         for (int c = 0; c < n; ++c) {
             const ulonglong2 a01 = *reinterpret_cast<const ulonglong2*>(At + c * U2_ROWS);
-            const ulonglong2 a23 = *reinterpret_cast<const ulonglong2*>(At + c * U2_ROWS + 4);
-            const ulonglong2 w01 = *reinterpret_cast<const ulonglong2*>(Wt + c * 128);
-            const ulonglong2 w23 = *reinterpret_cast<const ulonglong2*>(Wt + c * 128 + 4);
+            const ulonglong2 a23 = *reinterpret_cast<const ulonglong2*>(At + c * U2_ROWS + 64);
+            const ulonglong2* wv = reinterpret_cast<const ulonglong2*>(Wt + c * 128);
+            const ulonglong2 w01 = wv[0], w23 = wv[1], w45 = wv[2], w67 = wv[3];
             const unsigned long long ap[4] = {a01.x, a01.y, a23.x, a23.y};
-            const unsigned long long wp[4] = {w01.x, w01.y, w23.x, w23.y};
+            const unsigned long long wp[8] = {w01.x, w01.y, w23.x, w23.y, w45.x, w45.y, w67.x, w67.y};
 #pragma unroll
             for (int rp = 0; rp < 4; ++rp)
 #pragma unroll
-                for (int k = 0; k < 4; ++k) acc[rp][k] = ffma2(ap[rp], wp[k], acc[rp][k]);
+                for (int k = 0; k < 8; ++k) acc[rp][k] = ffma2(ap[rp], wp[k], acc[rp][k]);
         }
-        const int64_t r0 = tile * U2_ROWS + 8 * tr;
+        const int64_t rbase = tile * U2_ROWS;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int j = 4 * tc + k;
+        for (int k = 0; k < 8; ++k) {
+            const int j = 8 * tc + k;
             if (j >= n) continue;
             float v[8];
 #pragma unroll
             for (int rp = 0; rp < 4; ++rp) f2unpack(acc[rp][k], v[2 * rp], v[2 * rp + 1]);
-            float* dst = U + (size_t)j * ldu + r0;
-            if (r0 + 7 < m) {
-                reinterpret_cast<float4*>(dst)[0] = make_float4(v[0], v[1], v[2], v[3]);
-                reinterpret_cast<float4*>(dst)[1] = make_float4(v[4], v[5], v[6], v[7]);
-            } else {
 #pragma unroll
-                for (int r = 0; r < 8; ++r)
-                    if (r0 + r < m) dst[r] = v[r];
+            for (int hh = 0; hh < 2; ++hh) {
+                const int64_t r0 = rbase + 64 * hh + 4 * tr;
+                float* dst = U + (size_t)j * ldu + r0;
+                if (r0 + 3 < m) {
+                    *reinterpret_cast<float4*>(dst) = make_float4(v[4 * hh], v[4 * hh + 1], v[4 * hh + 2], v[4 * hh + 3]);
+                } else {
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+                        if (r0 + r < m) dst[r] = v[4 * hh + r];
+                }
             }
         }
-        stage = (stage + 1) % U2_STAGES;
+        stage ^= 1;
         __syncthreads();  // every thread is done with this stage before it is refilled
     }
     if (s_abort && tid == 0) {
@@ -241,7 +238,7 @@ cudaError_t launch_compute_u_v2(const float* A, int64_t m, int n, int64_t lda, c
     e = cudaFuncSetAttribute(compute_u_v2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t ntiles = (m + U2_ROWS - 1) / U2_ROWS;
-    int64_t grid = (int64_t)sm_count;
+    int64_t grid = (int64_t)sm_count * 2;
     if (grid > ntiles) grid = ntiles;
     compute_u_v2_kernel<<<(unsigned)grid, U2_THREADS, smem, s>>>(tmap, m, n, W, U, ldu, ntiles, info);
     return cudaGetLastError();
