@@ -4,7 +4,7 @@
 // digit split and the error analysis); this file only changes where the
 // exact integer sums are formed and how long they accumulate.
 //
-// Per CTA (one per SM, a contiguous range of rows, 640 threads):
+// Per CTA (one per SM, every P-th 64-row sub-chunk, 640 threads):
 //   warp 0      TMA producer -- 64-row x n FP32 sub-chunks into a 4-stage ring.
 //   warp 1      TMEM owner (512 columns) and, on one lane, the MMA issuer.
 //   warps 4-19  16 worker warps (4 per scheduler).  Per sub-chunk they split:
@@ -53,10 +53,12 @@ namespace {
 
 constexpr int TC_SUB = 64;           // rows per sub-chunk (= MMA K of one digit stage)
 constexpr int TC_PERIOD = 16;        // sub-chunks per exact accumulation period (1024 rows)
-constexpr int TC_SF = 4;             // FP32 stages
+constexpr int TC_SF = 6;             // FP32 stages
 constexpr int TC_SD = 2;             // digit stages
 constexpr int TC_THREADS = 640;   // 4 control warps + 16 workers
 constexpr int TC_WORKERS = 512;
+constexpr int TC_XCHG = TC_WORKERS + 32;  // the exchange barrier: workers + the stage waiter warp
+constexpr int BAR_XCHG = 1, BAR_WORK = 2;  // named barrier ids
 constexpr int TC_FP_BYTES = 64 * TC_SUB * 4;       // [64 cols][64 rows] FP32
 constexpr int TC_DIG_BYTES = 7 * 64 * 128;         // 7 slices x 64 rows x 128 B
 constexpr int TC_SMEM = TC_SD * TC_DIG_BYTES + TC_SF * TC_FP_BYTES + 1024;  // + alignment slack
@@ -124,10 +126,6 @@ __device__ __forceinline__ unsigned long long f2_mul(unsigned long long a, unsig
     asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
     return d;
 }
-__device__ __forceinline__ float tc_scale_pow2(float a, int k) {
-    const int k1 = k / 2, k2 = k - k1;
-    return (a * __int_as_float((k1 + 127) << 23)) * __int_as_float((k2 + 127) << 23);
-}
 __device__ __forceinline__ int tc_exp_above(float mx) {
     const unsigned b = __float_as_uint(mx);
     const int be = (b >> 23) & 0xff;
@@ -138,81 +136,177 @@ struct TcShared {
     uint64_t fp_full[TC_SF], fp_empty[TC_SF];
     uint64_t dig_full[TC_SD], dig_empty[TC_SD];
     uint64_t acc_full, acc_empty;
+    alignas(16) int wflags[2][20];  // per worker warp: growth (soft 1, hard 2) and abort (4) bits;
+                                    // slot 16: the stage waiter's abort bit
     uint32_t tmem_base;
-    int abort;             // any role gave up (bounded wait expired)
-    int wabort;            // workers: uniform abort decision
-    int dig_newp[TC_SD];   // sub-chunk starts a new period
-    int growth;            // some column scale grew in this sub-chunk
-    int E_cur[64];         // scale of the running period
+    int abort;             // a control role gave up (bounded wait expired)
+    int dig_newp[TC_SD];   // the sub-chunk in this digit stage starts a new period
+    int E_cur[64];         // scale of the running period (column j is owned by worker warp j % 16)
+    unsigned thr[64];      // bit pattern of 2^E_cur (1 while the column is still empty)
     int E_pend[64];        // largest scale seen so far
     int E_old[64];         // scale of the period being drained
     int E_acc[64];         // scale of the fixed-point accumulators
-    int e_sub[64];
+    int dsh[64];           // E_old - E_acc (64: accumulators still empty)
+    int regrid;            // some dsh is non-zero
 };
 
-// Drain one finished period from TMEM into the caller's fixed-point
-// accumulators (E_acc -> E_old re-grid first).  All 512 workers call it.
-__device__ __forceinline__ void tc_drain(TcShared& S, uint32_t tmem, int wt, int quad, int lane, int J0,
-                                         long long (&hi)[16], int (&lo)[16]) {
-    const int lanei = quad * 32 + lane;
-    const int h = lanei >> 6, i = lanei & 63;
-    const int Ei = S.E_old[i], Eai = S.E_acc[i];
+// Bit pattern of the float 1.5 * 2^e.  Adding it to a float x with |x| <= 2^(e-1)
+// rounds x to the grid 2^(e-23); the low mantissa bits of the sum then hold that
+// integer, offset by the pattern itself.
+__host__ __device__ constexpr uint32_t tc_magic(int e) { return ((uint32_t)(e + 127) << 23) | 0x400000u; }
+// the same constant in both halves of an f32x2 pair
+__host__ __device__ constexpr unsigned long long tc_magic2(int e) {
+    return ((unsigned long long)tc_magic(e) << 32) | tc_magic(e);
+}
+
+// Fold rules of one TMEM column block (digit pair (s, t), w = 8 (s + t)): the
+// block holds P * 2^-w, P the exact integer sum of the digit products.
+//   kind 0: hi += P * 2^SH       (P split into RN(P / 2^G) * 2^G + rest, both exact)
+//   kind 1: lo += P              (same split)
+//   kind 2: lo += RN(P / 2^RS)   (s + t = 6 only)
+// Every magic add leaves its constant's pattern in the sum; those offsets are
+// constants per block and are removed once per drain (modular arithmetic).
+struct TcFold { int kind, w, sh, g; };
+__host__ __device__ constexpr TcFold tc_fold(int h, int cb) {
+    // h = 0: A holds digit 0; h = 1: digit 1 (cover: B = [1, 4, 2, 3], then [5], and
+    // the three 64-wide MMAs [6;0]x[0], [4;2]x[2], [2;3]x[3])
+    return h == 0 ? (cb == 0 ? TcFold{0, 8, 25, 6}      // (0,1)
+                   : cb == 1 ? TcFold{0, 32, 1, 12}    // (0,4)
+                   : cb == 2 ? TcFold{0, 16, 17, 12}   // (0,2)
+                   : cb == 3 ? TcFold{0, 24, 9, 12}    // (0,3)
+                   : cb == 4 ? TcFold{1, 40, 0, 12}    // (0,5)
+                   : cb == 5 ? TcFold{2, 48, 8, 0}     // (6,0)
+                   : cb == 6 ? TcFold{2, 48, 8, 0}     // (4,2)
+                             : TcFold{1, 40, 0, 12})   // (2,3)
+                  : (cb == 0 ? TcFold{0, 16, 16, 12}   // (1,1) diagonal: 1/2
+                   : cb == 1 ? TcFold{1, 40, 0, 12}    // (1,4)
+                   : cb == 2 ? TcFold{0, 24, 9, 12}    // (1,2)
+                   : cb == 3 ? TcFold{0, 32, 1, 12}    // (1,3)
+                   : cb == 4 ? TcFold{2, 48, 8, 0}     // (1,5)
+                   : cb == 5 ? TcFold{0, 0, 32, 12}    // (0,0) diagonal: 1/2
+                   : cb == 6 ? TcFold{0, 32, 0, 12}    // (2,2) diagonal: 1/2
+                             : TcFold{2, 48, 9, 0});   // (3,3) diagonal: 1/2
+}
+__host__ __device__ constexpr unsigned long long tc_hi_offset(int h) {
+    unsigned long long o = 0;
+    for (int cb = 0; cb < 8; ++cb) {
+        const TcFold f = tc_fold(h, cb);
+        if (f.kind == 0)
+            o += ((unsigned long long)tc_magic(23 + f.g - f.w) << (f.sh + f.g)) +
+                 ((unsigned long long)tc_magic(23 - f.w) << f.sh);
+    }
+    return o;
+}
+__host__ __device__ constexpr uint32_t tc_lo_offset(int h) {
+    uint32_t o = 0;
+    for (int cb = 0; cb < 8; ++cb) {
+        const TcFold f = tc_fold(h, cb);
+        if (f.kind == 1) o += (tc_magic(23 + f.g - f.w) << f.g) + tc_magic(23 - f.w);
+        if (f.kind == 2) o += tc_magic(23 + f.sh - f.w);
+    }
+    return o;
+}
+
+// Empty asm with the accumulators as operands: everything before it that updates
+// them completes first, so the next block's TMEM load does not raise the number
+// of live registers (the compiler would otherwise overlap whole blocks).
+__device__ __forceinline__ void tc_pin(unsigned long long (&hi)[16], uint32_t (&lo)[16]) {
+    asm volatile("" : "+l"(hi[0]), "+l"(hi[1]), "+l"(hi[2]), "+l"(hi[3]), "+l"(hi[4]), "+l"(hi[5]), "+l"(hi[6]),
+                      "+l"(hi[7]), "+l"(hi[8]), "+l"(hi[9]), "+l"(hi[10]), "+l"(hi[11]), "+l"(hi[12]), "+l"(hi[13]),
+                      "+l"(hi[14]), "+l"(hi[15]));
+    asm volatile("" : "+r"(lo[0]), "+r"(lo[1]), "+r"(lo[2]), "+r"(lo[3]), "+r"(lo[4]), "+r"(lo[5]), "+r"(lo[6]),
+                      "+r"(lo[7]), "+r"(lo[8]), "+r"(lo[9]), "+r"(lo[10]), "+r"(lo[11]), "+r"(lo[12]), "+r"(lo[13]),
+                      "+r"(lo[14]), "+r"(lo[15]));
+}
+
+template <int H, int CB>
+__device__ __forceinline__ void tc_fold_block(uint32_t trow, unsigned long long (&hi)[16], uint32_t (&lo)[16]) {
+    constexpr TcFold F = tc_fold(H, CB);
+    uint32_t r[16];
+    tc_pin(hi, lo);
+    tmem_ld16(trow + CB * 64, r);
+    if constexpr (F.kind == 2) {
+        constexpr unsigned long long C = tc_magic2(23 + F.sh - F.w);
+#pragma unroll
+        for (int k = 0; k < 16; k += 2) {
+            float t0, t1;
+            f2_unpack(f2_add(f2_pack(__uint_as_float(r[k]), __uint_as_float(r[k + 1])), C), t0, t1);
+            lo[k] += __float_as_uint(t0);
+            lo[k + 1] += __float_as_uint(t1);
+        }
+    } else {
+        constexpr unsigned long long C1 = tc_magic2(23 + F.g - F.w), C2 = tc_magic2(23 - F.w);
+#pragma unroll
+        for (int k = 0; k < 16; k += 2) {
+            const unsigned long long v = f2_pack(__uint_as_float(r[k]), __uint_as_float(r[k + 1]));
+            const unsigned long long t1 = f2_add(v, C1);                 // RN(P / 2^G) in the low bits
+            const unsigned long long t2 = f2_add(f2_sub(v, f2_sub(t1, C1)), C2);  // P - RN(P / 2^G) 2^G
+            float x0, x1, y0, y1;
+            f2_unpack(t1, x0, x1);
+            f2_unpack(t2, y0, y1);
+            const uint32_t a0 = __float_as_uint(x0), a1 = __float_as_uint(x1);
+            const uint32_t b0 = __float_as_uint(y0), b1 = __float_as_uint(y1);
+            if constexpr (F.kind == 1) {
+                lo[k] += (a0 << F.g) + b0;
+                lo[k + 1] += (a1 << F.g) + b1;
+            } else if constexpr (F.sh >= 32) {
+                hi[k] += (unsigned long long)((a0 << F.g) + b0) << F.sh;
+                hi[k + 1] += (unsigned long long)((a1 << F.g) + b1) << F.sh;
+            } else {
+                static_assert(F.kind != 0 || F.sh >= 32 || F.sh + F.g <= 31, "multiplier must fit 32 bits");
+                hi[k] += (unsigned long long)a0 * (1u << (F.sh + F.g)) + (unsigned long long)b0 * (1u << F.sh);
+                hi[k + 1] += (unsigned long long)a1 * (1u << (F.sh + F.g)) + (unsigned long long)b1 * (1u << F.sh);
+            }
+        }
+    }
+}
+template <int H>
+__device__ __forceinline__ void tc_fold_all(uint32_t trow, unsigned long long (&hi)[16], uint32_t (&lo)[16]) {
+    tc_fold_block<H, 0>(trow, hi, lo);
+    tc_fold_block<H, 1>(trow, hi, lo);
+    tc_fold_block<H, 2>(trow, hi, lo);
+    tc_fold_block<H, 3>(trow, hi, lo);
+    tc_fold_block<H, 4>(trow, hi, lo);
+    tc_fold_block<H, 5>(trow, hi, lo);
+    tc_fold_block<H, 6>(trow, hi, lo);
+    tc_fold_block<H, 7>(trow, hi, lo);
+    constexpr unsigned long long OH = tc_hi_offset(H);
+    constexpr uint32_t OL = tc_lo_offset(H);
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
-        const int Ej = S.E_old[J0 + k], Eaj = S.E_acc[J0 + k];
-        const int sh = (Eai == EXP_EMPTY || Eaj == EXP_EMPTY) ? 64 : (Ei - Eai) + (Ej - Eaj);
-        if (sh > 0) {
-            hi[k] = sh >= 63 ? 0 : hi[k] >> sh;
-            lo[k] = sh >= 31 ? 0 : lo[k] >> sh;
+        hi[k] -= OH;
+        lo[k] -= OL;
+    }
+}
+
+// Drain one finished period from TMEM into the caller's fixed-point
+// accumulators (re-grid E_acc -> E_old first).  All 512 workers call it; the
+// lane quadrant `quad` is fixed by the warp (a warp may only read its own 32
+// TMEM lanes), columns J0..J0+15.
+__device__ __forceinline__ void tc_drain(TcShared& S, uint32_t tmem, int wt, int quad, int lane, int J0,
+                                         unsigned long long (&hi)[16], uint32_t (&lo)[16]) {
+    const int lanei = quad * 32 + lane;
+    const int i = lanei & 63;
+    if (S.regrid) {
+        // move the accumulators onto the coarser grid of the grown scales (truncating)
+        const int di = S.dsh[i];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const int sh = di + S.dsh[J0 + k];
+            if (sh > 0) {
+                hi[k] = sh >= 63 ? 0ull : (unsigned long long)((long long)hi[k] >> sh);
+                lo[k] = sh >= 31 ? 0u : (uint32_t)((int)lo[k] >> sh);
+            }
         }
     }
     const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16) + J0;
-    uint32_t r[16];
-    // exact integers |v| <= 2^24: the 1.5 * 2^23 bias converts |v| <= 2^22, F2I the rest
-#define TC_CVT(V)                                                                              \
-    ((fabsf(V) <= 4194304.0f) ? (__float_as_int((V) + 12582912.0f) - 0x4B400000) : __float2int_rn(V))
-#define TC_FOLD(CB, SH)                                                                        \
-    {                                                                                          \
-        tmem_ld16(trow + (CB) * 64, r);                                                        \
-        _Pragma("unroll") for (int k = 0; k < 16; ++k) {                                       \
-            const long long iv = (long long)TC_CVT(__uint_as_float(r[k]));                      \
-            hi[k] += (long long)((unsigned long long)iv << (SH));                              \
-        }                                                                                      \
-    }
-#define TC_FOLD_LO(CB, RS)                                                                     \
-    {                                                                                          \
-        tmem_ld16(trow + (CB) * 64, r);                                                        \
-        _Pragma("unroll") for (int k = 0; k < 16; ++k) {                                       \
-            const int iv = TC_CVT(__uint_as_float(r[k]));                                      \
-            lo[k] += (RS) == 0 ? iv : ((iv + (1 << ((RS) > 0 ? (RS) - 1 : 0))) >> (RS));        \
-        }                                                                                      \
-    }
-    if (h == 0) {
-        TC_FOLD(0, 25)      // (0,1)
-        TC_FOLD(1, 1)       // (0,4)
-        TC_FOLD(2, 17)      // (0,2)
-        TC_FOLD(3, 9)       // (0,3)
-        TC_FOLD_LO(4, 0)    // (0,5)
-        TC_FOLD_LO(5, 8)    // (6,0)
-        TC_FOLD_LO(6, 8)    // (4,2)
-        TC_FOLD_LO(7, 0)    // (2,3)
-    } else {
-        TC_FOLD(0, 16)      // (1,1) diagonal: 1/2
-        TC_FOLD_LO(1, 0)    // (1,4)
-        TC_FOLD(2, 9)       // (1,2)
-        TC_FOLD(3, 1)       // (1,3)
-        TC_FOLD_LO(4, 8)    // (1,5)
-        TC_FOLD(5, 32)      // (0,0) diagonal: 1/2
-        TC_FOLD(6, 0)       // (2,2) diagonal: 1/2
-        TC_FOLD_LO(7, 9)    // (3,3) diagonal: 1/2
-    }
-#undef TC_FOLD_LO
-#undef TC_FOLD
-#undef TC_CVT
+    if (quad < 2) tc_fold_all<0>(trow, hi, lo);   // TMEM lanes 0..63: first digit of A
+    else tc_fold_all<1>(trow, hi, lo);            // lanes 64..127: second digit
     tc_fence_before();
-    named_bar(1, TC_WORKERS);
+    named_bar(BAR_WORK, TC_WORKERS);
     if (wt < 64) S.E_acc[wt] = S.E_old[wt];
-    named_bar(1, TC_WORKERS);
+    if (wt == 0) S.regrid = 0;
+    named_bar(BAR_WORK, TC_WORKERS);
 }
 
 __global__ void __launch_bounds__(TC_THREADS, 1)
@@ -227,9 +321,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     __shared__ TcShared S;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int64_t r_begin = (int64_t)blockIdx.x * rows_per_cta;
-    const int64_t r_end = min(m, r_begin + rows_per_cta);
-    const int G = r_end > r_begin ? (int)((r_end - r_begin + TC_SUB - 1) / TC_SUB) : 0;
+    // sub-chunks are dealt round-robin (CTA b takes b, b + P, b + 2P, ...): at any time the
+    // CTAs stream neighbouring 256-byte pieces of every column, which keeps DRAM pages open.
+    // A CTA takes at most rows_per_cta rows (the fixed-point bounds need <= 2^15).
+    const int64_t subs = (m + TC_SUB - 1) / TC_SUB;
+    const int64_t P = gridDim.x;
+    const int G = (int64_t)blockIdx.x < subs ? (int)((subs - 1 - blockIdx.x) / P + 1) : 0;
+    (void)rows_per_cta;
 
     if (tid == 0) {
         for (int s = 0; s < TC_SF; ++s) { mbar_init(&S.fp_full[s], 1); mbar_init(&S.fp_empty[s], 1); }
@@ -238,11 +336,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         mbar_init(&S.acc_empty, 1);
         mbar_fence_init();
         S.abort = 0;
-        S.wabort = 0;
     }
     if (tid < 64) {
-        S.E_cur[tid] = EXP_EMPTY;
-        S.E_pend[tid] = EXP_EMPTY;
         S.E_old[tid] = EXP_EMPTY;
         S.E_acc[tid] = EXP_EMPTY;
     }
@@ -258,7 +353,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     int tma_issued = 0;
 
     if (warp < 4) {
-        asm volatile("setmaxnreg.dec.sync.aligned.u32 40;");
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 32;");
         if (warp == 0 && lane == 0) {
             // ---------------- TMA producer
             tma_prefetch_desc(&tmapA);
@@ -272,7 +367,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
                 if (S.abort) break;
                 mbar_expect_tx(&S.fp_full[f], bytes);
-                tma_load_2d(fpb + (size_t)f * 64 * TC_SUB, &tmapA, (int)(r_begin + (int64_t)g * TC_SUB), 0,
+                tma_load_2d(fpb + (size_t)f * 64 * TC_SUB, &tmapA, (int)(((int64_t)blockIdx.x + (int64_t)g * P) * TC_SUB), 0,
                             &S.fp_full[f]);
                 issued = g + 1;
             }
@@ -309,132 +404,216 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             // every MMA issued by this thread has completed once that phase completes
             mma_commit(&S.acc_full);
             (void)mbar_wait(&S.acc_full, period & 1);
+        } else if (warp == 2) {
+            // ---------------- stage waiter: one iteration ahead of the workers it waits for
+            // the FP32 sub-chunk and the digit stage they use next, then joins their exchange
+            // barrier; its waits overlap the workers' split instead of delaying the barrier.
+            if (G > 0) {
+                int fl = 0;
+                if (lane == 0) {
+                    if (!mbar_wait(&S.fp_full[0], 0)) fl |= 4;
+                    if (G > 1 && !mbar_wait(&S.fp_full[1 % TC_SF], (1 / TC_SF) & 1)) fl |= 4;
+                    S.wflags[0][16] = fl;
+                    S.regrid = 0;
+                }
+                named_bar(BAR_XCHG, TC_XCHG);
+                // the workers' first exchange carries no abort bit but this one
+                const int G_run = (S.wflags[0][16] & 4) ? 0 : G;
+                for (int g = 0; g < G_run; ++g) {
+                    fl = 0;
+                    if (lane == 0) {
+                        if (g + 2 < G && !mbar_wait(&S.fp_full[(g + 2) % TC_SF], ((g + 2) / TC_SF) & 1)) fl |= 4;
+                        if (g + 1 < G && g + 1 >= TC_SD &&
+                            !mbar_wait(&S.dig_empty[(g + 1) % TC_SD], (((g + 1) / TC_SD) - 1) & 1))
+                            fl |= 4;
+                        if (S.abort) fl |= 4;
+                        S.wflags[(g + 1) & 1][16] = fl;
+                    }
+                    named_bar(BAR_XCHG, TC_XCHG);
+                    // the same OR the workers form: everyone leaves the loop together
+                    int F = 0;
+#pragma unroll
+                    for (int w = 0; w < 17; ++w) F |= S.wflags[(g + 1) & 1][w];
+                    if (F & 4) break;
+                }
+            }
         }
     } else {
-        // ---------------- 16 worker warps: split every sub-chunk, drain every period
-        asm volatile("setmaxnreg.inc.sync.aligned.u32 104;");
+        // ---------------- 16 worker warps: split every sub-chunk, drain every period.
+        // Software-pipelined: iteration g writes the digits of sub-chunk g and reads
+        // sub-chunk g+1 (column maxima, growth class), then one barrier exchanges the
+        // per-warp growth / abort bits.  Warp w splits columns w, w+16, w+32, w+48 (lane l:
+        // rows 2l, 2l+1).  Warp 2 waits on the stage barriers for them.
+        asm volatile("setmaxnreg.inc.sync.aligned.u32 112;");
         const int wt = tid - 128;                  // worker thread 0..511
+        const int wq = warp - 4;                   // worker warp 0..15
         const int quad = warp & 3;                 // TMEM lane quadrant of this warp
-        const int J0 = 16 * ((warp - 4) >> 2);     // columns J0..J0+15 of the drain
-        const int half = lane >> 4, q = lane & 15; // split item: column half of the warp, row quad
-        const unsigned long long MAGIC = f2_pack(12582912.0f, 12582912.0f);  // 1.5 * 2^23
-        const unsigned long long S256 = f2_pack(256.0f, 256.0f);
-        long long hi[16];
-        int lo[16];
+        const int J0 = 16 * (wq >> 2);             // drain columns J0..J0+15
+        unsigned long long hi[16];
+        uint32_t lo[16];
 #pragma unroll
         for (int k = 0; k < 16; ++k) { hi[k] = 0; lo[k] = 0; }
-        int period_len = 0, drained = 0;
+        int period_len = 1, drained = 0, late = 0, newp = 1, next_newp = 0;
         bool bad = false, aborted = false;
-        for (int g = 0; g < G && !aborted; ++g) {
-            const int f = g % TC_SF, d = g % TC_SD;
-            if (!mbar_wait(&S.fp_full[f], (g / TC_SF) & 1)) atomicOr(&S.wabort, 1);
-            if (wt == 0 && S.abort) atomicOr(&S.wabort, 1);
-            named_bar(1, TC_WORKERS);
-            if (S.wabort) { aborted = true; break; }
-            // two items (column j, rows 4q..4q+3) per thread; a half-warp covers one column
-            const float* fp = fpb + (size_t)f * 64 * TC_SUB;
-            float v[2][4];
+        // 2^E as a bit pattern: |a| < 2^E  <=>  bits(|a|) < pattern (E = 128 gives +Inf's)
+        auto set_scale = [&](int j, int E) {
+            S.E_cur[j] = E;
+            S.thr[j] = E == EXP_EMPTY ? 1u : (unsigned)(E + 127) << 23;
+        };
+        if (lane < 4) {
+            set_scale(wq + 16 * lane, EXP_EMPTY);
+            S.E_pend[wq + 16 * lane] = EXP_EMPTY;
+        }
+        __syncwarp();
+
+        // classify sub-chunk gg (already resident) against this warp's running scales.
+        // Fast path: no entry reaches 2^E_cur in any of the warp's columns (one vote).
+        auto load_classify = [&](int gg) -> int {
+            int fl = 0;
+            const float* fp = fpb + (size_t)(gg % TC_SF) * 64 * TC_SUB + 2 * lane;
+            unsigned mb[4];
+            bool grow = false;
 #pragma unroll
-            for (int it = 0; it < 2; ++it) {
-                const int j = 2 * ((wt >> 5) + 16 * it) + half;
-                float4 a4 = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (j < n) a4 = *reinterpret_cast<const float4*>(fp + j * TC_SUB + 4 * q);
-                v[it][0] = a4.x; v[it][1] = a4.y; v[it][2] = a4.z; v[it][3] = a4.w;
-                // max |a| on the bit patterns (also exposes Inf / NaN, whose patterns are the largest)
-                unsigned mb = max(max(__float_as_uint(a4.x) & 0x7fffffffu, __float_as_uint(a4.y) & 0x7fffffffu),
-                                  max(__float_as_uint(a4.z) & 0x7fffffffu, __float_as_uint(a4.w) & 0x7fffffffu));
-                mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, 1));
-                mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, 2));
-                mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, 4));
-                mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, 8));
-                if (mb >= 0x7f800000u) bad = true;
-                if (q == 0) S.e_sub[j] = (mb == 0u || mb >= 0x7f800000u) ? EXP_EMPTY : tc_exp_above(__uint_as_float(mb));
+            for (int c = 0; c < 4; ++c) {
+                const int j = wq + 16 * c;
+                float2 a2 = make_float2(0.f, 0.f);
+                if (j < n) a2 = *reinterpret_cast<const float2*>(fp + j * TC_SUB);
+                // max |a| on the bit patterns (Inf / NaN have the largest patterns)
+                mb[c] = max(__float_as_uint(a2.x) & 0x7fffffffu, __float_as_uint(a2.y) & 0x7fffffffu);
+                grow |= mb[c] >= S.thr[j];
             }
-            if (wt == 0) S.growth = 0;
-            named_bar(1, TC_WORKERS);
-            if (wt < 64) {
-                // E_pend: largest scale seen; E_cur: scale of the running period.  One binade
-                // above E_cur is "soft" (top digit in [-256, 256], still exact in bf16); more,
-                // or a first non-zero entry, is "hard" and needs a new period.
-                const int e = S.e_sub[wt], cur = S.E_cur[wt];
-                S.E_pend[wt] = max(S.E_pend[wt], e);
-                if (e != EXP_EMPTY) {
-                    if (cur == EXP_EMPTY || e > cur + 1) atomicOr(&S.growth, 2);
-                    else if (e == cur + 1) atomicOr(&S.growth, 1);
+            if (__any_sync(0xffffffffu, grow)) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int j = wq + 16 * c;
+                    const unsigned m = __reduce_max_sync(0xffffffffu, mb[c]);
+                    if (m >= 0x7f800000u) bad = true;
+                    const int e = (m == 0u || m >= 0x7f800000u) ? EXP_EMPTY : tc_exp_above(__uint_as_float(m));
+                    const int cur = S.E_cur[j];
+                    // one binade above the running scale is "soft" (top digit in [-256, 256], still
+                    // exact in bf16); more, or a first non-zero entry, is "hard": new period
+                    if (e != EXP_EMPTY) {
+                        if (cur == EXP_EMPTY || e > cur + 1) fl |= 2;
+                        else if (e == cur + 1) fl |= 1;
+                    }
+                    if (lane == 0 && e > S.E_pend[j]) S.E_pend[j] = e;
                 }
             }
-            named_bar(1, TC_WORKERS);
-            // exactness budget of a period: sum |q_s q_t| <= 2^24 per block and (i, j);
-            // a normal sub-chunk may add 64 * 128^2 = 2^20 (1 unit), a soft one 2^22 (4 units)
-            const int cost = (S.growth & 1) ? 4 : 1;
-            const bool newp = (g == 0) || (S.growth & 2) || (period_len + cost > TC_PERIOD);
-            if (newp) {
-                named_bar(1, TC_WORKERS);  // every worker has read S.growth
-                if (wt < 64) {
-                    S.E_old[wt] = S.E_cur[wt];    // scale of the period that ends here
-                    S.E_cur[wt] = S.E_pend[wt];   // the new period starts on every grown scale
-                }
-                named_bar(1, TC_WORKERS);
-                period_len = 0;
-            }
-            period_len += newp ? 1 : cost;
-            // free digit stage?
-            if (g >= TC_SD && !mbar_wait(&S.dig_empty[d], ((g / TC_SD) - 1) & 1)) atomicOr(&S.wabort, 1);
-            named_bar(1, TC_WORKERS);
-            if (S.wabort) { aborted = true; break; }
-            unsigned char* ds = dig + (size_t)d * TC_DIG_BYTES;
+            return fl;
+        };
+        // OR of every worker's bits; slot parity alternates so one barrier suffices
+        auto exchange = [&](int par, int fl, int bar_id, int bar_count) -> int {
+            fl = __reduce_or_sync(0xffffffffu, fl);
+            if (lane == 0) S.wflags[par][wq] = fl;
+            named_bar(bar_id, bar_count);
+            const int4* w4 = reinterpret_cast<const int4*>(S.wflags[par]);
+            int F = S.wflags[par][16];
 #pragma unroll
-            for (int it = 0; it < 2; ++it) {
-                const int j = 2 * ((wt >> 5) + 16 * it) + half;
-                const int E = S.E_cur[j];
-                // y = 128 a 2^-E (|y| < 256); digit q = RN(y) by the 1.5*2^23 bias; y <- 256 (y - q)
-                unsigned long long y01 = 0ull, y23 = 0ull;
-                if (E != EXP_EMPTY) {
-                    const int k = 7 - E;
-                    y01 = f2_pack(tc_scale_pow2(v[it][0], k), tc_scale_pow2(v[it][1], k));
-                    y23 = f2_pack(tc_scale_pow2(v[it][2], k), tc_scale_pow2(v[it][3], k));
+            for (int u = 0; u < 4; ++u) {
+                const int4 x = w4[u];
+                F |= x.x | x.y | x.z | x.w;
+            }
+            return F;
+        };
+        // a period ends: record its scales for the drain, start the next on the grown ones
+        auto close_period = [&](bool start_next) {
+            if (lane < 4) {
+                const int j = wq + 16 * lane;
+                const int eo = S.E_cur[j], ea = S.E_acc[j];
+                S.E_old[j] = eo;
+                const int dd = ea == EXP_EMPTY ? 64 : eo - ea;
+                S.dsh[j] = dd;
+                if (dd != 0) S.regrid = 1;
+                if (start_next) set_scale(j, S.E_pend[j]);
+            }
+            __syncwarp();
+        };
+
+        if (G > 0) {
+            named_bar(BAR_XCHG, TC_XCHG);  // the waiter has seen sub-chunks 0 and 1 arrive
+            // (load_classify sets no abort bit: an abort here is the waiter's, which it acts on too)
+            const int F = exchange(0, load_classify(0), BAR_WORK, TC_WORKERS);
+            // sub-chunk 0 opens the first period on the scales just seen
+            if (lane < 4) set_scale(wq + 16 * lane, S.E_pend[wq + 16 * lane]);
+            __syncwarp();
+            if (F & 4) aborted = true;
+        }
+        // g == G only drains the last period
+        for (int g = 0; g <= G && !aborted && G > 0; ++g) {
+            const int d = g % TC_SD;
+            if (g < G) {
+                int fl = late;
+                // digits of sub-chunk g: y = 128 a 2^-E (|y| < 128, < 256 after a soft growth);
+                // digit s is y's remainder rounded to the grid 2^-8s (|digit| <= 128 grid units,
+                // exact in bf16: 8 significant bits); the MMA sees digit s scaled by 2^-8s
+                const float* fp = fpb + (size_t)(g % TC_SF) * 64 * TC_SUB + 2 * lane;
+                unsigned char* ds = dig + (size_t)d * TC_DIG_BYTES;
+                unsigned long long y[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int j = wq + 16 * c;
+                    const int E = S.E_cur[j];
+                    y[c] = 0ull;
+                    if (E != EXP_EMPTY) {
+                        const float2 a2 = *reinterpret_cast<const float2*>(fp + j * TC_SUB);
+                        const int k = 7 - E, k1 = k / 2, k2 = k - k1;
+                        const float s1 = __int_as_float((k1 + 127) << 23), s2 = __int_as_float((k2 + 127) << 23);
+                        y[c] = f2_mul(f2_mul(f2_pack(a2.x, a2.y), f2_pack(s1, s1)), f2_pack(s2, s2));
+                    }
                 }
 #pragma unroll
                 for (int sdig = 0; sdig < 7; ++sdig) {
-                    const unsigned long long q01 = f2_sub(f2_add(y01, MAGIC), MAGIC);
-                    const unsigned long long q23 = f2_sub(f2_add(y23, MAGIC), MAGIC);
-                    float a0, a1, a2, a3;
-                    f2_unpack(q01, a0, a1);
-                    f2_unpack(q23, a2, a3);
-                    const __nv_bfloat162 b01 = __floats2bfloat162_rn(a0, a1);
-                    const __nv_bfloat162 b23 = __floats2bfloat162_rn(a2, a3);
-                    y01 = f2_mul(f2_sub(y01, q01), S256);
-                    y23 = f2_mul(f2_sub(y23, q23), S256);
-                    const int row = c_pos_of_digit[sdig] * 64 + j;
-                    uint2* dst = reinterpret_cast<uint2*>(ds + row * 128 + (((q >> 1) ^ (row & 7)) << 4) + ((q & 1) << 3));
-                    *dst = make_uint2(*reinterpret_cast<const uint32_t*>(&b01), *reinterpret_cast<const uint32_t*>(&b23));
+                    const unsigned long long M2 = tc_magic2(23 - 8 * sdig);
+                    uint32_t bq[4];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const unsigned long long qd = f2_sub(f2_add(y[c], M2), M2);
+                        if (sdig < 6) y[c] = f2_sub(y[c], qd);
+                        float a0, a1;
+                        f2_unpack(qd, a0, a1);
+                        // the digit has at most 8 significant bits: its bf16 is the top half
+                        bq[c] = __byte_perm(__float_as_uint(a0), __float_as_uint(a1), 0x7632);
+                    }
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const int j = wq + 16 * c;
+                        // slice position of digit s: 64 rows (columns j) of 128 bytes, 16-byte
+                        // chunks swizzled by row
+                        *reinterpret_cast<uint32_t*>(ds + c_pos_of_digit[sdig] * 8192 + j * 128 +
+                                                     ((((lane >> 2) ^ (j & 7)) << 4) | ((lane & 3) << 2))) = bq[c];
+                    }
                 }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                if (g + 1 < G) fl |= load_classify(g + 1);
+                const int F = exchange((g + 1) & 1, fl, BAR_XCHG, TC_XCHG);
+                if (F & 4) { aborted = true; break; }
+                if (wt == 0) {
+                    S.dig_newp[d] = newp;
+                    mbar_arrive(&S.dig_full[d]);
+                    mbar_arrive(&S.fp_empty[g % TC_SF]);
+                }
+                // exactness budget of a period: sum |q_s q_t| <= 2^24 grid units per block and
+                // (i, j); a normal sub-chunk adds at most 64 * 128^2 = 2^20 (1 unit), one with a
+                // soft growth 64 * 256^2 = 2^22 (4 units)
+                const int cost = (F & 1) ? 4 : 1;
+                next_newp = (g + 1 < G) && ((F & 2) || (period_len + cost > TC_PERIOD));
+                period_len = next_newp ? 1 : period_len + cost;
             }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            named_bar(1, TC_WORKERS);
-            if (wt == 0) {
-                S.dig_newp[d] = newp ? 1 : 0;
-                mbar_arrive(&S.dig_full[d]);
-                mbar_arrive(&S.fp_empty[f]);
-            }
-            if (newp && g > 0) {
-                // the MMA issuer closes the previous period on seeing this stage; drain it
-                if (!mbar_wait(&S.acc_full, drained & 1)) atomicOr(&S.wabort, 1);
+            if ((newp && g > 0) || g == G) {
+                // the MMA issuer closes a period on seeing the first stage of the next one
+                // (or after the last sub-chunk); drain it
+                if (g == G) close_period(false);
+                if (!mbar_wait(&S.acc_full, drained & 1)) late |= 4;
                 tc_fence_after();
-                named_bar(1, TC_WORKERS);
-                if (S.wabort) { aborted = true; break; }
+                if (g == G) named_bar(BAR_WORK, TC_WORKERS);
                 tc_drain(S, tmem, wt, quad, lane, J0, hi, lo);
-                if (wt == 0) mbar_arrive(&S.acc_empty);
+                if (wt == 0 && g < G) mbar_arrive(&S.acc_empty);
                 ++drained;
             }
-        }
-        // the last period
-        if (!aborted && G > 0) {
-            if (wt < 64) S.E_old[wt] = S.E_cur[wt];
-            if (!mbar_wait(&S.acc_full, drained & 1)) atomicOr(&S.wabort, 1);
-            tc_fence_after();
-            named_bar(1, TC_WORKERS);
-            if (!S.wabort) tc_drain(S, tmem, wt, quad, lane, J0, hi, lo);
+            if (g < G) {
+                if (next_newp) close_period(true);
+                newp = next_newp;
+            }
         }
         if (bad) atomicOr(&info->flags, FLAG_NONFINITE);
         // partials of this CTA: W = sum over blocks (s < t) + 1/2 (s = s); G = W + W^T later.
@@ -446,16 +625,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             if (h == hh) {
 #pragma unroll
                 for (int k = 0; k < 16; ++k) {
-                    const long long l63 = (long long)((unsigned long long)(long long)lo[k] << 9);
-                    if (hh == 0) { ph[i * 64 + J0 + k] = hi[k]; pl[i * 64 + J0 + k] = l63; }
-                    else { ph[i * 64 + J0 + k] += hi[k]; pl[i * 64 + J0 + k] += l63; }
+                    const long long l63 = (long long)((unsigned long long)(long long)(int)lo[k] << 9);
+                    if (hh == 0) { ph[i * 64 + J0 + k] = (long long)hi[k]; pl[i * 64 + J0 + k] = l63; }
+                    else { ph[i * 64 + J0 + k] += (long long)hi[k]; pl[i * 64 + J0 + k] += l63; }
                 }
             }
             __threadfence_block();
-            named_bar(1, TC_WORKERS);
+            named_bar(BAR_WORK, TC_WORKERS);
         }
         if (wt < 64) part_E[(size_t)blockIdx.x * 64 + wt] = S.E_acc[wt];
-        if (wt == 0 && S.wabort) atomicExch(&S.abort, 1);
+        if (aborted || (late & 4)) atomicExch(&S.abort, 1);
     }
     // teardown: every tcgen05 access is complete before the TMEM is freed
     tc_fence_before();
