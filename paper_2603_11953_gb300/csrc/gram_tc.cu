@@ -57,8 +57,8 @@ constexpr int TC_SF = 6;             // FP32 stages
 constexpr int TC_SD = 2;             // digit stages
 constexpr int TC_THREADS = 640;   // 4 control warps + 16 workers
 constexpr int TC_WORKERS = 512;
-constexpr int TC_XCHG = TC_WORKERS + 32;  // the exchange barrier: workers + the stage waiter warp
-constexpr int BAR_XCHG = 1, BAR_WORK = 2;  // named barrier ids
+constexpr int TC_RD = 8;              // decision records
+constexpr int BAR_DEC = 1, BAR_WORK = 2;  // named barrier ids: the two decider warps, the workers
 constexpr int TC_FP_BYTES = 64 * TC_SUB * 4;       // [64 cols][64 rows] FP32
 constexpr int TC_DIG_BYTES = 7 * 64 * 128;         // 7 slices x 64 rows x 128 B
 constexpr int TC_SMEM = TC_SD * TC_DIG_BYTES + TC_SF * TC_FP_BYTES + 1024;  // + alignment slack
@@ -94,12 +94,10 @@ __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::
 __device__ __forceinline__ void named_bar(int id, int count) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 // packed FP32 pairs (two rows of one column), Blackwell f32x2 instructions
@@ -132,22 +130,25 @@ __device__ __forceinline__ int tc_exp_above(float mx) {
     return be == 0 ? -126 : be - 126;
 }
 
+// The deciders' verdict on one sub-chunk, read by the workers and the MMA issuer.
+struct TcRecord {
+    int newp;      // the sub-chunk opens a new period (the previous one is drained first)
+    int regrid[2]; // per decider warp: some dsh of its columns is non-zero
+    int pad;
+    int E[64];     // scale of each column for this sub-chunk's digits
+    int dsh[64];   // when newp: E_old - E_acc of the period that ends (64: nothing accumulated yet)
+};
+
 struct TcShared {
     uint64_t fp_full[TC_SF], fp_empty[TC_SF];
     uint64_t dig_full[TC_SD], dig_empty[TC_SD];
+    uint64_t dec_full[TC_RD], dec_empty[TC_RD];
     uint64_t acc_full, acc_empty;
-    alignas(16) int wflags[2][20];  // per worker warp: growth (soft 1, hard 2) and abort (4) bits;
-                                    // slot 16: the stage waiter's abort bit
+    TcRecord rec[TC_RD];
+    int dflags[2][2];      // decider warps: growth (soft 1, hard 2) and abort (4) bits, double-buffered
     uint32_t tmem_base;
-    int abort;             // a control role gave up (bounded wait expired)
-    int dig_newp[TC_SD];   // the sub-chunk in this digit stage starts a new period
-    int E_cur[64];         // scale of the running period (column j is owned by worker warp j % 16)
-    unsigned thr[64];      // bit pattern of 2^E_cur (1 while the column is still empty)
-    int E_pend[64];        // largest scale seen so far
-    int E_old[64];         // scale of the period being drained
-    int E_acc[64];         // scale of the fixed-point accumulators
-    int dsh[64];           // E_old - E_acc (64: accumulators still empty)
-    int regrid;            // some dsh is non-zero
+    int abort;             // some role gave up (bounded wait expired)
+    int dig_newp[TC_SD];   // the sub-chunk in this digit stage opens a new period
 };
 
 // Bit pattern of the float 1.5 * 2^e.  Adding it to a float x with |x| <= 2^(e-1)
@@ -222,40 +223,45 @@ __device__ __forceinline__ void tc_pin(unsigned long long (&hi)[16], uint32_t (&
 template <int H, int CB>
 __device__ __forceinline__ void tc_fold_block(uint32_t trow, unsigned long long (&hi)[16], uint32_t (&lo)[16]) {
     constexpr TcFold F = tc_fold(H, CB);
-    uint32_t r[16];
-    tc_pin(hi, lo);
-    tmem_ld16(trow + CB * 64, r);
-    if constexpr (F.kind == 2) {
-        constexpr unsigned long long C = tc_magic2(23 + F.sh - F.w);
+    // two halves of 8 columns keep the temporaries few (the accumulators use 48 registers)
 #pragma unroll
-        for (int k = 0; k < 16; k += 2) {
-            float t0, t1;
-            f2_unpack(f2_add(f2_pack(__uint_as_float(r[k]), __uint_as_float(r[k + 1])), C), t0, t1);
-            lo[k] += __float_as_uint(t0);
-            lo[k + 1] += __float_as_uint(t1);
-        }
-    } else {
-        constexpr unsigned long long C1 = tc_magic2(23 + F.g - F.w), C2 = tc_magic2(23 - F.w);
+    for (int hf = 0; hf < 2; ++hf) {
+        uint32_t r[8];
+        tc_pin(hi, lo);
+        tmem_ld8(trow + CB * 64 + 8 * hf, r);
+        if constexpr (F.kind == 2) {
+            constexpr unsigned long long C = tc_magic2(23 + F.sh - F.w);
 #pragma unroll
-        for (int k = 0; k < 16; k += 2) {
-            const unsigned long long v = f2_pack(__uint_as_float(r[k]), __uint_as_float(r[k + 1]));
-            const unsigned long long t1 = f2_add(v, C1);                 // RN(P / 2^G) in the low bits
-            const unsigned long long t2 = f2_add(f2_sub(v, f2_sub(t1, C1)), C2);  // P - RN(P / 2^G) 2^G
-            float x0, x1, y0, y1;
-            f2_unpack(t1, x0, x1);
-            f2_unpack(t2, y0, y1);
-            const uint32_t a0 = __float_as_uint(x0), a1 = __float_as_uint(x1);
-            const uint32_t b0 = __float_as_uint(y0), b1 = __float_as_uint(y1);
-            if constexpr (F.kind == 1) {
-                lo[k] += (a0 << F.g) + b0;
-                lo[k + 1] += (a1 << F.g) + b1;
-            } else if constexpr (F.sh >= 32) {
-                hi[k] += (unsigned long long)((a0 << F.g) + b0) << F.sh;
-                hi[k + 1] += (unsigned long long)((a1 << F.g) + b1) << F.sh;
-            } else {
-                static_assert(F.kind != 0 || F.sh >= 32 || F.sh + F.g <= 31, "multiplier must fit 32 bits");
-                hi[k] += (unsigned long long)a0 * (1u << (F.sh + F.g)) + (unsigned long long)b0 * (1u << F.sh);
-                hi[k + 1] += (unsigned long long)a1 * (1u << (F.sh + F.g)) + (unsigned long long)b1 * (1u << F.sh);
+            for (int k = 0; k < 8; k += 2) {
+                float t0, t1;
+                f2_unpack(f2_add(f2_pack(__uint_as_float(r[k]), __uint_as_float(r[k + 1])), C), t0, t1);
+                lo[8 * hf + k] += __float_as_uint(t0);
+                lo[8 * hf + k + 1] += __float_as_uint(t1);
+            }
+        } else {
+            constexpr unsigned long long C1 = tc_magic2(23 + F.g - F.w), C2 = tc_magic2(23 - F.w);
+#pragma unroll
+            for (int k = 0; k < 8; k += 2) {
+                const int kk = 8 * hf + k;
+                const unsigned long long v = f2_pack(__uint_as_float(r[k]), __uint_as_float(r[k + 1]));
+                const unsigned long long t1 = f2_add(v, C1);                 // RN(P / 2^G) in the low bits
+                const unsigned long long t2 = f2_add(f2_sub(v, f2_sub(t1, C1)), C2);  // P - RN(P / 2^G) 2^G
+                float x0, x1, y0, y1;
+                f2_unpack(t1, x0, x1);
+                f2_unpack(t2, y0, y1);
+                const uint32_t a0 = __float_as_uint(x0), a1 = __float_as_uint(x1);
+                const uint32_t b0 = __float_as_uint(y0), b1 = __float_as_uint(y1);
+                if constexpr (F.kind == 1) {
+                    lo[kk] += (a0 << F.g) + b0;
+                    lo[kk + 1] += (a1 << F.g) + b1;
+                } else if constexpr (F.sh >= 32) {
+                    hi[kk] += (unsigned long long)((a0 << F.g) + b0) << F.sh;
+                    hi[kk + 1] += (unsigned long long)((a1 << F.g) + b1) << F.sh;
+                } else {
+                    static_assert(F.kind != 0 || F.sh >= 32 || F.sh + F.g <= 31, "multiplier must fit 32 bits");
+                    hi[kk] += (unsigned long long)a0 * (1u << (F.sh + F.g)) + (unsigned long long)b0 * (1u << F.sh);
+                    hi[kk + 1] += (unsigned long long)a1 * (1u << (F.sh + F.g)) + (unsigned long long)b1 * (1u << F.sh);
+                }
             }
         }
     }
@@ -279,20 +285,19 @@ __device__ __forceinline__ void tc_fold_all(uint32_t trow, unsigned long long (&
     }
 }
 
-// Drain one finished period from TMEM into the caller's fixed-point
-// accumulators (re-grid E_acc -> E_old first).  All 512 workers call it; the
-// lane quadrant `quad` is fixed by the warp (a warp may only read its own 32
-// TMEM lanes), columns J0..J0+15.
-__device__ __forceinline__ void tc_drain(TcShared& S, uint32_t tmem, int wt, int quad, int lane, int J0,
+// Drain one finished period from TMEM into the calling warp's fixed-point
+// accumulators, after moving them onto the period's (coarser or equal) grid: dsh
+// holds E_old - E_acc per column.  Each warp works alone: its lane quadrant
+// `quad` is fixed by the warp (a warp may only read its own 32 TMEM lanes),
+// columns J0..J0+15.
+__device__ __forceinline__ void tc_drain(const TcRecord& R, uint32_t tmem, int quad, int lane, int J0,
                                          unsigned long long (&hi)[16], uint32_t (&lo)[16]) {
-    const int lanei = quad * 32 + lane;
-    const int i = lanei & 63;
-    if (S.regrid) {
-        // move the accumulators onto the coarser grid of the grown scales (truncating)
-        const int di = S.dsh[i];
+    if (R.regrid[0] | R.regrid[1]) {
+        // truncating shift onto the grid of the grown scales
+        const int di = R.dsh[(quad * 32 + lane) & 63];
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
-            const int sh = di + S.dsh[J0 + k];
+            const int sh = di + R.dsh[J0 + k];
             if (sh > 0) {
                 hi[k] = sh >= 63 ? 0ull : (unsigned long long)((long long)hi[k] >> sh);
                 lo[k] = sh >= 31 ? 0u : (uint32_t)((int)lo[k] >> sh);
@@ -302,11 +307,6 @@ __device__ __forceinline__ void tc_drain(TcShared& S, uint32_t tmem, int wt, int
     const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16) + J0;
     if (quad < 2) tc_fold_all<0>(trow, hi, lo);   // TMEM lanes 0..63: first digit of A
     else tc_fold_all<1>(trow, hi, lo);            // lanes 64..127: second digit
-    tc_fence_before();
-    named_bar(BAR_WORK, TC_WORKERS);
-    if (wt < 64) S.E_acc[wt] = S.E_old[wt];
-    if (wt == 0) S.regrid = 0;
-    named_bar(BAR_WORK, TC_WORKERS);
 }
 
 __global__ void __launch_bounds__(TC_THREADS, 1)
@@ -322,24 +322,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     // sub-chunks are dealt round-robin (CTA b takes b, b + P, b + 2P, ...): at any time the
-    // CTAs stream neighbouring 256-byte pieces of every column, which keeps DRAM pages open.
-    // A CTA takes at most rows_per_cta rows (the fixed-point bounds need <= 2^15).
+    // CTAs stream neighbouring 256-byte pieces of every column.  A CTA takes at most
+    // rows_per_cta rows (the fixed-point bounds need <= 2^15).
     const int64_t subs = (m + TC_SUB - 1) / TC_SUB;
     const int64_t P = gridDim.x;
     const int G = (int64_t)blockIdx.x < subs ? (int)((subs - 1 - blockIdx.x) / P + 1) : 0;
     (void)rows_per_cta;
 
     if (tid == 0) {
-        for (int s = 0; s < TC_SF; ++s) { mbar_init(&S.fp_full[s], 1); mbar_init(&S.fp_empty[s], 1); }
-        for (int s = 0; s < TC_SD; ++s) { mbar_init(&S.dig_full[s], 1); mbar_init(&S.dig_empty[s], 1); }
+        for (int s = 0; s < TC_SF; ++s) { mbar_init(&S.fp_full[s], 1); mbar_init(&S.fp_empty[s], 2 + 16); }
+        for (int s = 0; s < TC_SD; ++s) { mbar_init(&S.dig_full[s], 16); mbar_init(&S.dig_empty[s], 1); }
+        for (int s = 0; s < TC_RD; ++s) { mbar_init(&S.dec_full[s], 2); mbar_init(&S.dec_empty[s], 16); }
         mbar_init(&S.acc_full, 1);
-        mbar_init(&S.acc_empty, 1);
+        mbar_init(&S.acc_empty, 16);
         mbar_fence_init();
         S.abort = 0;
-    }
-    if (tid < 64) {
-        S.E_old[tid] = EXP_EMPTY;
-        S.E_acc[tid] = EXP_EMPTY;
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
@@ -367,8 +364,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
                 if (S.abort) break;
                 mbar_expect_tx(&S.fp_full[f], bytes);
-                tma_load_2d(fpb + (size_t)f * 64 * TC_SUB, &tmapA, (int)(((int64_t)blockIdx.x + (int64_t)g * P) * TC_SUB), 0,
-                            &S.fp_full[f]);
+                tma_load_2d(fpb + (size_t)f * 64 * TC_SUB, &tmapA, (int)(((int64_t)blockIdx.x + (int64_t)g * P) * TC_SUB),
+                            0, &S.fp_full[f]);
                 issued = g + 1;
             }
             tma_issued = issued;
@@ -404,48 +401,88 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             // every MMA issued by this thread has completed once that phase completes
             mma_commit(&S.acc_full);
             (void)mbar_wait(&S.acc_full, period & 1);
-        } else if (warp == 2) {
-            // ---------------- stage waiter: one iteration ahead of the workers it waits for
-            // the FP32 sub-chunk and the digit stage they use next, then joins their exchange
-            // barrier; its waits overlap the workers' split instead of delaying the barrier.
-            if (G > 0) {
+        } else if (warp >= 2) {
+            // ---------------- deciders (warps 2, 3; lane l owns column j = 32 (warp - 2) + l).
+            // For each sub-chunk as soon as it lands: column maxima -> growth class; the two
+            // warps agree on whether a new period starts (an entry needs more than one binade
+            // above the running scale, or the exactness budget is spent) and publish a record.
+            const int dw = warp - 2, j = 32 * dw + lane;
+            int Ecur = EXP_EMPTY, Epend = EXP_EMPTY, Eacc = EXP_EMPTY, period_len = 0;
+            bool bad = false;
+            for (int g = 0; g <= G; ++g) {
+                const int r = g % TC_RD;
                 int fl = 0;
-                if (lane == 0) {
-                    if (!mbar_wait(&S.fp_full[0], 0)) fl |= 4;
-                    if (G > 1 && !mbar_wait(&S.fp_full[1 % TC_SF], (1 / TC_SF) & 1)) fl |= 4;
-                    S.wflags[0][16] = fl;
-                    S.regrid = 0;
-                }
-                named_bar(BAR_XCHG, TC_XCHG);
-                // the workers' first exchange carries no abort bit but this one
-                const int G_run = (S.wflags[0][16] & 4) ? 0 : G;
-                for (int g = 0; g < G_run; ++g) {
-                    fl = 0;
-                    if (lane == 0) {
-                        if (g + 2 < G && !mbar_wait(&S.fp_full[(g + 2) % TC_SF], ((g + 2) / TC_SF) & 1)) fl |= 4;
-                        if (g + 1 < G && g + 1 >= TC_SD &&
-                            !mbar_wait(&S.dig_empty[(g + 1) % TC_SD], (((g + 1) / TC_SD) - 1) & 1))
-                            fl |= 4;
-                        if (S.abort) fl |= 4;
-                        S.wflags[(g + 1) & 1][16] = fl;
+                if (g < G) {
+                    const int f = g % TC_SF;
+                    if (!mbar_wait(&S.fp_full[f], (g / TC_SF) & 1)) fl |= 4;
+                    // max |a| of column j on the bit patterns (Inf / NaN have the largest); the
+                    // lanes start at staggered row quads so each 16-byte load is conflict-free
+                    unsigned mine = 0;
+                    if (j < n) {
+                        const float* col = fpb + (size_t)f * 64 * TC_SUB + (size_t)j * TC_SUB;
+#pragma unroll 4
+                        for (int k = 0; k < 16; ++k) {
+                            const uint4 v = *reinterpret_cast<const uint4*>(col + 4 * ((k + lane) & 15));
+                            mine = max(mine, max(max(v.x & 0x7fffffffu, v.y & 0x7fffffffu),
+                                                 max(v.z & 0x7fffffffu, v.w & 0x7fffffffu)));
+                        }
                     }
-                    named_bar(BAR_XCHG, TC_XCHG);
-                    // the same OR the workers form: everyone leaves the loop together
-                    int F = 0;
-#pragma unroll
-                    for (int w = 0; w < 17; ++w) F |= S.wflags[(g + 1) & 1][w];
-                    if (F & 4) break;
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&S.fp_empty[f]);
+                    if (mine >= 0x7f800000u) bad = true;
+                    const int e = (mine == 0u || mine >= 0x7f800000u) ? EXP_EMPTY : tc_exp_above(__uint_as_float(mine));
+                    // one binade above the running scale is "soft" (top digit in [-256, 256], still
+                    // exact in bf16); more, or a first non-zero entry, is "hard"
+                    if (e != EXP_EMPTY) {
+                        if (Ecur == EXP_EMPTY || e > Ecur + 1) fl |= 2;
+                        else if (e == Ecur + 1) fl |= 1;
+                    }
+                    Epend = max(Epend, e);
                 }
+                if (g >= TC_RD && !mbar_wait(&S.dec_empty[r], ((g / TC_RD) - 1) & 1)) fl |= 4;
+                if (S.abort) fl |= 4;
+                fl = __reduce_or_sync(0xffffffffu, fl);
+                if (lane == 0) S.dflags[g & 1][dw] = fl;
+                named_bar(BAR_DEC, 64);
+                const int F = S.dflags[g & 1][0] | S.dflags[g & 1][1];
+                if (F & 4) {
+                    atomicExch(&S.abort, 1);
+                    break;
+                }
+                // exactness budget of a period: sum |q_s q_t| <= 2^24 grid units per block and
+                // (i, j); a normal sub-chunk adds at most 64 * 128^2 = 2^20 (1 unit), one with a
+                // soft growth 64 * 256^2 = 2^22 (4 units).  g == G closes the last period.
+                const int cost = (F & 1) ? 4 : 1;
+                const bool newp = g == 0 || g == G || (F & 2) || period_len + cost > TC_PERIOD;
+                int dsh = 0;
+                if (newp) {
+                    if (g > 0) {
+                        dsh = Eacc == EXP_EMPTY ? 64 : Ecur - Eacc;  // re-grid of the accumulators
+                        Eacc = Ecur;
+                    }
+                    Ecur = Epend;  // the new period starts on every grown scale
+                    period_len = 1;
+                } else {
+                    period_len += cost;
+                }
+                TcRecord& R = S.rec[r];
+                R.E[j] = Ecur;
+                R.dsh[j] = dsh;
+                const bool rg = __any_sync(0xffffffffu, dsh != 0);
+                if (lane == 0) R.regrid[dw] = rg ? 1 : 0;
+                if (j == 0) R.newp = newp ? 1 : 0;
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&S.dec_full[r]);
             }
+            if (bad) atomicOr(&info->flags, FLAG_NONFINITE);
+            part_E[(size_t)blockIdx.x * 64 + j] = Eacc;
         }
     } else {
-        // ---------------- 16 worker warps: split every sub-chunk, drain every period.
-        // Software-pipelined: iteration g writes the digits of sub-chunk g and reads
-        // sub-chunk g+1 (column maxima, growth class), then one barrier exchanges the
-        // per-warp growth / abort bits.  Warp w splits columns w, w+16, w+32, w+48 (lane l:
-        // rows 2l, 2l+1).  Warp 2 waits on the stage barriers for them.
+        // ---------------- 16 worker warps.  Per sub-chunk: take the record, write the 7 digit
+        // slices of columns w, w+16, w+32, w+48 (lane l: rows 2l, 2l+1), hand the stage to
+        // the MMA; when a period closes, drain TMEM lanes 32 (w % 4).. x columns 16 (w / 4)...
+        // Warps only meet on mbarriers: no CTA-wide barrier until the partials are written.
         asm volatile("setmaxnreg.inc.sync.aligned.u32 112;");
-        const int wt = tid - 128;                  // worker thread 0..511
         const int wq = warp - 4;                   // worker warp 0..15
         const int quad = warp & 3;                 // TMEM lane quadrant of this warp
         const int J0 = 16 * (wq >> 2);             // drain columns J0..J0+15
@@ -453,106 +490,29 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         uint32_t lo[16];
 #pragma unroll
         for (int k = 0; k < 16; ++k) { hi[k] = 0; lo[k] = 0; }
-        int period_len = 1, drained = 0, late = 0, newp = 1, next_newp = 0;
-        bool bad = false, aborted = false;
-        // 2^E as a bit pattern: |a| < 2^E  <=>  bits(|a|) < pattern (E = 128 gives +Inf's)
-        auto set_scale = [&](int j, int E) {
-            S.E_cur[j] = E;
-            S.thr[j] = E == EXP_EMPTY ? 1u : (unsigned)(E + 127) << 23;
-        };
-        if (lane < 4) {
-            set_scale(wq + 16 * lane, EXP_EMPTY);
-            S.E_pend[wq + 16 * lane] = EXP_EMPTY;
-        }
-        __syncwarp();
-
-        // classify sub-chunk gg (already resident) against this warp's running scales.
-        // Fast path: no entry reaches 2^E_cur in any of the warp's columns (one vote).
-        auto load_classify = [&](int gg) -> int {
-            int fl = 0;
-            const float* fp = fpb + (size_t)(gg % TC_SF) * 64 * TC_SUB + 2 * lane;
-            unsigned mb[4];
-            bool grow = false;
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const int j = wq + 16 * c;
-                float2 a2 = make_float2(0.f, 0.f);
-                if (j < n) a2 = *reinterpret_cast<const float2*>(fp + j * TC_SUB);
-                // max |a| on the bit patterns (Inf / NaN have the largest patterns)
-                mb[c] = max(__float_as_uint(a2.x) & 0x7fffffffu, __float_as_uint(a2.y) & 0x7fffffffu);
-                grow |= mb[c] >= S.thr[j];
-            }
-            if (__any_sync(0xffffffffu, grow)) {
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    const int j = wq + 16 * c;
-                    const unsigned m = __reduce_max_sync(0xffffffffu, mb[c]);
-                    if (m >= 0x7f800000u) bad = true;
-                    const int e = (m == 0u || m >= 0x7f800000u) ? EXP_EMPTY : tc_exp_above(__uint_as_float(m));
-                    const int cur = S.E_cur[j];
-                    // one binade above the running scale is "soft" (top digit in [-256, 256], still
-                    // exact in bf16); more, or a first non-zero entry, is "hard": new period
-                    if (e != EXP_EMPTY) {
-                        if (cur == EXP_EMPTY || e > cur + 1) fl |= 2;
-                        else if (e == cur + 1) fl |= 1;
-                    }
-                    if (lane == 0 && e > S.E_pend[j]) S.E_pend[j] = e;
-                }
-            }
-            return fl;
-        };
-        // OR of every worker's bits; slot parity alternates so one barrier suffices
-        auto exchange = [&](int par, int fl, int bar_id, int bar_count) -> int {
-            fl = __reduce_or_sync(0xffffffffu, fl);
-            if (lane == 0) S.wflags[par][wq] = fl;
-            named_bar(bar_id, bar_count);
-            const int4* w4 = reinterpret_cast<const int4*>(S.wflags[par]);
-            int F = S.wflags[par][16];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int4 x = w4[u];
-                F |= x.x | x.y | x.z | x.w;
-            }
-            return F;
-        };
-        // a period ends: record its scales for the drain, start the next on the grown ones
-        auto close_period = [&](bool start_next) {
-            if (lane < 4) {
-                const int j = wq + 16 * lane;
-                const int eo = S.E_cur[j], ea = S.E_acc[j];
-                S.E_old[j] = eo;
-                const int dd = ea == EXP_EMPTY ? 64 : eo - ea;
-                S.dsh[j] = dd;
-                if (dd != 0) S.regrid = 1;
-                if (start_next) set_scale(j, S.E_pend[j]);
-            }
-            __syncwarp();
-        };
-
-        if (G > 0) {
-            named_bar(BAR_XCHG, TC_XCHG);  // the waiter has seen sub-chunks 0 and 1 arrive
-            // (load_classify sets no abort bit: an abort here is the waiter's, which it acts on too)
-            const int F = exchange(0, load_classify(0), BAR_WORK, TC_WORKERS);
-            // sub-chunk 0 opens the first period on the scales just seen
-            if (lane < 4) set_scale(wq + 16 * lane, S.E_pend[wq + 16 * lane]);
-            __syncwarp();
-            if (F & 4) aborted = true;
-        }
-        // g == G only drains the last period
-        for (int g = 0; g <= G && !aborted && G > 0; ++g) {
-            const int d = g % TC_SD;
+        int drained = 0;
+        bool failed = false;
+        for (int g = 0; g <= G; ++g) {
+            const int r = g % TC_RD;
+            bool ok = mbar_wait(&S.dec_full[r], (g / TC_RD) & 1) && !S.abort;
+            if (!__all_sync(0xffffffffu, ok)) { failed = true; break; }
+            const TcRecord& R = S.rec[r];
+            const int newp = R.newp;
             if (g < G) {
-                int fl = late;
+                const int d = g % TC_SD, f = g % TC_SF;
+                ok = (g < TC_SD || mbar_wait(&S.dig_empty[d], ((g / TC_SD) - 1) & 1)) &&
+                     mbar_wait(&S.fp_full[f], (g / TC_SF) & 1);
+                if (!__all_sync(0xffffffffu, ok)) { failed = true; break; }
                 // digits of sub-chunk g: y = 128 a 2^-E (|y| < 128, < 256 after a soft growth);
                 // digit s is y's remainder rounded to the grid 2^-8s (|digit| <= 128 grid units,
                 // exact in bf16: 8 significant bits); the MMA sees digit s scaled by 2^-8s
-                const float* fp = fpb + (size_t)(g % TC_SF) * 64 * TC_SUB + 2 * lane;
+                const float* fp = fpb + (size_t)f * 64 * TC_SUB + 2 * lane;
                 unsigned char* ds = dig + (size_t)d * TC_DIG_BYTES;
                 unsigned long long y[4];
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
                     const int j = wq + 16 * c;
-                    const int E = S.E_cur[j];
+                    const int E = R.E[j];
                     y[c] = 0ull;
                     if (E != EXP_EMPTY) {
                         const float2 a2 = *reinterpret_cast<const float2*>(fp + j * TC_SUB);
@@ -584,38 +544,29 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     }
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                if (g + 1 < G) fl |= load_classify(g + 1);
-                const int F = exchange((g + 1) & 1, fl, BAR_XCHG, TC_XCHG);
-                if (F & 4) { aborted = true; break; }
-                if (wt == 0) {
-                    S.dig_newp[d] = newp;
+                __syncwarp();
+                if (lane == 0) {
+                    S.dig_newp[d] = newp;  // every warp writes the same value
                     mbar_arrive(&S.dig_full[d]);
-                    mbar_arrive(&S.fp_empty[g % TC_SF]);
+                    mbar_arrive(&S.fp_empty[f]);
                 }
-                // exactness budget of a period: sum |q_s q_t| <= 2^24 grid units per block and
-                // (i, j); a normal sub-chunk adds at most 64 * 128^2 = 2^20 (1 unit), one with a
-                // soft growth 64 * 256^2 = 2^22 (4 units)
-                const int cost = (F & 1) ? 4 : 1;
-                next_newp = (g + 1 < G) && ((F & 2) || (period_len + cost > TC_PERIOD));
-                period_len = next_newp ? 1 : period_len + cost;
             }
-            if ((newp && g > 0) || g == G) {
+            if (((newp && g > 0) || g == G) && G > 0) {
                 // the MMA issuer closes a period on seeing the first stage of the next one
                 // (or after the last sub-chunk); drain it
-                if (g == G) close_period(false);
-                if (!mbar_wait(&S.acc_full, drained & 1)) late |= 4;
+                ok = mbar_wait(&S.acc_full, drained & 1);
+                if (!__all_sync(0xffffffffu, ok)) { failed = true; break; }
                 tc_fence_after();
-                if (g == G) named_bar(BAR_WORK, TC_WORKERS);
-                tc_drain(S, tmem, wt, quad, lane, J0, hi, lo);
-                if (wt == 0 && g < G) mbar_arrive(&S.acc_empty);
+                tc_drain(R, tmem, quad, lane, J0, hi, lo);
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0 && g < G) mbar_arrive(&S.acc_empty);
                 ++drained;
             }
-            if (g < G) {
-                if (next_newp) close_period(true);
-                newp = next_newp;
-            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&S.dec_empty[r]);
         }
-        if (bad) atomicOr(&info->flags, FLAG_NONFINITE);
+        if (failed && lane == 0) atomicExch(&S.abort, 1);
         // partials of this CTA: W = sum over blocks (s < t) + 1/2 (s = s); G = W + W^T later.
         // The two digit halves of row i add into the same W(i, j): half 0 first, then half 1.
         const int lanei = quad * 32 + lane, h = lanei >> 6, i = lanei & 63;
@@ -633,8 +584,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             __threadfence_block();
             named_bar(BAR_WORK, TC_WORKERS);
         }
-        if (wt < 64) part_E[(size_t)blockIdx.x * 64 + wt] = S.E_acc[wt];
-        if (aborted || (late & 4)) atomicExch(&S.abort, 1);
     }
     // teardown: every tcgen05 access is complete before the TMEM is freed
     tc_fence_before();
