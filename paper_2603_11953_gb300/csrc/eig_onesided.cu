@@ -18,15 +18,16 @@
 //   3. The pairs are scheduled by the round-robin ("circle") tournament over
 //      a thread-block cluster: each CTA owns P pair slots (one warp per
 //      pair); after each step one column moves to each neighbouring CTA
-//      through distributed shared memory, followed by one cluster barrier.
+//      through distributed shared memory, signalled on the neighbour's
+//      mbarrier (no cluster-wide barrier within a sweep).
 //
-// The rotation angle is estimated in FP32 while the applied rotation is kept
-// orthogonal to FP64 precision (c = rsqrt(1 + t^2) in FP64): an inexact angle
-// only leaves a residual g * O(2^-24) on a pair, which later sweeps remove,
-// whereas a non-orthogonal rotation would change the singular values.  On
-// GB300 every FP64 warp instruction occupies the thin FP64 pipe for tens of
-// cycles, so the divisions and square roots of the angle go to the FP32
-// units.  Squared norms are updated within a sweep by the exact quadratic
+// The rotation angle and (c0, s0) are computed in FP32 while the applied
+// rotation is made orthogonal to FP64 precision by one FP64 correction
+// factor: an inexact angle only leaves a residual g * O(2^-24) on a pair,
+// which later sweeps remove, whereas a non-orthogonal rotation would change
+// the singular values.  On GB300 a dependent FP64 operation costs about 60
+// cycles and an FP64 reciprocal square root about 350, so every division and
+// square root goes to the FP32 units.  Squared norms are updated within a sweep by the exact quadratic
 // form of the rotation, recomputed at the start of every sweep and whenever
 // a norm drops below 1/16 of its previous value; the stopping test of the
 // final, rotation-free sweep therefore uses exact norms.
@@ -141,7 +142,55 @@ __device__ __forceinline__ double warp_sum(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
+__device__ __forceinline__ uint32_t os_smem(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+// Conversions by integer bit operations (the FP64 pipe is the scarce resource):
+// double -> float truncates the significand and flushes values outside the normal
+// float range to 0 / +-max (only angles and heuristics use it); float -> double is
+// exact for normal floats and gives 0 for subnormal ones.
+__device__ __forceinline__ float os_to_float(double x) {
+    const long long b = __double_as_longlong(x);
+    const int ex = (int)((b >> 52) & 0x7ff) - 1023;
+    const unsigned sgn = (unsigned)((unsigned long long)b >> 63) << 31;
+    if (ex < -126) return __uint_as_float(sgn);
+    if (ex > 127) return __uint_as_float(sgn | 0x7f7fffffu);
+    return __uint_as_float(sgn | ((unsigned)(ex + 127) << 23) | (unsigned)((b >> 29) & 0x7fffff));
+}
+__device__ __forceinline__ double os_to_double(float x) {
+    const unsigned b = __float_as_uint(x);
+    const unsigned ex = (b >> 23) & 0xff;
+    if (ex == 0) return 0.0;
+    const unsigned long long d = ((unsigned long long)(b >> 31) << 63) | ((unsigned long long)(ex + 896) << 52) |
+                                 ((unsigned long long)(b & 0x7fffff) << 29);
+    return __longlong_as_double((long long)d);
+}
+__device__ __forceinline__ int os_hi(double x) { return __double2hiint(x); }
+// arrive on an mbarrier of CTA `rank` of the cluster, releasing this thread's prior stores
+__device__ __forceinline__ void os_remote_arrive(const uint64_t* local_bar, int rank) {
+    uint32_t raddr;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(raddr) : "r"(os_smem(local_bar)), "r"(rank));
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(raddr) : "memory");
+}
+// bounded wait (about 1 s of GPU clock) with cluster-scope acquire
+__device__ __forceinline__ bool os_wait(const uint64_t* bar, unsigned parity) {
+    const long long t0 = clock64();
+    for (;;) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(os_smem(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (clock64() - t0 > (1ll << 31)) return false;
+    }
+}
 
+// Each step: every warp rotates its pair; then one column moves to each
+// neighbouring CTA (warp 0 owns the link to the right, warp 1 the link to the
+// left): the sender stores it into the neighbour's receive buffer and arrives
+// on the neighbour's mbarrier; the receiver waits only for its two
+// neighbours, so no cluster-wide barrier is needed within a sweep.
 __global__ void __launch_bounds__(512) onesided_jacobi_kernel(OsParams prm) {
     cg::cluster_group cluster = cg::this_cluster();
     const int C = (int)cluster.num_blocks();
@@ -150,16 +199,28 @@ __global__ void __launch_bounds__(512) onesided_jacobi_kernel(OsParams prm) {
     const int LD = ((n + 2) + 1) & ~1;  // x[0..n-1], idx, nrm
     extern __shared__ double sm[];
     double* bufs = sm;                       // [2P][LD]
-    double* recv = sm + (size_t)2 * P * LD;  // [2 parity][2 side][LD]
-    __shared__ int top_buf[32], bot_buf[32], new_top[32], new_bot[32];
+    double* recv = sm + (size_t)2 * P * LD;  // [2 parity][2 side: 0 from the left, 1 from the right][LD]
+    __shared__ uint64_t rbar[2][2];          // same indexing as recv
+    __shared__ int map_top[2][32], map_bot[2][32];  // slot -> buffer, double-buffered by step parity
     __shared__ int s_rot;
-    __shared__ unsigned long long s_off;     // bits of a non-negative double
     __shared__ int s_cnt[2];                 // used in CTA 0: per-sweep cluster totals
     __shared__ int s_total;
+    __shared__ int s_timeout;
+    __shared__ float s_off[32];              // per warp: the largest scaled |g| left in the sweep
+    __shared__ float s_off_cta;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int N = np - 1;
     const double tol2 = prm.tol * prm.tol;
 
+    if (tid == 0) {
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b)
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], 32;" ::"r"(os_smem(&rbar[a][b])));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_cnt[0] = 0;
+        s_cnt[1] = 0;
+        s_timeout = 0;
+    }
     // initial placement: local top u <- column cP+u, bottom u <- column np-1-cP-u
     for (int u = warp; u < 2 * P; u += blockDim.x / 32) {
         const int col = (u < P) ? c * P + u : np - 1 - c * P - (u - P);
@@ -171,18 +232,19 @@ __global__ void __launch_bounds__(512) onesided_jacobi_kernel(OsParams prm) {
             s2 += v * v;
         }
         s2 = warp_sum(s2);
-        if (lane == 0) { b[n] = (double)col; b[n + 1] = s2; }
+        if (lane == 0) { b[n] = __longlong_as_double((long long)col); b[n + 1] = s2; }
     }
-    if (tid < P) { top_buf[tid] = tid; bot_buf[tid] = P + tid; }
-    if (tid == 0) { s_cnt[0] = 0; s_cnt[1] = 0; s_off = 0ull; }
+    if (tid < P) { map_top[0][tid] = tid; map_bot[0][tid] = P + tid; }
     cluster.sync();
 
     int sweep = 0;
     bool converged = false;
-    unsigned step_par = 0;
+    unsigned K = 0;  // global step counter (parity of buffers and mbarrier phases)
+    float best_off = 0.0f;
     while (sweep < prm.max_sweeps) {
         ++sweep;
-        if (tid == 0) { s_rot = 0; s_off = 0ull; }
+        if (tid == 0) s_rot = 0;
+        best_off = 0.0f;
         // exact squared norms at the start of the sweep
         for (int u = warp; u < 2 * P; u += blockDim.x / 32) {
             double* b = bufs + (size_t)u * LD;
@@ -192,52 +254,70 @@ __global__ void __launch_bounds__(512) onesided_jacobi_kernel(OsParams prm) {
             if (lane == 0) b[n + 1] = s2;
         }
         __syncthreads();
-        for (int k = 0; k < N; ++k) {
-            // one warp per pair: g = x_p^T x_q, the rotation, and its application
+        for (int k = 0; k < N; ++k, ++K) {
+            const int par = (int)(K & 1u);
+            const int* top = map_top[par];
+            const int* bot = map_bot[par];
+            // one warp per pair: g = x_p^T x_q, the rotation, and its application.  Every FP64
+            // warp instruction holds its SMSP's FP64 pipe for about 64 cycles on GB300, so the
+            // scalar work is kept to the few FP64 operations that set the result.
             if (warp < P) {
-                double* xp = bufs + (size_t)top_buf[warp] * LD;
-                double* xq = bufs + (size_t)bot_buf[warp] * LD;
-                double g = 0.0;
-                for (int r = lane; r < n; r += 32) g += xp[r] * xq[r];
-                g = warp_sum(g);
+                double* xp = bufs + (size_t)top[warp] * LD;
+                double* xq = bufs + (size_t)bot[warp] * LD;
                 const double app = xp[n + 1], aqq = xq[n + 1];
-                const bool live = (int)xp[n] < n && (int)xq[n] < n && app > 0.0 && aqq > 0.0;
-                const double g2 = g * g, pq = app * aqq;
-                if (live && lane == 0 && g2 > __longlong_as_double((long long)s_off) * pq)
-                    atomicMax(&s_off, (unsigned long long)__double_as_longlong(g2 / pq));
-                if (live && g != 0.0 && g2 > tol2 * pq) {
+                double g = 0.0;
+                for (int r = lane; r < n; r += 32) g = fma(xp[r], xq[r], g);
+                g = warp_sum(g);
+                // column ids are stored as integer bit patterns; positive doubles have positive
+                // patterns (integer compares keep these tests off the FP64 pipe)
+                const bool live = __double_as_longlong(xp[n]) < n && __double_as_longlong(xq[n]) < n &&
+                                  __double_as_longlong(app) > 0 && __double_as_longlong(aqq) > 0;
+                // the scaled test |g| > tol sqrt(a_pp a_qq), exactly as in FP64
+                const double g2 = g * g;
+                if (live && g2 > tol2 * (app * aqq)) {
                     // Rotation angle from Rutishauser's t = sgn(zeta)/(|zeta| + sqrt(1 + zeta^2)),
-                    // zeta = (a_qq - a_pp) / 2g, evaluated in FP32 (its accuracy only sets how
-                    // far g is reduced); the rotation itself is made orthogonal to FP64
-                    // precision by c = rsqrt(1 + t^2), s = t c computed in FP64.
-                    const float df = (float)(aqq - app), hf = 2.0f * (float)g;
+                    // zeta = (a_qq - a_pp) / 2g, sgn(0) = +1, evaluated in FP32 from ratios <= 1
+                    // (its accuracy only sets how far g is reduced), and c0 = 1/sqrt(1 + t^2),
+                    // s0 = t c0 in FP32.  The applied rotation (c0, s0) f is orthogonal to FP64
+                    // precision: with e = c0^2 + s0^2 - 1 (exact in FP64, |e| ~ 2^-24),
+                    // f = 1 - e/2 + 3e^2/8 = (1 + e)^(-1/2) + O(e^3).
+                    const float df = os_to_float(aqq) - os_to_float(app);
+                    const float hf = 2.0f * os_to_float(g);
+                    const float adf = fabsf(df), ahf = fabsf(hf);
+                    const float sz = (df == 0.0f || (df > 0.0f) == (hf > 0.0f)) ? 1.0f : -1.0f;
                     float tf;
-                    if (df == 0.0f) {
-                        tf = 1.0f;
+                    if (adf >= ahf) {
+                        const float z = ahf / adf;
+                        tf = sz * z / (1.0f + sqrtf(fmaf(z, z, 1.0f)));
                     } else {
-                        const float rf = sqrtf(df * df + hf * hf);
-                        tf = (df > 0.0f ? hf : -hf) / (fabsf(df) + rf);
+                        const float w = adf / ahf;
+                        tf = sz / (w + sqrtf(fmaf(w, w, 1.0f)));
                     }
-                    const double t = (double)tf;
-                    const double cs = rsqrt(1.0 + t * t);
-                    const double sn = t * cs;
+                    const float cf = rsqrtf(fmaf(tf, tf, 1.0f));
+                    const double c0 = os_to_double(cf), s0 = os_to_double(tf * cf);
+                    const double e = fma(c0, c0, fma(s0, s0, -1.0));
+                    const double f = fma(e, fma(e, 0.375, -0.5), 1.0);
+                    const double cs = c0 * f, sn = s0 * f;
                     for (int r = lane; r < n; r += 32) {
                         const double a = xp[r], b = xq[r];
-                        xp[r] = cs * a - sn * b;
-                        xq[r] = sn * a + cs * b;
+                        xp[r] = fma(cs, a, -sn * b);
+                        xq[r] = fma(sn, a, cs * b);
                     }
-                    // ||x_p'||^2 = c^2 a_pp - 2cs g + s^2 a_qq (exact for any angle)
-                    double np2 = cs * cs * app - 2.0 * cs * sn * g + sn * sn * aqq;
-                    double nq2 = sn * sn * app + 2.0 * cs * sn * g + cs * cs * aqq;
+                    // Within a sweep the squared norms only steer later angles and tests; they
+                    // follow the exact-angle update a_pp - t g, a_qq + t g.  Every sweep starts
+                    // from exact norms, and the final sweep (no rotation) uses only those.
+                    const double tg = os_to_double(tf) * g;
+                    double np2 = app - tg, nq2 = aqq + tg;
                     __syncwarp();
-                    if (np2 < 0.0625 * app) {
+                    // a norm that dropped by 16x is recomputed (cancellation in the update)
+                    if (os_hi(np2) < os_hi(app) - (4 << 20)) {
                         double s2 = 0.0;
-                        for (int r = lane; r < n; r += 32) s2 += xp[r] * xp[r];
+                        for (int r = lane; r < n; r += 32) s2 = fma(xp[r], xp[r], s2);
                         np2 = warp_sum(s2);
                     }
-                    if (nq2 < 0.0625 * aqq) {
+                    if (os_hi(nq2) < os_hi(aqq) - (4 << 20)) {
                         double s2 = 0.0;
-                        for (int r = lane; r < n; r += 32) s2 += xq[r] * xq[r];
+                        for (int r = lane; r < n; r += 32) s2 = fma(xq[r], xq[r], s2);
                         nq2 = warp_sum(s2);
                     }
                     __syncwarp();
@@ -246,60 +326,48 @@ __global__ void __launch_bounds__(512) onesided_jacobi_kernel(OsParams prm) {
                         xq[n + 1] = nq2;
                         atomicAdd(&s_rot, 1);
                     }
+                } else if (live && lane == 0) {
+                    // largest scaled |g| among the pairs left alone (informational)
+                    const float rr = os_to_float(g) * rsqrtf(os_to_float(app)) * rsqrtf(os_to_float(aqq));
+                    best_off = fmaxf(best_off, fabsf(rr));
                 }
             }
             __syncthreads();
-            // circle tournament move: slot j -> j+1 (1 <= j <= np-2), slot np-1 -> 1, slot 0 fixed
-            const int par = (int)(step_par & 1u);
-            if (C > 1) {
-                if (c < C - 1 && warp == 0) {  // my last top goes to the next CTA's first top
-                    double* dst = cluster.map_shared_rank(recv + (size_t)(par * 2 + 0) * LD, c + 1);
-                    const double* src = bufs + (size_t)top_buf[P - 1] * LD;
-                    for (int r = lane; r < n + 2; r += 32) dst[r] = src[r];
-                }
-                if (c > 0 && warp == (blockDim.x / 32 > 1 ? 1 : 0)) {  // my first bottom goes left
-                    double* dst = cluster.map_shared_rank(recv + (size_t)(par * 2 + 1) * LD, c - 1);
-                    const double* src = bufs + (size_t)bot_buf[0] * LD;
-                    for (int r = lane; r < n + 2; r += 32) dst[r] = src[r];
-                }
-                cluster.sync();
+            // circle tournament move: slot j -> j+1 (1 <= j <= np-2), slot np-1 -> 1, slot 0 fixed.
+            // The buffer sent away on each link is reused for the column received on it.
+            const int free_a = top[P - 1];  // sent to the right (when there is a right neighbour)
+            const int free_b = bot[0];      // sent to the left
+            const unsigned ph = (K >> 1) & 1u;
+            if (warp == 0 && c < C - 1) {
+                double* dst = cluster.map_shared_rank(recv + (size_t)(par * 2 + 0) * LD, c + 1);
+                const double* src = bufs + (size_t)free_a * LD;
+                for (int r = lane; r < n + 2; r += 32) dst[r] = src[r];
+                os_remote_arrive(&rbar[par][0], c + 1);
+                if (!os_wait(&rbar[par][1], ph)) s_timeout = 1;
+                const double* rs = recv + (size_t)(par * 2 + 1) * LD;
+                double* rd = bufs + (size_t)free_a * LD;
+                for (int r = lane; r < n + 2; r += 32) rd[r] = rs[r];
+            }
+            if (warp == 1 && c > 0) {
+                double* dst = cluster.map_shared_rank(recv + (size_t)(par * 2 + 1) * LD, c - 1);
+                const double* src = bufs + (size_t)free_b * LD;
+                for (int r = lane; r < n + 2; r += 32) dst[r] = src[r];
+                os_remote_arrive(&rbar[par][1], c - 1);
+                if (!os_wait(&rbar[par][0], ph)) s_timeout = 1;
+                const double* rs = recv + (size_t)(par * 2 + 0) * LD;
+                double* rd = bufs + (size_t)free_b * LD;
+                for (int r = lane; r < n + 2; r += 32) rd[r] = rs[r];
             }
             if (tid == 0) {
-                // new tops
-                if (c == 0) {
-                    new_top[0] = top_buf[0];
-                    new_top[1] = bot_buf[0];
-                    for (int u = 2; u < P; ++u) new_top[u] = top_buf[u - 1];
-                } else {
-                    new_top[0] = -1;  // received from the left
-                    for (int u = 1; u < P; ++u) new_top[u] = top_buf[u - 1];
-                }
-                // new bottoms
-                for (int u = 0; u < P - 1; ++u) new_bot[u] = bot_buf[u + 1];
-                new_bot[P - 1] = (c == C - 1) ? top_buf[P - 1] : -2;  // -2: received from the right
-                // free buffers: what was sent away
-                int free_a = -1, free_b = -1;
-                if (c < C - 1) free_a = top_buf[P - 1];
-                if (c > 0) free_b = bot_buf[0];
-                if (new_top[0] == -1) new_top[0] = (free_b >= 0) ? free_b : free_a;
-                if (new_bot[P - 1] == -2) new_bot[P - 1] = (free_a >= 0) ? free_a : free_b;
-                for (int u = 0; u < P; ++u) { top_buf[u] = new_top[u]; bot_buf[u] = new_bot[u]; }
+                int* nt = map_top[par ^ 1];
+                int* nb = map_bot[par ^ 1];
+                nt[0] = (c == 0) ? top[0] : free_b;
+                nt[1] = (c == 0) ? bot[0] : top[0];
+                for (int u = 2; u < P; ++u) nt[u] = top[u - 1];
+                for (int u = 0; u < P - 1; ++u) nb[u] = bot[u + 1];
+                nb[P - 1] = (c == C - 1) ? top[P - 1] : free_a;
             }
             __syncthreads();
-            if (C > 1) {
-                if (c > 0 && warp == 0) {
-                    const double* src = recv + (size_t)(par * 2 + 0) * LD;
-                    double* dst = bufs + (size_t)top_buf[0] * LD;
-                    for (int r = lane; r < n + 2; r += 32) dst[r] = src[r];
-                }
-                if (c < C - 1 && warp == (blockDim.x / 32 > 1 ? 1 : 0)) {
-                    const double* src = recv + (size_t)(par * 2 + 1) * LD;
-                    double* dst = bufs + (size_t)bot_buf[P - 1] * LD;
-                    for (int r = lane; r < n + 2; r += 32) dst[r] = src[r];
-                }
-                __syncthreads();
-            }
-            ++step_par;
         }
         // cluster-wide rotation count of this sweep
         const int sp = sweep & 1;
@@ -320,7 +388,7 @@ __global__ void __launch_bounds__(512) onesided_jacobi_kernel(OsParams prm) {
     // outputs: lambda_j = ||x_j||^2, v_j = P^T x_j / ||x_j||
     for (int u = warp; u < 2 * P; u += blockDim.x / 32) {
         const double* b = bufs + (size_t)u * LD;
-        const int j = (int)b[n];
+        const int j = (int)__double_as_longlong(b[n]);
         if (j >= n) continue;
         double s2 = 0.0;
         for (int r = lane; r < n; r += 32) s2 += b[r] * b[r];
@@ -331,23 +399,32 @@ __global__ void __launch_bounds__(512) onesided_jacobi_kernel(OsParams prm) {
         if (lane == 0) prm.lam[j] = s2;
     }
     // info: sweeps and the largest scaled |g| seen in the last sweep
+    if (lane == 0 && warp < 32) s_off[warp] = best_off;
+    __syncthreads();
     if (tid == 0) {
-        unsigned long long* off0 = cluster.map_shared_rank(&s_off, 0);
-        if (c != 0) atomicMax(off0, s_off);
+        float off = 0.0f;
+        for (int w = 0; w < P && w < 32; ++w) off = fmaxf(off, s_off[w]);
+        s_off_cta = off;
     }
     cluster.sync();
     if (c == 0 && tid == 0) {
+        float off = 0.0f;
+        for (int r = 0; r < C; ++r) off = fmaxf(off, *cluster.map_shared_rank(&s_off_cta, r));
         prm.info->sweeps = sweep;
-        prm.info->off_norm = sqrt(__longlong_as_double((long long)s_off));
+        prm.info->off_norm = (double)off;
         if (!converged) atomicOr(&prm.info->flags, FLAG_NO_CONVERGENCE);
     }
+    if (s_timeout && tid == 0) atomicOr(&prm.info->flags, FLAG_TIMEOUT);
+    cluster.sync();  // no CTA leaves while a neighbour may still read its shared memory
 }
 
-int cluster_size_for(int n) {
+// The FP64 pipe of one SM sets the pace, so the pairs are spread over as many
+// SMs as a cluster allows (16 needs the non-portable cluster size; 8 otherwise).
+int cluster_size_for(int n, bool allow16) {
     if (n <= 8) return 1;
     if (n <= 16) return 2;
-    if (n <= 32) return 4;
-    return 8;
+    if (n <= 32) return allow16 ? 8 : 4;
+    return allow16 ? 16 : 8;
 }
 
 }  // namespace
@@ -368,7 +445,10 @@ cudaError_t launch_eig_onesided(const double* M, int n, int64_t ldm, double tol,
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
 
-    const int C = cluster_size_for(n);
+    const bool allow16 =
+        cudaFuncSetAttribute(onesided_jacobi_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess;
+    if (!allow16) (void)cudaGetLastError();
+    int C = cluster_size_for(n, allow16);
     int np = ((n < 4 ? 4 : n) + 4 * C - 1) / (4 * C) * (4 * C);
     const int P = np / (2 * C);
     const int LD = ((n + 2) + 1) & ~1;
@@ -390,6 +470,22 @@ cudaError_t launch_eig_onesided(const double* M, int n, int64_t ldm, double tol,
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     e = cudaLaunchKernelEx(&cfg, onesided_jacobi_kernel, prm);
+    if (e != cudaSuccess && C == 16) {
+        // the device may not schedule a 16-CTA cluster: the portable size instead
+        (void)cudaGetLastError();
+        C = 8;
+        np = ((n < 4 ? 4 : n) + 4 * C - 1) / (4 * C) * (4 * C);
+        prm.np = np;
+        prm.P = np / (2 * C);
+        const size_t smem8 = sizeof(double) * ((size_t)2 * prm.P * LD + (size_t)4 * LD);
+        e = cudaFuncSetAttribute(onesided_jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem8);
+        if (e != cudaSuccess) return e;
+        cfg.gridDim = dim3(C, 1, 1);
+        cfg.blockDim = dim3(32 * (prm.P < 2 ? 2 : prm.P), 1, 1);
+        cfg.dynamicSmemBytes = smem8;
+        attr[0].val.clusterDim.x = C;
+        e = cudaLaunchKernelEx(&cfg, onesided_jacobi_kernel, prm);
+    }
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
