@@ -80,6 +80,9 @@ typedef struct {
                               input cannot be TMA-loaded), 1 = plain FP64 Gram,
                               2 = Ozaki-BF16 Gram on mma.sync (comparison) */
     int timing;            /* 1 = record per-stage CUDA events (tsvd_last_stage_ms) */
+    int u_variant;         /* 0 = U = A W on tcgen05 in a 3-term TF32 split when the input
+                              can be TMA-loaded (FP32, n <= 64), else CUDA cores;
+                              1 = CUDA-core FP32 kernel */
 } tsvd_opts;
 
 /* Per-call numeric report (written asynchronously by the device). */

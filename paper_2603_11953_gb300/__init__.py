@@ -33,7 +33,7 @@ class tsvd_opts(ctypes.Structure):
                 ("jacobi_tol", ctypes.c_double), ("max_sweeps", ctypes.c_int),
                 ("eig_variant", ctypes.c_int), ("autotune", ctypes.c_int),
                 ("timeout_cycles", ctypes.c_longlong), ("gram_variant", ctypes.c_int),
-                ("timing", ctypes.c_int)]
+                ("timing", ctypes.c_int), ("u_variant", ctypes.c_int)]
 
 
 class tsvd_info(ctypes.Structure):

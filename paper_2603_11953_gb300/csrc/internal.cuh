@@ -97,6 +97,10 @@ cudaError_t launch_compute_u(const void* A, int working, int64_t m, int n, int64
 // Streaming FP32 U kernel (bulk-copy pipeline, packed FMA); requires
 // compute_u_v2_ok(): FP32, n <= 64, 16-byte aligned columns, m % 4 == 0.
 bool compute_u_v2_ok(const void* A, int working, int64_t m, int n, int64_t lda, const void* U, int64_t ldu);
+// tcgen05 U (3-term TF32 split): FP32, n <= 64, TMA-loadable A.
+bool compute_u_tc_ok(const void* A, int working, int64_t m, int n, int64_t lda);
+cudaError_t launch_compute_u_tc(const float* A, int64_t m, int n, int64_t lda, const float* W, float* U,
+                                int64_t ldu, int sm_count, DevInfo* info, cudaStream_t s);
 cudaError_t launch_compute_u_v2(const float* A, int64_t m, int n, int64_t lda, const float* W, float* U,
                                 int64_t ldu, int sm_count, DevInfo* info, cudaStream_t s);
 

@@ -170,7 +170,10 @@ tsvd_status solve_one(tsvd_ctx* h, const void* A, int64_t m, int n, int64_t lda,
     if (e != cudaSuccess) return from_cuda(e);
     if (timed) record(h, 2);
     if (U) {
-        if (compute_u_v2_ok(A, working, m, n, lda, U, ldu))
+        if (h->opts.u_variant == 0 && compute_u_tc_ok(A, working, m, n, lda))
+            e = launch_compute_u_tc(static_cast<const float*>(A), m, n, lda, static_cast<const float*>(W),
+                                    static_cast<float*>(U), ldu, h->sm_count, h->dinfo, h->stream);
+        else if (compute_u_v2_ok(A, working, m, n, lda, U, ldu))
             e = launch_compute_u_v2(static_cast<const float*>(A), m, n, lda, static_cast<const float*>(W),
                                     static_cast<float*>(U), ldu, h->sm_count, h->dinfo, h->stream);
         else
@@ -217,6 +220,7 @@ tsvd_status tsvd_create(tsvd_handle* out, int device, void* stream, const tsvd_o
         if (opts->split_k < 0 || opts->max_sweeps < 0 || opts->jacobi_tol < 0.0) return TSVD_ERR_ARG;
         if (opts->eig_variant < 0 || opts->eig_variant > 2) return TSVD_ERR_UNSUPPORTED;
         if (opts->gram_variant < 0 || opts->gram_variant > 2) return TSVD_ERR_ARG;
+        if (opts->u_variant < 0 || opts->u_variant > 1) return TSVD_ERR_ARG;
     }
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {

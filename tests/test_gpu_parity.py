@@ -8,7 +8,11 @@ Tolerances (each derived in the design doc):
     <= 32 n u_h kappa(C), C = D^-1 M D^-1.
   * sigma end to end, FP32 working: |sigma - sigma_oracle| <= 2 u_32 sigma_oracle
     (the higher-precision errors are far below one FP32 ulp for kappa(B) <= 1e3).
-  * U (eq. (AV-0)): |U - RN_32(A W)| <= (n + 1) u_32 (|A| |W|), W = RN_32(V / sigma).
+  * U (eq. (AV-0)): |U - RN_32(A W)| <= (n + 13) u_32 (|A| |W|), W = RN_32(V / sigma):
+    the FP32 dot-product bound (n + 1) u_32 plus 12 u_32 for the 3-term TF32 split
+    of the tensor-core kernel (each rounded low part and the dropped lo x lo term
+    contribute at most 2^-22 |a||w| per product); the CUDA-core kernel (u_variant 1)
+    is held to (n + 1) u_32.
 """
 import math
 
@@ -185,13 +189,13 @@ def test_eig_matches_oracle_jacobi(n, kappa, logd, variant):
 
 
 # ------------------------------------------------------------------ solve (a1-a7)
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1])  # 0: defaults (tensor-core U); 1: two-sided Jacobi, CUDA-core U
 @pytest.mark.parametrize("m,n,kappa,logd", [(20000, 16, 1e3, 3.0), (5000, 1, 1.0, 0.0), (16, 16, 1e2, 1.0),
                                             (12345, 33, 1e3, 3.0), (65537, 64, 1e3, 3.0),
-                                            (40964, 64, 1e3, 3.0)])
+                                            (40964, 64, 1e3, 3.0), (300, 64, 1e2, 2.0)])
 def test_solve_matches_oracle(m, n, kappa, logd, variant):
     A, _ = workloads.small_case(m, n, kappa_sigma=kappa, logd=logd, seed=5 * m + n, device="cuda")
-    h = handle(eig_variant=variant) if variant else None
+    h = handle(eig_variant=variant, u_variant=1) if variant else None
     sig, V, U, st, sweeps = gpu_solve(A, m, n, m, h=h)
     if h is not None:
         T.tsvd_destroy(h)
@@ -210,7 +214,8 @@ def test_solve_matches_oracle(m, n, kappa, logd, variant):
     W = (V.astype(np.float32) / sig.astype(np.float32)).astype(np.float64)
     rows = np.unique(np.concatenate([np.arange(min(m, 64)), np.linspace(0, m - 1, 200).astype(np.int64)]))
     Uref = oracle.rows_times(A_np, W, rows, 24)
-    bound = (n + 1) * U32 * (np.abs(A_np[rows].astype(np.float64)) @ np.abs(W)) + 1e-38
+    slack = 1 if variant else 13
+    bound = (n + slack) * U32 * (np.abs(A_np[rows].astype(np.float64)) @ np.abs(W)) + 1e-38
     assert np.all(np.abs(U[rows] - Uref) <= bound)
     # Remark 1: U is orthonormal to O(u) + O(u_h) kappa^2(B)
     orth = np.abs(U.T @ U - np.eye(n)).max()
@@ -297,7 +302,7 @@ def test_full_size_sampled(name):
     rows = np.unique(np.concatenate([[0, 1, m - 1], rng.integers(0, m, 61)]))
     A_rows = A[torch.from_numpy(rows).cuda()].cpu().numpy()
     Uref = oracle.rows_times(np.asfortranarray(A_rows), W, np.arange(len(rows)), 24)
-    bound = (n + 1) * U32 * (np.abs(A_rows.astype(np.float64)) @ np.abs(W)) + 1e-38
+    bound = (n + 13) * U32 * (np.abs(A_rows.astype(np.float64)) @ np.abs(W)) + 1e-38
     assert np.all(np.abs(U[rows] - Uref) <= bound)
     Ut = torch.from_numpy(U).cuda()
     orth = (Ut.T @ Ut - torch.eye(n, dtype=torch.float64, device="cuda")).abs().max().item()
