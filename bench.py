@@ -29,7 +29,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "A GB/s per thin SVD, mixed vs all-FP64 on GB300, sigma rel err≤1e-5; %HBM peak"
 DEFAULT_WORKLOAD = "ozaki_4194304x64_fp32"
-KERNELS_PER_STEP = 6  # gram_ozaki, gram_combine, jacobi, finish, compute_u, finalize_info
+# gram_tc, gram_combine, chol_piv, onesided_jacobi, finish, compute_u_tc, finalize_info
+KERNELS_PER_STEP = 7
+FP64_DFMA_PER_CLK_SM = 1.68  # measured on GB300: 16 warps x independent DFMA chains, one SM
 
 
 def peaks():
@@ -180,6 +182,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-rows", type=int, default=32768)
     ap.add_argument("--ref-rows", type=int, default=16384)
+    ap.add_argument("--rows", type=int, default=0,
+                    help="smaller m of the same workload (profiling captures); 0 = the workload's m")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -194,14 +198,15 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     spec = workloads.CONFIGS[args.workload]
-    m, n = spec.m, spec.n
-    A, meta = workloads.make_config(spec, device=dev, seed_offset=rank)
+    m, n = (args.rows if args.rows > 0 else spec.m), spec.n
+    A, meta = workloads.make_config(spec, device=dev, seed_offset=rank, m=m)
     esize = A.element_size()
     working = T.TSVD_FP32 if spec.dtype == torch.float32 else T.TSVD_FP64
     higher = T.TSVD_FP64 if working == T.TSVD_FP32 else T.TSVD_DD
     wdt = spec.dtype
     stream = torch.cuda.current_stream(dev)
-    h, _ = T.tsvd_create(local, stream.cuda_stream, T.tsvd_opts(timing=1))
+    # per-stage events of every timed call (averaged over the timed region below)
+    h, _ = T.tsvd_create(local, stream.cuda_stream, T.tsvd_opts(timing=max(3, min(args.steps, 1024))))
     sigma = torch.zeros(n, dtype=wdt, device=dev)
     V = torch.zeros(n, n, dtype=wdt, device=dev)
     U = torch.zeros(n, m, dtype=wdt, device=dev)
@@ -214,12 +219,6 @@ def main():
         step()
     torch.cuda.synchronize(dev)
     status = int(info[0].item())
-    # per-stage device times of single steps (events on the library's stream)
-    stage = []
-    for _ in range(3):
-        step()
-        stage.append(T.tsvd_last_stage_ms(h))
-    stage_ms = [statistics.median(s[k] for s in stage) for k in range(4)]
 
     barrier(world)
     torch.cuda.synchronize(dev)
@@ -232,6 +231,9 @@ def main():
         torch.cuda.synchronize(dev)
     barrier(world)
     ms_total = ev0.elapsed_time(ev1)
+    # per-stage device times averaged over the timed steps (events the library recorded on
+    # its stream around each stage of each call)
+    stage_ms = T.tsvd_stage_ms_mean(h, min(args.steps, 1024))
     ms_total = max_over_ranks(ms_total, world, dev)
     ms_step = ms_total / args.steps
     bytes_A = m * n * esize
@@ -300,14 +302,19 @@ def main():
     u_bytes = 2.0 * bytes_A
     # FP64 work of one Jacobi pass is data dependent; count it from the sweeps reported
     sweeps = int(info[1].item())
-    jac_flops = sweeps * (n - 1 + (n & 1)) * ((n + 1) // 2) * (12 * n + 30)
-    fp64_peak_1sm = 2 * 2 * pk["sm_max_mhz"] * 1e6 / 1e9  # GFLOP/s of one SM (2 DFMA/clk)
+    # algorithmic FP64 flops of the n x n stage: pivoted Cholesky n^3/3, then per sweep every
+    # pair's dot product (2n) and rotation (6n), counted as if every pair rotated
+    jac_flops = n ** 3 / 3.0 + sweeps * (n * (n - 1) // 2) * 8 * n
+    # FP64 peak of the SMs the n x n stage uses: a 16-CTA cluster (8 for n <= 32), one CTA per
+    # SM, at the measured 1.68 DFMA lanes per clock per SM (2 flops each)
+    eig_sms = 16 if n > 32 else 8 if n > 16 else 2 if n > 8 else 1
+    fp64_peak = eig_sms * 2 * FP64_DFMA_PER_CLK_SM * pk["sm_max_mhz"] * 1e6 / 1e9
     cands = {
         "gram": (gram_ms, {"bound": "tensor", "achieved": gram_flops / (gram_ms * 1e-3) / 1e12,
                            "peak": pk["bf16_sus"], "unit": "TFLOP/s",
                            "hbm_gbs": gram_bytes / (gram_ms * 1e-3) / 1e9}),
         "jacobi": (eig_ms, {"bound": "alu", "achieved": jac_flops / (eig_ms * 1e-3) / 1e9,
-                            "peak": fp64_peak_1sm, "unit": "GFLOP/s"}),
+                            "peak": fp64_peak, "unit": "GFLOP/s"}),
         "compute_u": (u_ms, {"bound": "hbm", "achieved": u_bytes / (u_ms * 1e-3) / 1e9,
                              "peak": pk["hbm"], "unit": "GB/s"}),
     }

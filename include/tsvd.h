@@ -79,7 +79,8 @@ typedef struct {
     int gram_variant;      /* 0 = Ozaki-BF16 Gram on tcgen05/TMEM (mma.sync when the
                               input cannot be TMA-loaded), 1 = plain FP64 Gram,
                               2 = Ozaki-BF16 Gram on mma.sync (comparison) */
-    int timing;            /* 1 = record per-stage CUDA events (tsvd_last_stage_ms) */
+    int timing;            /* k >= 1: record per-stage CUDA events of the last k calls
+                              (k <= TSVD_MAX_TIMED; tsvd_last_stage_ms, tsvd_stage_ms_mean) */
     int u_variant;         /* 0 = U = A W on tcgen05 in a 3-term TF32 split when the input
                               can be TMA-loaded (FP32, n <= 64), else CUDA cores;
                               1 = CUDA-core FP32 kernel */
@@ -160,6 +161,12 @@ TSVD_API tsvd_status tsvd_sync_status(tsvd_handle h);
  * sort, cast), ms[2] compute U, ms[3] total.  Synchronises the stream.
  * These are the components of the paper's time breakdown (Sec. 4.1.2). */
 TSVD_API tsvd_status tsvd_last_stage_ms(tsvd_handle h, float ms[4]);
+
+/* Mean per-stage device times (same layout as tsvd_last_stage_ms) over the
+ * last `last` timed calls (1 <= last <= min(calls so far, opts.timing)).
+ * Synchronises on the recorded events only.  TSVD_ERR_ARG otherwise. */
+#define TSVD_MAX_TIMED 1024
+TSVD_API tsvd_status tsvd_stage_ms_mean(tsvd_handle h, int last, float ms[4]);
 
 /* Size of the one device array that tsvd_gram_static works in (16 MiB). */
 #define TSVD_GRAM_STATIC_SCRATCH_BYTES ((size_t)16 << 20)

@@ -25,7 +25,7 @@ TSVD_FP32, TSVD_FP64, TSVD_DD = 0, 1, 2
 
 EXPORTED = ["tsvd_create", "tsvd_destroy", "tsvd_status_string", "tsvd_gram", "tsvd_eig",
             "tsvd_solve", "tsvd_batch_solve", "tsvd_sync_status", "tsvd_last_stage_ms",
-            "tsvd_gram_static"]
+            "tsvd_stage_ms_mean", "tsvd_gram_static"]
 
 
 class tsvd_opts(ctypes.Structure):
@@ -166,4 +166,10 @@ def tsvd_sync_status(h) -> int:
 def tsvd_last_stage_ms(h):
     out = (ctypes.c_float * 4)()
     _check("tsvd_last_stage_ms", load_library().tsvd_last_stage_ms(h, out))
+    return list(out)
+
+
+def tsvd_stage_ms_mean(h, last):
+    out = (ctypes.c_float * 4)()
+    _check("tsvd_stage_ms_mean", load_library().tsvd_stage_ms_mean(h, int(last), out))
     return list(out)

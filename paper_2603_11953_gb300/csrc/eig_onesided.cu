@@ -43,83 +43,74 @@ namespace tsvd {
 namespace {
 
 // ---------------------------------------------------------------- pivoted Cholesky
-// One CTA.  M (n x n, ldm) -> X = R^T (n x n, ld n, lower triangular) and perm.
+// One CTA.  M (n x n, ldm) -> X = R^T (n x n, ld n, lower triangular, rows in pivot
+// order) and perm (pivot position -> original index).  Nothing is swapped in memory:
+// the trailing matrix stays in the original index order and the pivot order lives
+// in a permutation, so each step needs two barriers.  Every warp finds the pivot
+// itself (the largest remaining diagonal, lowest position on ties).
 __global__ void __launch_bounds__(256)
     chol_piv_kernel(const double* __restrict__ M, int n, int64_t ldm, double* __restrict__ X,
                     int* __restrict__ perm_out, DevInfo* info) {
-    extern __shared__ double sa[];  // [n][n] working copy (trailing Schur complement)
-    __shared__ int perm[256];
-    __shared__ int s_piv;
-    __shared__ double s_d;
-    const int tid = threadIdx.x, nt = blockDim.x;
+    extern __shared__ double sa[];  // [n][n] trailing Schur complement (original indices), then R rows
+    double* Rr = sa + (size_t)n * n;  // [n][n]: row k of R by original column index
+    __shared__ int perm[2][64];
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
     for (int idx = tid; idx < n * n; idx += nt) {
         const int r = idx % n, c = idx / n;
         sa[idx] = M[r + (size_t)c * ldm];
-        X[idx] = 0.0;
+        Rr[idx] = 0.0;
     }
-    for (int i = tid; i < n; i += nt) perm[i] = i;
+    if (tid < 64) perm[0][tid] = tid;
     __syncthreads();
     bool deficient = false;
+    int kend = n;
     for (int k = 0; k < n; ++k) {
-        if (tid < 32) {  // pivot: largest remaining diagonal (lowest index on ties)
-            // the bit patterns of non-negative doubles order like the values, and
-            // every negative value (rank deficiency) sorts below them as a signed int
-            long long best = LLONG_MIN;
-            int bi = k;
-            for (int i = k + tid; i < n; i += 32) {
-                const long long d = __double_as_longlong(sa[i + (size_t)i * n]);
-                const long long key = d < 0 ? LLONG_MIN + 1 : d;
-                if (key > best) { best = key; bi = i; }
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                const long long ob = __shfl_xor_sync(0xffffffffu, best, o);
-                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-            }
-            if (tid == 0) { s_piv = bi; s_d = sa[bi + (size_t)bi * n]; }
+        const int* pc = perm[k & 1];
+        int* pn = perm[(k & 1) ^ 1];
+        // pivot: largest remaining diagonal.  The bit patterns of non-negative doubles order
+        // like the values; every negative value (rank deficiency) sorts below them.
+        long long best = LLONG_MIN;
+        int bq = k;
+        for (int q = k + lane; q < n; q += 32) {
+            const int o = pc[q];
+            const long long dd = __double_as_longlong(sa[o + (size_t)o * n]);
+            const long long key = dd < 0 ? LLONG_MIN + 1 : dd;
+            if (key > best) { best = key; bq = q; }
         }
-        __syncthreads();
-        const int p = s_piv;
-        const double d = s_d;
-        if (!(d > 0.0)) { deficient = true; break; }
-        if (p != k) {  // symmetric swap of rows/cols k and p (trailing block) and of R's columns
-            for (int i = tid; i < n; i += nt) {
-                if (i >= k) {
-                    const double a = sa[k + (size_t)i * n], b = sa[p + (size_t)i * n];
-                    sa[k + (size_t)i * n] = b;
-                    sa[p + (size_t)i * n] = a;
-                }
-            }
-            __syncthreads();
-            for (int i = tid; i < n; i += nt) {
-                if (i >= k) {
-                    const double a = sa[i + (size_t)k * n], b = sa[i + (size_t)p * n];
-                    sa[i + (size_t)k * n] = b;
-                    sa[i + (size_t)p * n] = a;
-                }
-                if (i < k) {  // X = R^T: row k and row p of X, columns < k
-                    const double a = X[k + (size_t)i * n], b = X[p + (size_t)i * n];
-                    X[k + (size_t)i * n] = b;
-                    X[p + (size_t)i * n] = a;
-                }
-            }
-            if (tid == 0) { const int t = perm[k]; perm[k] = perm[p]; perm[p] = t; }
-            __syncthreads();
+        for (int off = 16; off > 0; off >>= 1) {
+            const long long ob = __shfl_xor_sync(0xffffffffu, best, off);
+            const int oq = __shfl_xor_sync(0xffffffffu, bq, off);
+            if (ob > best || (ob == best && oq < bq)) { best = ob; bq = oq; }
         }
+        const int ok = pc[bq];
+        const double d = sa[ok + (size_t)ok * n];
+        if (!(d > 0.0)) { deficient = true; kend = k; break; }
+        // the permutation with positions k and bq exchanged
+        if (tid < n) pn[tid] = (tid == k) ? ok : (tid == bq) ? pc[k] : pc[tid];
         const double rinv = rsqrt(d);  // 1 / r_kk
-        // R[k][j] = A[k][j] / r_kk for j >= k, stored as X[j][k]
-        for (int j = k + tid; j < n; j += nt)
-            X[j + (size_t)k * n] = (j == k) ? d * rinv : sa[k + (size_t)j * n] * rinv;
+        // row k of R: R[k][o] = S[ok][o] / r_kk over the remaining original indices o
+        for (int t = tid; t < n - k; t += nt) {
+            const int q = k + t;
+            const int o = (q == k) ? ok : (q == bq) ? pc[k] : pc[q];
+            Rr[(size_t)k * n + o] = (q == k) ? d * rinv : sa[ok + (size_t)o * n] * rinv;
+        }
         __syncthreads();
-        // trailing update A[i][j] -= R[k][i] R[k][j], i, j > k
+        // trailing update S[a][b] -= R[k][a] R[k][b] over the remaining positions > k
         const int rem = n - k - 1;
+        const double* rk = Rr + (size_t)k * n;
         for (int idx = tid; idx < rem * rem; idx += nt) {
-            const int i = k + 1 + idx % rem, j = k + 1 + idx / rem;
-            sa[i + (size_t)j * n] -= X[i + (size_t)k * n] * X[j + (size_t)k * n];
+            const int oa = pn[k + 1 + idx % rem], ob = pn[k + 1 + idx / rem];
+            sa[oa + (size_t)ob * n] -= rk[oa] * rk[ob];
         }
         __syncthreads();
     }
-    for (int i = tid; i < n; i += nt) perm_out[i] = perm[i];
+    // X = R^T with rows in pivot order: X[pos][c] = R[c][perm[pos]] for pos >= c
+    const int* pf = perm[kend & 1];
+    for (int idx = tid; idx < n * n; idx += nt) {
+        const int pos = idx % n, c = idx / n;
+        X[idx] = (pos >= c && c < kend) ? Rr[(size_t)c * n + pf[pos]] : 0.0;
+    }
+    for (int i = tid; i < n; i += nt) perm_out[i] = pf[i];
     if (tid == 0 && deficient) atomicOr(&info->flags, FLAG_NOT_FULL_RANK);
 }
 
@@ -164,7 +155,8 @@ __device__ __forceinline__ double os_to_double(float x) {
     return __longlong_as_double((long long)d);
 }
 __device__ __forceinline__ int os_hi(double x) { return __double2hiint(x); }
-// arrive on an mbarrier of CTA `rank` of the cluster, releasing this thread's prior stores
+// arrive on an mbarrier of CTA `rank` of the cluster, releasing the prior stores of this
+// thread and of the warp lanes it has synchronised with (__syncwarp)
 __device__ __forceinline__ void os_remote_arrive(const uint64_t* local_bar, int rank) {
     uint32_t raddr;
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(raddr) : "r"(os_smem(local_bar)), "r"(rank));
@@ -211,11 +203,12 @@ __global__ void __launch_bounds__(512) onesided_jacobi_kernel(OsParams prm) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int N = np - 1;
     const double tol2 = prm.tol * prm.tol;
+    const float tol_f = (float)prm.tol;
 
     if (tid == 0) {
         for (int a = 0; a < 2; ++a)
             for (int b = 0; b < 2; ++b)
-                asm volatile("mbarrier.init.shared::cta.b64 [%0], 32;" ::"r"(os_smem(&rbar[a][b])));
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(os_smem(&rbar[a][b])));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_cnt[0] = 0;
         s_cnt[1] = 0;
@@ -272,9 +265,21 @@ __global__ void __launch_bounds__(512) onesided_jacobi_kernel(OsParams prm) {
                 // patterns (integer compares keep these tests off the FP64 pipe)
                 const bool live = __double_as_longlong(xp[n]) < n && __double_as_longlong(xq[n]) < n &&
                                   __double_as_longlong(app) > 0 && __double_as_longlong(aqq) > 0;
-                // the scaled test |g| > tol sqrt(a_pp a_qq), exactly as in FP64
-                const double g2 = g * g;
-                if (live && g2 > tol2 * (app * aqq)) {
+                // the scaled test |g| > tol sqrt(a_pp a_qq): decided in FP32 when the FP32 ratio
+                // is clearly on one side (factor 4), exactly in FP64 otherwise
+                bool rot = false;
+                if (live && g != 0.0) {
+                    const float gf = fabsf(os_to_float(g)), af = os_to_float(app), bf = os_to_float(aqq);
+                    // all three well inside the FP32 range: r = |g| / sqrt(a_pp a_qq) to ~2^-22
+                    const bool in_range = af > 1e-30f && af < 1e30f && bf > 1e-30f && bf < 1e30f &&
+                                          gf > 1e-30f && gf < 1e30f;
+                    const float rr = in_range ? gf * rsqrtf(af) * rsqrtf(bf) : 0.0f;
+                    const float tl = tol_f;
+                    if (in_range && rr > 2.0f * tl) rot = true;
+                    else if (!in_range || rr > 0.5f * tl) rot = g * g > tol2 * (app * aqq);
+                    if (!rot && lane == 0) best_off = fmaxf(best_off, rr);
+                }
+                if (rot) {
                     // Rotation angle from Rutishauser's t = sgn(zeta)/(|zeta| + sqrt(1 + zeta^2)),
                     // zeta = (a_qq - a_pp) / 2g, sgn(0) = +1, evaluated in FP32 from ratios <= 1
                     // (its accuracy only sets how far g is reduced), and c0 = 1/sqrt(1 + t^2),
@@ -326,38 +331,34 @@ __global__ void __launch_bounds__(512) onesided_jacobi_kernel(OsParams prm) {
                         xq[n + 1] = nq2;
                         atomicAdd(&s_rot, 1);
                     }
-                } else if (live && lane == 0) {
-                    // largest scaled |g| among the pairs left alone (informational)
-                    const float rr = os_to_float(g) * rsqrtf(os_to_float(app)) * rsqrtf(os_to_float(aqq));
-                    best_off = fmaxf(best_off, fabsf(rr));
+                }
+                // The links: warp P-1 (holding the last top column) moves it to the right
+                // neighbour, warp 0 (holding the first bottom column) moves it to the left one,
+                // each as soon as its own pair is done; each receives into the buffer it sent.
+                const unsigned ph = (K >> 1) & 1u;
+                if (warp == P - 1 && c < C - 1) {
+                    double* dst = cluster.map_shared_rank(recv + (size_t)(par * 2 + 0) * LD, c + 1);
+                    for (int r = lane; r < n + 2; r += 32) dst[r] = xp[r];
+                    __syncwarp();
+                    if (lane == 0) os_remote_arrive(&rbar[par][0], c + 1);
+                    if (!os_wait(&rbar[par][1], ph)) s_timeout = 1;
+                    const double* rs = recv + (size_t)(par * 2 + 1) * LD;
+                    for (int r = lane; r < n + 2; r += 32) xp[r] = rs[r];
+                }
+                if (warp == 0 && c > 0) {
+                    double* dst = cluster.map_shared_rank(recv + (size_t)(par * 2 + 1) * LD, c - 1);
+                    for (int r = lane; r < n + 2; r += 32) dst[r] = xq[r];
+                    __syncwarp();
+                    if (lane == 0) os_remote_arrive(&rbar[par][1], c - 1);
+                    if (!os_wait(&rbar[par][0], ph)) s_timeout = 1;
+                    const double* rs = recv + (size_t)(par * 2 + 0) * LD;
+                    for (int r = lane; r < n + 2; r += 32) xq[r] = rs[r];
                 }
             }
-            __syncthreads();
             // circle tournament move: slot j -> j+1 (1 <= j <= np-2), slot np-1 -> 1, slot 0 fixed.
             // The buffer sent away on each link is reused for the column received on it.
             const int free_a = top[P - 1];  // sent to the right (when there is a right neighbour)
             const int free_b = bot[0];      // sent to the left
-            const unsigned ph = (K >> 1) & 1u;
-            if (warp == 0 && c < C - 1) {
-                double* dst = cluster.map_shared_rank(recv + (size_t)(par * 2 + 0) * LD, c + 1);
-                const double* src = bufs + (size_t)free_a * LD;
-                for (int r = lane; r < n + 2; r += 32) dst[r] = src[r];
-                os_remote_arrive(&rbar[par][0], c + 1);
-                if (!os_wait(&rbar[par][1], ph)) s_timeout = 1;
-                const double* rs = recv + (size_t)(par * 2 + 1) * LD;
-                double* rd = bufs + (size_t)free_a * LD;
-                for (int r = lane; r < n + 2; r += 32) rd[r] = rs[r];
-            }
-            if (warp == 1 && c > 0) {
-                double* dst = cluster.map_shared_rank(recv + (size_t)(par * 2 + 1) * LD, c - 1);
-                const double* src = bufs + (size_t)free_b * LD;
-                for (int r = lane; r < n + 2; r += 32) dst[r] = src[r];
-                os_remote_arrive(&rbar[par][1], c - 1);
-                if (!os_wait(&rbar[par][0], ph)) s_timeout = 1;
-                const double* rs = recv + (size_t)(par * 2 + 0) * LD;
-                double* rd = bufs + (size_t)free_b * LD;
-                for (int r = lane; r < n + 2; r += 32) rd[r] = rs[r];
-            }
             if (tid == 0) {
                 int* nt = map_top[par ^ 1];
                 int* nb = map_bot[par ^ 1];
@@ -437,9 +438,9 @@ cudaError_t launch_eig_onesided(const double* M, int n, int64_t ldm, double tol,
     if (n > 64) return cudaErrorNotSupported;
     double* X = reinterpret_cast<double*>(scratch);
     int* perm = reinterpret_cast<int*>(reinterpret_cast<char*>(scratch) + sizeof(double) * (size_t)n * n);
-    const size_t chol_smem = sizeof(double) * (size_t)n * n;
+    const size_t chol_smem = 2 * sizeof(double) * (size_t)n * n;
     cudaError_t e = cudaFuncSetAttribute(chol_piv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(sizeof(double) * 64 * 64));
+                                         (int)(2 * sizeof(double) * 64 * 64));
     if (e != cudaSuccess) return e;
     chol_piv_kernel<<<1, 256, chol_smem, s>>>(M, n, ldm, X, perm, info);
     e = cudaGetLastError();

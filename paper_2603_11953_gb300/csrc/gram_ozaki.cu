@@ -299,28 +299,40 @@ __device__ double round_i128(__int128 v, int scale, __int128& rounded_int) {
     return neg ? -d : d;
 }
 
-__global__ void gram_combine_kernel(const long long* __restrict__ part_hi,
-                                    const long long* __restrict__ part_lo,
-                                    const int* __restrict__ part_E, int P, int NP, int n,
-                                    double* __restrict__ G, double* __restrict__ G_lo, int64_t ldg) {
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+// One warp per Gram entry (i, j), i <= j: the lanes take every 32nd partial, and the
+// exact int128 sums are added across the warp (integer addition: the result does not
+// depend on the order, so the Gram is bitwise reproducible).
+__device__ __forceinline__ __int128 shfl_xor_i128(__int128 v, int o) {
+    const unsigned long long lo = (unsigned long long)v, hi = (unsigned long long)(v >> 64);
+    const unsigned long long l2 = __shfl_xor_sync(0xffffffffu, lo, o), h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+    return (__int128)(((unsigned __int128)h2 << 64) | (unsigned __int128)l2);
+}
+
+__global__ void __launch_bounds__(256) gram_combine_kernel(const long long* __restrict__ part_hi,
+                                                           const long long* __restrict__ part_lo,
+                                                           const int* __restrict__ part_E, int P, int NP, int n,
+                                                           double* __restrict__ G, double* __restrict__ G_lo,
+                                                           int64_t ldg) {
+    const int idx = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
     const int npairs = n * (n + 1) / 2;
-    if (idx >= npairs) return;
+    if (idx >= npairs) return;  // whole warps only
     int j = (int)((sqrtf(8.0f * (float)idx + 1.0f) - 1.0f) * 0.5f);
     while ((j + 1) * (j + 2) / 2 <= idx) ++j;
     while (j * (j + 1) / 2 > idx) --j;
     const int i = idx - j * (j + 1) / 2;
     int emax = EXP_EMPTY;
-    for (int c = 0; c < P; ++c) {
+    for (int c = lane; c < P; c += 32) {
         const int Ei = part_E[(size_t)c * NP + i], Ej = part_E[(size_t)c * NP + j];
         if (Ei == EXP_EMPTY || Ej == EXP_EMPTY) continue;
         emax = max(emax, Ei + Ej);
     }
+    emax = __reduce_max_sync(0xffffffffu, emax);
     double hi = 0.0, lo = 0.0;
     if (emax != EXP_EMPTY) {
         // value_c = 2^(e_c - 63) * (h * 2^16 + l); fixed point unit 2^(emax - 63 - 29)
         __int128 acc = 0;
-        for (int c = 0; c < P; ++c) {
+        for (int c = lane; c < P; c += 32) {
             const int Ei = part_E[(size_t)c * NP + i], Ej = part_E[(size_t)c * NP + j];
             if (Ei == EXP_EMPTY || Ej == EXP_EMPTY) continue;
             const int sh = emax - (Ei + Ej);
@@ -331,15 +343,19 @@ __global__ void gram_combine_kernel(const long long* __restrict__ part_hi,
             const __int128 X = h * ((__int128)1 << 16) + l;
             acc += (X * ((__int128)1 << 29)) >> sh;
         }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += shfl_xor_i128(acc, o);
         __int128 r1, r2;
         hi = round_i128(acc, emax - 92, r1);
         lo = round_i128(acc - r1, emax - 92, r2);
     }
-    G[i + (size_t)j * ldg] = hi;
-    G[j + (size_t)i * ldg] = hi;
-    if (G_lo) {
-        G_lo[i + (size_t)j * ldg] = lo;
-        G_lo[j + (size_t)i * ldg] = lo;
+    if (lane == 0) {
+        G[i + (size_t)j * ldg] = hi;
+        G[j + (size_t)i * ldg] = hi;
+        if (G_lo) {
+            G_lo[i + (size_t)j * ldg] = lo;
+            G_lo[j + (size_t)i * ldg] = lo;
+        }
     }
 }
 
@@ -482,8 +498,7 @@ cudaError_t launch_gram_combine(const GramPlan& plan, const void* part, int n, d
     const long long* pl = ph + (size_t)plan.P * plan.NP * plan.NP;
     const int* pE = reinterpret_cast<const int*>(pl + (size_t)plan.P * plan.NP * plan.NP);
     const int npairs = n * (n + 1) / 2;
-    gram_combine_kernel<<<(npairs + 127) / 128, 128, 0, s>>>(ph, pl, pE, plan.P, plan.NP, n, G, G_lo,
-                                                             ldg);
+    gram_combine_kernel<<<(npairs + 7) / 8, 256, 0, s>>>(ph, pl, pE, plan.P, plan.NP, n, G, G_lo, ldg);
     return cudaGetLastError();
 }
 

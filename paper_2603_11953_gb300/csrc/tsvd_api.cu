@@ -20,7 +20,9 @@ struct tsvd_ctx {
     void* ws = nullptr;
     size_t ws_bytes = 0;
     DevInfo* dinfo = nullptr;
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    // per-stage events of the last `timing` calls (a ring of 4 events per call)
+    std::vector<cudaEvent_t> ev;
+    long long calls = 0;     // timed calls so far
     bool have_times = false;
 };
 
@@ -144,8 +146,9 @@ cudaError_t run_eig(tsvd_ctx* h, const double* M, int n, int64_t ldm, double* sc
     return launch_jacobi(M, n, ldm, jacobi_tol(h, n), max_sweeps(h), scratch, lam, Vh, h->dinfo, h->stream);
 }
 
+int ring(const tsvd_ctx* h) { return (int)(h->ev.size() / 4); }
 void record(tsvd_ctx* h, int k) {
-    if (h->opts.timing) cudaEventRecord(h->ev[k], h->stream);
+    if (h->opts.timing) cudaEventRecord(h->ev[4 * (size_t)(h->calls % ring(h)) + k], h->stream);
 }
 
 // One instance of Algorithm 1, workspace already sized by the caller.
@@ -187,7 +190,10 @@ tsvd_status solve_one(tsvd_ctx* h, const void* A, int64_t m, int n, int64_t lda,
         e = cudaMemcpyAsync(info, h->dinfo, sizeof(DevInfo), cudaMemcpyDefault, h->stream);
         if (e != cudaSuccess) return from_cuda(e);
     }
-    if (timed) h->have_times = true;
+    if (timed) {
+        h->have_times = true;
+        ++h->calls;
+    }
     return TSVD_OK;
 }
 
@@ -221,6 +227,7 @@ tsvd_status tsvd_create(tsvd_handle* out, int device, void* stream, const tsvd_o
         if (opts->eig_variant < 0 || opts->eig_variant > 2) return TSVD_ERR_UNSUPPORTED;
         if (opts->gram_variant < 0 || opts->gram_variant > 2) return TSVD_ERR_ARG;
         if (opts->u_variant < 0 || opts->u_variant > 1) return TSVD_ERR_ARG;
+        if (opts->timing < 0) return TSVD_ERR_ARG;
     }
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
@@ -239,7 +246,10 @@ tsvd_status tsvd_create(tsvd_handle* out, int device, void* stream, const tsvd_o
         delete h;
         return TSVD_ERR_CUDA;
     }
-    for (auto& ev : h->ev) cudaEventCreate(&ev);
+    if (h->opts.timing > 0) {
+        h->ev.assign(4 * (size_t)(h->opts.timing < TSVD_MAX_TIMED ? h->opts.timing : TSVD_MAX_TIMED), nullptr);
+        for (auto& ev : h->ev) cudaEventCreate(&ev);
+    }
     *out = h;
     return TSVD_OK;
 }
@@ -357,17 +367,36 @@ tsvd_status tsvd_sync_status(tsvd_handle h) {
     return static_cast<tsvd_status>(d.flags);
 }
 
+static bool stage_times(tsvd_ctx* h, long long call, float ms[4]) {
+    const cudaEvent_t* e = &h->ev[4 * (size_t)(call % ring(h))];
+    if (cudaEventSynchronize(e[3]) != cudaSuccess) return false;
+    float a = 0, b = 0, c = 0, t = 0;
+    cudaEventElapsedTime(&a, e[0], e[1]);
+    cudaEventElapsedTime(&b, e[1], e[2]);
+    cudaEventElapsedTime(&c, e[2], e[3]);
+    cudaEventElapsedTime(&t, e[0], e[3]);
+    ms[0] = a; ms[1] = b; ms[2] = c; ms[3] = t;
+    return true;
+}
+
 tsvd_status tsvd_last_stage_ms(tsvd_handle h, float ms[4]) {
     if (!h || !ms) return TSVD_ERR_ARG;
     if (!h->opts.timing || !h->have_times) return TSVD_ERR_ARG;
     DeviceGuard g(h->device);
-    if (cudaEventSynchronize(h->ev[3]) != cudaSuccess) return TSVD_ERR_CUDA;
-    float a = 0, b = 0, c = 0, t = 0;
-    cudaEventElapsedTime(&a, h->ev[0], h->ev[1]);
-    cudaEventElapsedTime(&b, h->ev[1], h->ev[2]);
-    cudaEventElapsedTime(&c, h->ev[2], h->ev[3]);
-    cudaEventElapsedTime(&t, h->ev[0], h->ev[3]);
-    ms[0] = a; ms[1] = b; ms[2] = c; ms[3] = t;
+    return stage_times(h, h->calls - 1, ms) ? TSVD_OK : TSVD_ERR_CUDA;
+}
+
+tsvd_status tsvd_stage_ms_mean(tsvd_handle h, int last, float ms[4]) {
+    if (!h || !ms || last < 1) return TSVD_ERR_ARG;
+    if (!h->opts.timing || !h->have_times || last > ring(h) || last > h->calls) return TSVD_ERR_ARG;
+    DeviceGuard g(h->device);
+    double acc[4] = {0, 0, 0, 0};
+    for (long long c = h->calls - last; c < h->calls; ++c) {
+        float one[4];
+        if (!stage_times(h, c, one)) return TSVD_ERR_CUDA;
+        for (int k = 0; k < 4; ++k) acc[k] += one[k];
+    }
+    for (int k = 0; k < 4; ++k) ms[k] = (float)(acc[k] / last);
     return TSVD_OK;
 }
 
