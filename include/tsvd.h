@@ -110,6 +110,10 @@ TSVD_API const char* tsvd_status_string(tsvd_status s);
  *   G: device FP64, n x n column-major, ldg >= n, both triangles written.
  *      higher == TSVD_DD additionally writes the low parts of the
  *      double-double result at G + ldg*n (another n x n block, same ldg).
+ * Built for FP32 working precision: n <= 64 in one tensor-core pass; 64 < n
+ * <= 256 as one pass per pair of 32-column blocks (A 16-byte aligned and lda
+ * a multiple of 4, so that the tiles can be TMA-loaded).  FP64 working
+ * precision: the plain FP64 Gram (gram_variant 1), n <= 64.
  * Errors: TSVD_ERR_ARG (m < 1, n < 1, lda < m, ldg < n, null pointer, bad
  * tag), TSVD_ERR_UNSUPPORTED (n > 256 or a combination not built). */
 TSVD_API tsvd_status tsvd_gram(tsvd_handle h, const void* A, int64_t m, int64_t n, int64_t lda,

@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(256) gram_combine_kernel(const long long* __re
                                                            const long long* __restrict__ part_lo,
                                                            const int* __restrict__ part_E, int P, int NP, int n,
                                                            double* __restrict__ G, double* __restrict__ G_lo,
-                                                           int64_t ldg) {
+                                                           int64_t ldg, int c1, int c2, int wmask, int nglob) {
     const int idx = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     const int npairs = n * (n + 1) / 2;
@@ -349,12 +349,20 @@ __global__ void __launch_bounds__(256) gram_combine_kernel(const long long* __re
         hi = round_i128(acc, emax - 92, r1);
         lo = round_i128(acc - r1, emax - 92, r2);
     }
+    int gi = i, gj = j;
+    if (c1 >= 0) {
+        // two-group launch: map the local columns, keep only the tiles asked for
+        const int tile = (j < 32) ? 1 : (i >= 32) ? 2 : 4;
+        gi = i < 32 ? c1 + i : c2 + i - 32;
+        gj = j < 32 ? c1 + j : c2 + j - 32;
+        if (!(wmask & tile) || gi >= nglob || gj >= nglob) return;
+    }
     if (lane == 0) {
-        G[i + (size_t)j * ldg] = hi;
-        G[j + (size_t)i * ldg] = hi;
+        G[gi + (size_t)gj * ldg] = hi;
+        G[gj + (size_t)gi * ldg] = hi;
         if (G_lo) {
-            G_lo[i + (size_t)j * ldg] = lo;
-            G_lo[j + (size_t)i * ldg] = lo;
+            G_lo[gi + (size_t)gj * ldg] = lo;
+            G_lo[gj + (size_t)gi * ldg] = lo;
         }
     }
 }
@@ -498,7 +506,19 @@ cudaError_t launch_gram_combine(const GramPlan& plan, const void* part, int n, d
     const long long* pl = ph + (size_t)plan.P * plan.NP * plan.NP;
     const int* pE = reinterpret_cast<const int*>(pl + (size_t)plan.P * plan.NP * plan.NP);
     const int npairs = n * (n + 1) / 2;
-    gram_combine_kernel<<<(npairs + 7) / 8, 256, 0, s>>>(ph, pl, pE, plan.P, plan.NP, n, G, G_lo, ldg);
+    gram_combine_kernel<<<(npairs + 7) / 8, 256, 0, s>>>(ph, pl, pE, plan.P, plan.NP, n, G, G_lo, ldg, -1, -1, 0,
+                                                         n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gram_combine2(const GramPlan& plan, const void* part, int n, int c1, int c2, int wmask, double* G,
+                                 double* G_lo, int64_t ldg, cudaStream_t s) {
+    const long long* ph = reinterpret_cast<const long long*>(part);
+    const long long* pl = ph + (size_t)plan.P * plan.NP * plan.NP;
+    const int* pE = reinterpret_cast<const int*>(pl + (size_t)plan.P * plan.NP * plan.NP);
+    const int npairs = 64 * 65 / 2;
+    gram_combine_kernel<<<(npairs + 7) / 8, 256, 0, s>>>(ph, pl, pE, plan.P, plan.NP, 64, G, G_lo, ldg, c1, c2, wmask,
+                                                         n);
     return cudaGetLastError();
 }
 

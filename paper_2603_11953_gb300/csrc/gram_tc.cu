@@ -310,7 +310,8 @@ __device__ __forceinline__ void tc_drain(const TcRecord& R, uint32_t tmem, int q
 }
 
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    gram_tc_kernel(const __grid_constant__ CUtensorMap tmapA, int64_t m, int n, int64_t rows_per_cta,
+    gram_tc_kernel(const __grid_constant__ CUtensorMap tmapA, const __grid_constant__ CUtensorMap tmapB, int64_t m,
+                   int n, int split, int64_t rows_per_cta,
                    long long* __restrict__ part_hi, long long* __restrict__ part_lo, int* __restrict__ part_E,
                    DevInfo* info) {
     extern __shared__ unsigned char tc_dyn[];
@@ -354,7 +355,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (warp == 0 && lane == 0) {
             // ---------------- TMA producer
             tma_prefetch_desc(&tmapA);
-            const unsigned bytes = (unsigned)(TC_SUB * n * 4);
+            if (split) tma_prefetch_desc(&tmapB);
+            // split: two 32-column groups (FP columns 0..31 and 32..63) from two maps
+            const unsigned bytes = (unsigned)(TC_SUB * (split ? 64 : n) * 4);
             int issued = 0;
             for (int g = 0; g < G; ++g) {
                 const int f = g % TC_SF;
@@ -364,8 +367,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
                 if (S.abort) break;
                 mbar_expect_tx(&S.fp_full[f], bytes);
-                tma_load_2d(fpb + (size_t)f * 64 * TC_SUB, &tmapA, (int)(((int64_t)blockIdx.x + (int64_t)g * P) * TC_SUB),
-                            0, &S.fp_full[f]);
+                const int row0 = (int)(((int64_t)blockIdx.x + (int64_t)g * P) * TC_SUB);
+                tma_load_2d(fpb + (size_t)f * 64 * TC_SUB, &tmapA, row0, 0, &S.fp_full[f]);
+                if (split) tma_load_2d(fpb + (size_t)f * 64 * TC_SUB + 32 * TC_SUB, &tmapB, row0, 0, &S.fp_full[f]);
                 issued = g + 1;
             }
             tma_issued = issued;
@@ -604,7 +608,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 }  // namespace
 
 bool gram_tc_ok(const void* A, int working, int n, int64_t lda) {
-    return working == 0 && n >= 1 && n <= 64 && ((uintptr_t)A % 16 == 0) && (lda % 4 == 0);
+    return working == 0 && n >= 1 && n <= 256 && ((uintptr_t)A % 16 == 0) && (lda % 4 == 0);
 }
 
 GramPlan gram_tc_plan(int64_t m, int n, int sm_count, int split_k_opt) {
@@ -625,16 +629,36 @@ GramPlan gram_tc_plan(int64_t m, int n, int sm_count, int split_k_opt) {
 
 cudaError_t launch_gram_tc(const void* A, int64_t m, int n, int64_t lda, const GramPlan& plan, void* part,
                            DevInfo* info, cudaStream_t s) {
-    CUtensorMap tmap;
-    cudaError_t e = make_tmap_2d(&tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, sizeof(float), A, (uint64_t)m, (uint64_t)n,
-                                 (uint64_t)lda, TC_SUB, (uint32_t)n, CU_TENSOR_MAP_SWIZZLE_NONE);
+    return launch_gram_tc2(A, m, n, lda, -1, -1, plan, part, info, s);
+}
+
+// c1 < 0: columns 0..n-1 (n <= 64).  Otherwise the virtual 64 columns are the
+// 32-column groups starting at c1 and c2 of A (columns >= n read as zero).
+cudaError_t launch_gram_tc2(const void* A, int64_t m, int n, int64_t lda, int c1, int c2, const GramPlan& plan,
+                            void* part, DevInfo* info, cudaStream_t s) {
+    CUtensorMap tmapA, tmapB;
+    const bool split = c1 >= 0;
+    const float* Af = static_cast<const float*>(A);
+    cudaError_t e;
+    if (!split) {
+        e = make_tmap_2d(&tmapA, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, sizeof(float), A, (uint64_t)m, (uint64_t)n,
+                         (uint64_t)lda, TC_SUB, (uint32_t)n, CU_TENSOR_MAP_SWIZZLE_NONE);
+        tmapB = tmapA;
+    } else {
+        e = make_tmap_2d(&tmapA, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, sizeof(float), Af + (size_t)c1 * lda, (uint64_t)m,
+                         (uint64_t)(n - c1), (uint64_t)lda, TC_SUB, 32, CU_TENSOR_MAP_SWIZZLE_NONE);
+        if (e == cudaSuccess)
+            e = make_tmap_2d(&tmapB, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, sizeof(float), Af + (size_t)c2 * lda,
+                             (uint64_t)m, (uint64_t)(n - c2), (uint64_t)lda, TC_SUB, 32, CU_TENSOR_MAP_SWIZZLE_NONE);
+    }
     if (e != cudaSuccess) return e;
     long long* ph = reinterpret_cast<long long*>(part);
     long long* pl = ph + (size_t)plan.P * 64 * 64;
     int* pE = reinterpret_cast<int*>(pl + (size_t)plan.P * 64 * 64);
     e = cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
     if (e != cudaSuccess) return e;
-    gram_tc_kernel<<<plan.P, TC_THREADS, TC_SMEM, s>>>(tmap, m, n, plan.rows_per_cta, ph, pl, pE, info);
+    gram_tc_kernel<<<plan.P, TC_THREADS, TC_SMEM, s>>>(tmapA, tmapB, m, split ? 64 : n, split ? 1 : 0,
+                                                       plan.rows_per_cta, ph, pl, pE, info);
     return cudaGetLastError();
 }
 

@@ -52,12 +52,20 @@ cudaError_t launch_gram_ozaki(const void* A, int working, int64_t m, int n, int6
 // NP = 64; plan from gram_tc_plan.
 bool gram_tc_ok(const void* A, int working, int n, int64_t lda);
 GramPlan gram_tc_plan(int64_t m, int n, int sm_count, int split_k_opt);
+// Two 32-column groups (c1, c2) of a wider A as the 64 virtual columns (n > 64).
+cudaError_t launch_gram_tc2(const void* A, int64_t m, int n, int64_t lda, int c1, int c2, const GramPlan& plan,
+                            void* part, DevInfo* info, cudaStream_t s);
 cudaError_t launch_gram_tc(const void* A, int64_t m, int n, int64_t lda, const GramPlan& plan, void* part,
                            DevInfo* info, cudaStream_t s);
 // Combine the partials into G (n x n FP64, both triangles) and optionally the
 // double-double low parts G_lo (may be null).
 cudaError_t launch_gram_combine(const GramPlan& plan, const void* part, int n, double* G,
                                 double* G_lo, int64_t ldg, cudaStream_t s);
+// The 64 x 64 partials of a two-group launch into G: local column l maps to
+// (l < 32 ? c1 + l : c2 + l - 32) (dropped when >= n); wmask bit 0 writes the
+// first group's diagonal tile, bit 1 the second's, bit 2 the cross tile.
+cudaError_t launch_gram_combine2(const GramPlan& plan, const void* part, int n, int c1, int c2, int wmask, double* G,
+                                 double* G_lo, int64_t ldg, cudaStream_t s);
 
 // Plain all-FP64 Gram (the comparison form): DFMA over m, fixed-order combine.
 size_t gram_plain_partials_bytes(int64_t m, int n, int sm_count);

@@ -110,6 +110,22 @@ tsvd_status run_gram(tsvd_ctx* h, const void* A, int64_t m, int n, int64_t lda, 
         return from_cuda(e);
     }
     const bool tc = use_tc(h, A, working, n, lda);
+    if (tc && n > 64) {
+        // 32-column blocks b1 < b2, one launch per pair: the cross tile always, block b1's
+        // diagonal tile from the pair (b1, b1 + 1), the last block's from (nb - 2, nb - 1)
+        const GramPlan plan = gram_tc_plan(m, 64, h->sm_count, h->opts.split_k);
+        const int nb = (n + 31) / 32;
+        for (int b1 = 0; b1 < nb - 1; ++b1)
+            for (int b2 = b1 + 1; b2 < nb; ++b2) {
+                const int wmask = 4 | (b2 == b1 + 1 ? 1 : 0) | (b1 == nb - 2 && b2 == nb - 1 ? 2 : 0);
+                e = launch_gram_tc2(A, m, n, lda, 32 * b1, 32 * b2, plan, base(h) + part_off, h->dinfo, h->stream);
+                if (e == cudaSuccess)
+                    e = launch_gram_combine2(plan, base(h) + part_off, n, 32 * b1, 32 * b2, wmask, G, G_lo, ldg,
+                                             h->stream);
+                if (e != cudaSuccess) return from_cuda(e);
+            }
+        return TSVD_OK;
+    }
     const GramPlan plan = tc ? gram_tc_plan(m, n, h->sm_count, h->opts.split_k)
                              : gram_plan(m, n, h->sm_count, h->opts.split_k);
     e = tc ? launch_gram_tc(A, m, n, lda, plan, base(h) + part_off, h->dinfo, h->stream)
@@ -124,10 +140,11 @@ size_t part_bytes_for(tsvd_ctx* h, const void* A, int working, int64_t m, int n,
     return gram_partials_bytes(gram_plan(m, n, h->sm_count, h->opts.split_k));
 }
 
-bool gram_supported(tsvd_ctx* h, int working, int64_t n) {
-    if (n > 64) return false;                      // tensor-core Gram built for n <= 64
+bool gram_supported(tsvd_ctx* h, const void* A, int working, int64_t n, int64_t lda) {
     if (h->opts.gram_variant != 1 && working != TSVD_FP32) return false;
-    return true;
+    if (n <= 64) return true;
+    // 64 < n <= 256: the tensor-core Gram over pairs of 32-column blocks
+    return n <= 256 && use_tc(h, A, working, (int)n, lda);
 }
 
 double jacobi_tol(tsvd_ctx* h, int64_t n) {
@@ -270,7 +287,7 @@ tsvd_status tsvd_gram(tsvd_handle h, const void* A, int64_t m, int64_t n, int64_
                       tsvd_prec working, tsvd_prec higher, double* G, int64_t ldg) {
     if (!h || !A || !G || m < 1 || n < 1 || lda < m || ldg < n || !valid_prec_pair(working, higher))
         return TSVD_ERR_ARG;
-    if (!gram_supported(h, working, n)) return TSVD_ERR_UNSUPPORTED;
+    if (!gram_supported(h, A, working, n, lda)) return TSVD_ERR_UNSUPPORTED;
     if (higher == TSVD_DD && h->opts.gram_variant == 1) return TSVD_ERR_UNSUPPORTED;
     DeviceGuard g(h->device);
     const size_t pb = part_bytes_for(h, A, working, m, (int)n, lda);
@@ -314,7 +331,7 @@ tsvd_status tsvd_solve(tsvd_handle h, const void* A, int64_t m, int64_t n, int64
         !valid_prec_pair(working, higher))
         return TSVD_ERR_ARG;
     if (!(working == TSVD_FP32 && higher == TSVD_FP64)) return TSVD_ERR_UNSUPPORTED;
-    if (!gram_supported(h, working, n)) return TSVD_ERR_UNSUPPORTED;
+    if (!gram_supported(h, A, working, n, lda)) return TSVD_ERR_UNSUPPORTED;
     DeviceGuard g(h->device);
     const Layout L = layout_for(n, part_bytes_for(h, A, working, m, (int)n, lda), working);
     tsvd_status st = ensure_ws(h, L.total);

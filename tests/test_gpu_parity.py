@@ -94,7 +94,8 @@ def check_gram(A_np, Gh, m, n):
 
 # ------------------------------------------------------------------ Gram (a1-a3)
 @pytest.mark.parametrize("m,n,split", [(1000, 1, 0), (1000, 5, 0), (20000, 16, 0), (4133, 33, 3),
-                                       (70001, 48, 0), (131077, 64, 0), (131077, 64, 5)])
+                                       (70001, 48, 0), (131077, 64, 0), (131077, 64, 5),
+                                       (5004, 65, 0), (9000, 96, 0), (4100, 200, 0), (20480, 256, 0)])
 def test_gram_matches_exact_sum(m, n, split):
     A, _ = workloads.small_case(m, n, kappa_sigma=1e3, logd=3.0, seed=m + n, device="cuda")
     h = handle(split_k=split) if split else None
@@ -186,6 +187,25 @@ def test_eig_matches_oracle_jacobi(n, kappa, logd, variant):
     # eigenvectors: scaled residual of every column against the same M
     R = S_hi @ Vg - Vg * lam_g
     assert np.all(np.linalg.norm(R, axis=0) <= 64 * n * UH * kC * np.abs(lam_g).max() + 1e-300)
+
+
+# ------------------------------------------------------------------ wide n (64 < n <= 256)
+@pytest.mark.parametrize("m,n", [(3000, 100), (4100, 256)])
+def test_solve_wide_matches_oracle(m, n):
+    A, _ = workloads.small_case(m, n, kappa_sigma=1e2, logd=2.0, seed=11 * m + n, device="cuda")
+    sig, V, U, st, sweeps = gpu_solve(A, m, n, m)
+    assert st == T.TSVD_OK
+    A_np = workloads.to_numpy_colmajor(A, m)
+    ref = oracle.svd(A_np, higher=1)
+    assert ref["status"] == 0
+    rel = np.abs(sig - ref["sigma_h"]) / ref["sigma_h"]
+    assert rel.max() <= 2 * U32, rel.max()
+    W = (V.astype(np.float32) / sig.astype(np.float32)).astype(np.float64)
+    rows = np.unique(np.linspace(0, m - 1, 64).astype(np.int64))
+    Uref = oracle.rows_times(A_np, W, rows, 24)
+    bound = (n + 1) * U32 * (np.abs(A_np[rows].astype(np.float64)) @ np.abs(W)) + 1e-38
+    assert np.all(np.abs(U[rows] - Uref) <= bound)
+    assert np.abs(U.T @ U - np.eye(n)).max() <= 1e-4
 
 
 # ------------------------------------------------------------------ solve (a1-a7)
