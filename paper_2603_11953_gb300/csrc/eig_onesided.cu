@@ -155,13 +155,28 @@ __device__ __forceinline__ double os_to_double(float x) {
     return __longlong_as_double((long long)d);
 }
 __device__ __forceinline__ int os_hi(double x) { return __double2hiint(x); }
-// arrive on an mbarrier of CTA `rank` of the cluster, releasing the prior stores of this
-// thread and of the warp lanes it has synchronised with (__syncwarp)
-__device__ __forceinline__ void os_remote_arrive(const uint64_t* local_bar, int rank) {
+__device__ __forceinline__ uint32_t os_mapa(const void* local, int rank) {
     uint32_t raddr;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(raddr) : "r"(os_smem(local_bar)), "r"(rank));
-    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(raddr) : "memory");
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(raddr) : "r"(os_smem(local)), "r"(rank));
+    return raddr;
 }
+// this CTA expects `bytes` more on its own mbarrier (and counts as its one arrival)
+__device__ __forceinline__ void os_arm(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(os_smem(bar)), "r"(bytes) : "memory");
+}
+// bulk copy of `bytes` from this CTA's shared memory into CTA `rank`'s, completing the
+// transaction on that CTA's mbarrier (no fence on the sender's critical path)
+__device__ __forceinline__ void os_bulk_to(const void* src, const void* dst_local_equiv, const uint64_t* bar_local_equiv,
+                                           int rank, unsigned bytes) {
+    const uint32_t dst = os_mapa(dst_local_equiv, rank), bar = os_mapa(bar_local_equiv, rank);
+    asm volatile(
+        "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+        "r"(os_smem(src)), "r"(bytes), "r"(bar)
+        : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+// the source of this thread's bulk copies has been read
+__device__ __forceinline__ void os_bulk_read_done() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 // bounded wait (about 1 s of GPU clock) with cluster-scope acquire
 __device__ __forceinline__ bool os_wait(const uint64_t* bar, unsigned parity) {
     const long long t0 = clock64();
@@ -189,7 +204,7 @@ __global__ void __launch_bounds__(512) onesided_jacobi_kernel(OsParams prm) {
     const int c = (int)cluster.block_rank();
     const int n = prm.n, np = prm.np, P = prm.P;
     const int LD = ((n + 2) + 1) & ~1;  // x[0..n-1], idx, nrm
-    extern __shared__ double sm[];
+    extern __shared__ __align__(16) double sm[];
     double* bufs = sm;                       // [2P][LD]
     double* recv = sm + (size_t)2 * P * LD;  // [2 parity][2 side: 0 from the left, 1 from the right][LD]
     __shared__ uint64_t rbar[2][2];          // same indexing as recv
@@ -209,6 +224,9 @@ __global__ void __launch_bounds__(512) onesided_jacobi_kernel(OsParams prm) {
         for (int a = 0; a < 2; ++a)
             for (int b = 0; b < 2; ++b)
                 asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(os_smem(&rbar[a][b])));
+        // each receive buffer expects one column at steps 0 and 1 (re-armed after every use)
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b) os_arm(&rbar[a][b], (unsigned)(sizeof(double) * LD));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_cnt[0] = 0;
         s_cnt[1] = 0;
@@ -334,23 +352,37 @@ __global__ void __launch_bounds__(512) onesided_jacobi_kernel(OsParams prm) {
                 }
                 // The links: warp P-1 (holding the last top column) moves it to the right
                 // neighbour, warp 0 (holding the first bottom column) moves it to the left one,
-                // each as soon as its own pair is done; each receives into the buffer it sent.
+                // each as soon as its own pair is done, by a bulk copy into the neighbour's
+                // receive buffer; each receives into the buffer it sent once that copy has read it.
                 const unsigned ph = (K >> 1) & 1u;
+                const unsigned colb = (unsigned)(sizeof(double) * LD);
                 if (warp == P - 1 && c < C - 1) {
-                    double* dst = cluster.map_shared_rank(recv + (size_t)(par * 2 + 0) * LD, c + 1);
-                    for (int r = lane; r < n + 2; r += 32) dst[r] = xp[r];
                     __syncwarp();
-                    if (lane == 0) os_remote_arrive(&rbar[par][0], c + 1);
+                    if (lane == 0) {
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        os_bulk_to(xp, recv + (size_t)(par * 2 + 0) * LD, &rbar[par][0], c + 1, colb);
+                    }
                     if (!os_wait(&rbar[par][1], ph)) s_timeout = 1;
+                    if (lane == 0) {
+                        os_arm(&rbar[par][1], colb);  // for step K + 2
+                        os_bulk_read_done();
+                    }
+                    __syncwarp();
                     const double* rs = recv + (size_t)(par * 2 + 1) * LD;
                     for (int r = lane; r < n + 2; r += 32) xp[r] = rs[r];
                 }
                 if (warp == 0 && c > 0) {
-                    double* dst = cluster.map_shared_rank(recv + (size_t)(par * 2 + 1) * LD, c - 1);
-                    for (int r = lane; r < n + 2; r += 32) dst[r] = xq[r];
                     __syncwarp();
-                    if (lane == 0) os_remote_arrive(&rbar[par][1], c - 1);
+                    if (lane == 0) {
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        os_bulk_to(xq, recv + (size_t)(par * 2 + 1) * LD, &rbar[par][1], c - 1, colb);
+                    }
                     if (!os_wait(&rbar[par][0], ph)) s_timeout = 1;
+                    if (lane == 0) {
+                        os_arm(&rbar[par][0], colb);  // for step K + 2
+                        os_bulk_read_done();
+                    }
+                    __syncwarp();
                     const double* rs = recv + (size_t)(par * 2 + 0) * LD;
                     for (int r = lane; r < n + 2; r += 32) xq[r] = rs[r];
                 }

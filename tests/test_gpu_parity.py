@@ -263,6 +263,33 @@ def test_batch_equals_single_solves():
         assert np.array_equal(U1, Us[k][:m].cpu().numpy().astype(np.float64))
 
 
+def test_batch_ragged_workload_matches_oracle():
+    """The batched workload's recipe (ragged m log-uniform, n from {8,...,64}, lda = m
+    rounded up to 4, 256-byte aligned bases in one buffer) at 40 instances with m <= 8192."""
+    buf, metas = workloads.make_batch(count=40, device="cuda", m_hi=8192)
+    count = len(metas)
+    As = [buf[md["offset"]:] for md in metas]
+    sig = [torch.zeros(md["n"], device="cuda") for md in metas]
+    Vs = [colmajor(md["n"], md["n"], torch.float32) for md in metas]
+    info = torch.zeros(6 * count, dtype=torch.int32, device="cuda")
+    h = handle()
+    T.tsvd_batch_solve(h, count, As, [md["m"] for md in metas], [md["n"] for md in metas],
+                       [md["lda"] for md in metas], T.TSVD_FP32, T.TSVD_FP64, sig, Vs,
+                       [md["n"] for md in metas], None, None, info)
+    torch.cuda.synchronize()
+    T.tsvd_destroy(h)
+    assert np.all(info.view(count, 6)[:, 0].cpu().numpy() == 0)
+    for k, md in enumerate(metas):
+        m, n, lda = md["m"], md["n"], md["lda"]
+        A_np = buf[md["offset"]:md["offset"] + lda * n].view(n, lda).T[:m].cpu().numpy()
+        ref = oracle.svd(np.asfortranarray(A_np), higher=1)
+        assert ref["status"] == 0
+        # this spectrum reaches sigma_n / sigma_1 = 1e-5 (kappa(B) up to ~1e5), past the
+        # kappa(B) <= 1e3 range where one FP32 ulp bounds the error: the target 1e-5 applies
+        rel = np.abs(sig[k].cpu().numpy().astype(np.float64) - ref["sigma_h"]) / ref["sigma_h"]
+        assert rel.max() <= 1e-5, (k, m, n, rel.max())
+
+
 # ------------------------------------------------------------------ statuses and arguments
 def test_status_nonfinite_rank_convergence_and_args():
     m, n = 4096, 8
