@@ -331,7 +331,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     (void)rows_per_cta;
 
     if (tid == 0) {
-        for (int s = 0; s < TC_SF; ++s) { mbar_init(&S.fp_full[s], 1); mbar_init(&S.fp_empty[s], 2 + 16); }
+        // an FP32 stage is free once both deciders and the MMA issuer (which sees every worker's
+        // digits of that sub-chunk) have passed it
+        for (int s = 0; s < TC_SF; ++s) { mbar_init(&S.fp_full[s], 1); mbar_init(&S.fp_empty[s], 2 + 1); }
         for (int s = 0; s < TC_SD; ++s) { mbar_init(&S.dig_full[s], 16); mbar_init(&S.dig_empty[s], 1); }
         for (int s = 0; s < TC_RD; ++s) { mbar_init(&S.dec_full[s], 2); mbar_init(&S.dec_empty[s], 16); }
         mbar_init(&S.acc_full, 1);
@@ -380,6 +382,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             for (int g = 0; g < G; ++g) {
                 const int d = g % TC_SD;
                 if (!mbar_wait(&S.dig_full[d], (g / TC_SD) & 1) || S.abort) { atomicExch(&S.abort, 1); break; }
+                mbar_arrive(&S.fp_empty[g % TC_SF]);  // every worker has read this FP32 stage
                 const int newp = S.dig_newp[d];
                 if (newp && g > 0) {
                     // close the running period: the workers drain it before it is overwritten
@@ -504,8 +507,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const int newp = R.newp;
             if (g < G) {
                 const int d = g % TC_SD, f = g % TC_SF;
-                ok = (g < TC_SD || mbar_wait(&S.dig_empty[d], ((g / TC_SD) - 1) & 1)) &&
-                     mbar_wait(&S.fp_full[f], (g / TC_SF) & 1);
+                // the FP32 stage has landed: the deciders waited for it before publishing the record
+                // (their release on dec_full orders it before this warp's acquire)
+                ok = g < TC_SD || mbar_wait(&S.dig_empty[d], ((g / TC_SD) - 1) & 1);
                 if (!__all_sync(0xffffffffu, ok)) { failed = true; break; }
                 // digits of sub-chunk g: y = 128 a 2^-E (|y| < 128, < 256 after a soft growth);
                 // digit s is y's remainder rounded to the grid 2^-8s (|digit| <= 128 grid units,
@@ -552,7 +556,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 if (lane == 0) {
                     S.dig_newp[d] = newp;  // every warp writes the same value
                     mbar_arrive(&S.dig_full[d]);
-                    mbar_arrive(&S.fp_empty[f]);
                 }
             }
             if (((newp && g > 0) || g == G) && G > 0) {
