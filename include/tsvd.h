@@ -113,7 +113,12 @@ TSVD_API const char* tsvd_status_string(tsvd_status s);
  * Built for FP32 working precision: n <= 64 in one tensor-core pass; 64 < n
  * <= 256 as one pass per pair of 32-column blocks (A 16-byte aligned and lda
  * a multiple of 4, so that the tiles can be TMA-loaded).  FP64 working
- * precision: the plain FP64 Gram (gram_variant 1), n <= 64.
+ * precision, n <= 64: each column scaled by a power of two and cut into four
+ * exact 23-bit fixed-point FP32 pieces (an m x 4n FP32 copy in the handle's
+ * workspace), whose block-pair Grams run on the same tensor-core kernel and
+ * are summed in double-double: |G - A^T A|_ij <= 2^-88 m 2^(e_i + e_j), with
+ * 2^e_j the least power of two above max_r |a_rj|.  gram_variant 1 gives the
+ * plain FP64 Gram instead (no double-double form).
  * Errors: TSVD_ERR_ARG (m < 1, n < 1, lda < m, ldg < n, null pointer, bad
  * tag), TSVD_ERR_UNSUPPORTED (n > 256 or a combination not built). */
 TSVD_API tsvd_status tsvd_gram(tsvd_handle h, const void* A, int64_t m, int64_t n, int64_t lda,
@@ -135,9 +140,13 @@ TSVD_API tsvd_status tsvd_eig(tsvd_handle h, const double* M, int64_t n, int64_t
  *   V: device n x n working type, ldv >= n.
  *   U: device m x n working type, ldu >= m, or NULL to skip line 6.
  *   info: NULL, or device / pinned-host tsvd_info written at the end.
- * higher must be TSVD_FP64 for FP32 working and TSVD_DD for FP64 working.
+ * higher must be TSVD_FP64 for FP32 working.  FP64 working (n <= 64): the
+ * double-double Gram of tsvd_gram, then with higher = TSVD_DD a double-double
+ * pivoted Cholesky and one-sided Jacobi (Alg. 2 form, one CTA), with higher =
+ * TSVD_FP64 the FP64 n x n stage on the Gram's high part; U in FP64.
  * Errors: TSVD_ERR_ARG (m < n, n < 1, lda < m, ldv < n, ldu < m with U,
- * null required pointer, bad tag), TSVD_ERR_UNSUPPORTED (n > 256). */
+ * null required pointer, bad tag), TSVD_ERR_UNSUPPORTED (n > 256, FP32 with
+ * higher = TSVD_DD, FP64 with n > 64, or TSVD_DD with gram_variant 1). */
 TSVD_API tsvd_status tsvd_solve(tsvd_handle h, const void* A, int64_t m, int64_t n, int64_t lda,
                        tsvd_prec working, tsvd_prec higher, void* sigma, void* V, int64_t ldv,
                        void* U, int64_t ldu, tsvd_info* info);

@@ -73,6 +73,21 @@ cudaError_t launch_gram_plain(const void* A, int working, int64_t m, int n, int6
                               int sm_count, void* part, double* G, int64_t ldg, DevInfo* info,
                               cudaStream_t s);
 
+// Double-double Gram of an FP64 A (working FP64): exact 23-bit fixed-point
+// pieces (four per entry, column-scaled by powers of two) into an m x 4NB FP32
+// matrix in `extra` (fp64_extra_bytes), whose 32-column block pairs
+// (fp64_pair_needed) go through the tensor-core Gram into the 4NB x 4NB
+// double-double G3 (fp64_g3); launch_fp64_fold sums the pieces into G, G_lo.
+int fp64_block_cols(int n);
+int64_t fp64_split_ld(int64_t m);
+size_t fp64_extra_bytes(int64_t m, int n);
+bool fp64_pair_needed(int n, int b1, int b2);
+const float* fp64_split_matrix(const void* extra);
+double* fp64_g3(void* extra, int64_t m, int n, double** g3lo);
+cudaError_t launch_fp64_split(const double* A, int64_t m, int n, int64_t lda, void* extra, DevInfo* info,
+                              cudaStream_t s);
+cudaError_t launch_fp64_fold(void* extra, int64_t m, int n, double* G, double* G_lo, int64_t ldg, cudaStream_t s);
+
 // ---------------------------------------------------------------- eigen stage (Alg. 1 l.3-5)
 // Two-sided Jacobi in FP64 on M (n x n, read from M/ldm), one CTA.
 // scratch: 2*n*n doubles (used when n > 64).  Writes unsorted lambda and V
@@ -88,16 +103,24 @@ cudaError_t launch_eig_onesided(const double* M, int n, int64_t ldm, double tol,
                                 void* scratch, double* lam_ws, double* V_ws, DevInfo* info,
                                 cudaStream_t s);
 
+// Double-double eigen stage for FP64 working (n <= 64, one CTA): pivoted
+// Cholesky of M = G + G_lo in double-double, then a one-sided Jacobi SVD of
+// R^T in double-double.  scratch: unused.  Writes unsorted lambda (rounded to
+// FP64) and V like launch_jacobi.
+cudaError_t launch_eig_dd(const double* M, const double* M_lo, int n, int64_t ldm, double tol, int max_sweeps,
+                          double* lam_ws, double* V_ws, DevInfo* info, cudaStream_t s);
+
 // Eigensolver variants (tsvd_opts.eig_variant).
 enum : int { EIG_DEFAULT = 0, EIG_TWO_SIDED = 1, EIG_ONE_SIDED = 2 };
 
 // Sort descending, sign rule, sigma = sqrt(lambda), round to working.
 // working: 0 FP32, 1 FP64.  Outputs (any may be null):
 //   sigma_w [n], V_w (ldv), W_w = RN(V_w / sigma_w) (ld n) in working type;
-//   lam_sorted [n], V_sorted (ld_vs) in FP64.
+//   lam_sorted [n], V_sorted (ld_vs) in FP64.  sigma_n < uh sigma_1 flags rank deficiency.
 cudaError_t launch_finish(const double* lam_ws, const double* V_ws, int n, int working,
                           void* sigma_w, void* V_w, int64_t ldv, void* W_w, double* lam_sorted,
-                          double* V_sorted, int64_t ld_vs, DevInfo* info, cudaStream_t s);
+                          double* V_sorted, int64_t ld_vs, DevInfo* info, cudaStream_t s,
+                          double uh = 1.1102230246251565e-16);
 
 // ---------------------------------------------------------------- U (Alg. 1 l.6)
 cudaError_t launch_compute_u(const void* A, int working, int64_t m, int n, int64_t lda,

@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(256)
     finish_kernel(const double* __restrict__ lam, const double* __restrict__ V, int n,
                   WT* __restrict__ sigma_w, WT* __restrict__ V_w, int64_t ldv, WT* __restrict__ W_w,
                   double* __restrict__ lam_sorted, double* __restrict__ V_sorted, int64_t ld_vs,
-                  DevInfo* info) {
+                  DevInfo* info, double uh) {
     __shared__ int order[256];
     __shared__ double sig[256];
     __shared__ double sgn[256];
@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(256)
         sgn[tid] = V[best + (size_t)src * n] < 0.0 ? -1.0 : 1.0;
     }
     __syncthreads();
-    if (tid == 0 && n > 1 && sig[n - 1] < 1.1102230246251565e-16 * sig[0])
+    if (tid == 0 && n > 1 && sig[n - 1] < uh * sig[0])
         atomicOr(&info->flags, FLAG_NOT_FULL_RANK);  // sigma_n / sigma_1 below u_h
     for (int idx = tid; idx < n * n; idx += blockDim.x) {
         const int r = idx % n, k = idx / n;
@@ -227,14 +227,14 @@ cudaError_t launch_jacobi(const double* M, int n, int64_t ldm, double tol, int m
 
 cudaError_t launch_finish(const double* lam_ws, const double* V_ws, int n, int working,
                           void* sigma_w, void* V_w, int64_t ldv, void* W_w, double* lam_sorted,
-                          double* V_sorted, int64_t ld_vs, DevInfo* info, cudaStream_t s) {
+                          double* V_sorted, int64_t ld_vs, DevInfo* info, cudaStream_t s, double uh) {
     if (n > 256) return cudaErrorNotSupported;
     if (working == 0)
         finish_kernel<float><<<1, 256, 0, s>>>(lam_ws, V_ws, n, (float*)sigma_w, (float*)V_w, ldv,
-                                               (float*)W_w, lam_sorted, V_sorted, ld_vs, info);
+                                               (float*)W_w, lam_sorted, V_sorted, ld_vs, info, uh);
     else
         finish_kernel<double><<<1, 256, 0, s>>>(lam_ws, V_ws, n, (double*)sigma_w, (double*)V_w,
-                                                ldv, (double*)W_w, lam_sorted, V_sorted, ld_vs, info);
+                                                ldv, (double*)W_w, lam_sorted, V_sorted, ld_vs, info, uh);
     return cudaGetLastError();
 }
 

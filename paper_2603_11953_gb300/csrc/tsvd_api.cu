@@ -99,6 +99,41 @@ bool use_tc(tsvd_ctx* h, const void* A, int working, int n, int64_t lda) {
     return h->opts.gram_variant == 0 && gram_tc_ok(A, working, n, lda);
 }
 
+// FP64 working precision on the tensor cores: exact 23-bit pieces of the
+// column-scaled A, the Gram of the needed 32-column block pairs of the piece
+// matrix X into the double-double G3, then the piece sums into G (and G_lo).
+bool use_fp64_pieces(tsvd_ctx* h, int working, int64_t n) {
+    return working == TSVD_FP64 && h->opts.gram_variant == 0 && n <= 64;
+}
+
+tsvd_status run_gram_fp64(tsvd_ctx* h, const void* A, int64_t m, int n, int64_t lda, double* G, double* G_lo,
+                          int64_t ldg, size_t part_off) {
+    const GramPlan plan = gram_tc_plan(m, 64, h->sm_count, h->opts.split_k);
+    char* part = base(h) + part_off;
+    void* extra = part + align_up(gram_partials_bytes(plan));
+    cudaError_t e = launch_fp64_split(static_cast<const double*>(A), m, n, lda, extra, h->dinfo, h->stream);
+    if (e != cudaSuccess) return from_cuda(e);
+    const float* X = fp64_split_matrix(extra);
+    const int C = 4 * fp64_block_cols(n);
+    const int64_t ldx = fp64_split_ld(m);
+    double* g3lo = nullptr;
+    double* g3 = fp64_g3(extra, m, n, &g3lo);
+    const int nb = C / 32;
+    bool diag_done[8] = {false, false, false, false, false, false, false, false};
+    for (int b1 = 0; b1 < nb - 1; ++b1)
+        for (int b2 = b1 + 1; b2 < nb; ++b2) {
+            if (!fp64_pair_needed(n, b1, b2)) continue;
+            int wmask = 4;
+            if (!diag_done[b1] && fp64_pair_needed(n, b1, b1)) { wmask |= 1; diag_done[b1] = true; }
+            if (!diag_done[b2] && fp64_pair_needed(n, b2, b2)) { wmask |= 2; diag_done[b2] = true; }
+            e = launch_gram_tc2(X, m, C, ldx, 32 * b1, 32 * b2, plan, part, h->dinfo, h->stream);
+            if (e == cudaSuccess)
+                e = launch_gram_combine2(plan, part, C, 32 * b1, 32 * b2, wmask, g3, g3lo, C, h->stream);
+            if (e != cudaSuccess) return from_cuda(e);
+        }
+    return from_cuda(launch_fp64_fold(extra, m, n, G, G_lo, ldg, h->stream));
+}
+
 // Gram into G (and G_lo) for one matrix.  Caller validated the arguments.
 tsvd_status run_gram(tsvd_ctx* h, const void* A, int64_t m, int n, int64_t lda, int working,
                      double* G, double* G_lo, int64_t ldg, size_t part_off) {
@@ -109,6 +144,7 @@ tsvd_status run_gram(tsvd_ctx* h, const void* A, int64_t m, int n, int64_t lda, 
         if (e == cudaSuccess && G_lo) e = cudaMemsetAsync(G_lo, 0, sizeof(double) * ldg * n, h->stream);
         return from_cuda(e);
     }
+    if (use_fp64_pieces(h, working, n)) return run_gram_fp64(h, A, m, n, lda, G, G_lo, ldg, part_off);
     const bool tc = use_tc(h, A, working, n, lda);
     if (tc && n > 64) {
         // 32-column blocks b1 < b2, one launch per pair: the cross tile always, block b1's
@@ -136,12 +172,15 @@ tsvd_status run_gram(tsvd_ctx* h, const void* A, int64_t m, int n, int64_t lda, 
 
 size_t part_bytes_for(tsvd_ctx* h, const void* A, int working, int64_t m, int n, int64_t lda) {
     if (h->opts.gram_variant == 1) return gram_plain_partials_bytes(m, n, h->sm_count);
+    if (use_fp64_pieces(h, working, n))
+        return align_up(gram_partials_bytes(gram_tc_plan(m, 64, h->sm_count, h->opts.split_k))) +
+               fp64_extra_bytes(m, n);
     if (use_tc(h, A, working, n, lda)) return gram_partials_bytes(gram_tc_plan(m, n, h->sm_count, h->opts.split_k));
     return gram_partials_bytes(gram_plan(m, n, h->sm_count, h->opts.split_k));
 }
 
 bool gram_supported(tsvd_ctx* h, const void* A, int working, int64_t n, int64_t lda) {
-    if (h->opts.gram_variant != 1 && working != TSVD_FP32) return false;
+    if (working == TSVD_FP64) return h->opts.gram_variant == 1 ? n <= 64 : use_fp64_pieces(h, working, n);
     if (n <= 64) return true;
     // 64 < n <= 256: the tensor-core Gram over pairs of 32-column blocks
     return n <= 256 && use_tc(h, A, working, (int)n, lda);
@@ -149,6 +188,10 @@ bool gram_supported(tsvd_ctx* h, const void* A, int working, int64_t n, int64_t 
 
 double jacobi_tol(tsvd_ctx* h, int64_t n) {
     return h->opts.jacobi_tol > 0.0 ? h->opts.jacobi_tol : (double)n * U_FP64;
+}
+constexpr double U_DD = 4.930380657631324e-32;  // 2^-104
+double jacobi_tol_dd(tsvd_ctx* h, int64_t n) {
+    return h->opts.jacobi_tol > 0.0 ? h->opts.jacobi_tol : (double)n * U_DD;
 }
 int max_sweeps(tsvd_ctx* h) { return h->opts.max_sweeps > 0 ? h->opts.max_sweeps : 40; }
 
@@ -169,7 +212,7 @@ void record(tsvd_ctx* h, int k) {
 }
 
 // One instance of Algorithm 1, workspace already sized by the caller.
-tsvd_status solve_one(tsvd_ctx* h, const void* A, int64_t m, int n, int64_t lda, int working,
+tsvd_status solve_one(tsvd_ctx* h, const void* A, int64_t m, int n, int64_t lda, int working, int higher,
                       void* sigma, void* V, int64_t ldv, void* U, int64_t ldu, tsvd_info* info,
                       bool timed) {
     const Layout L = layout_for(n, part_bytes_for(h, A, working, m, n, lda), working);
@@ -181,12 +224,17 @@ tsvd_status solve_one(tsvd_ctx* h, const void* A, int64_t m, int n, int64_t lda,
     double* scratch = reinterpret_cast<double*>(base(h) + L.scratch);
     void* W = base(h) + L.W;
     if (timed) record(h, 0);
-    tsvd_status st = run_gram(h, A, m, n, lda, working, G, nullptr, n, L.part);
+    // double-double n x n stage: FP64 working with the double-double Gram
+    const bool dd_eig = higher == TSVD_DD && use_fp64_pieces(h, working, n);
+    double* G_lo = dd_eig ? reinterpret_cast<double*>(base(h) + L.Glo) : nullptr;
+    tsvd_status st = run_gram(h, A, m, n, lda, working, G, G_lo, n, L.part);
     if (st != TSVD_OK) return st;
     if (timed) record(h, 1);
-    e = run_eig(h, G, n, n, scratch, lam, Vh);
+    e = dd_eig ? launch_eig_dd(G, G_lo, n, n, jacobi_tol_dd(h, n), max_sweeps(h), lam, Vh, h->dinfo, h->stream)
+               : run_eig(h, G, n, n, scratch, lam, Vh);
     if (e != cudaSuccess) return from_cuda(e);
-    e = launch_finish(lam, Vh, n, working, sigma, V, ldv, W, nullptr, nullptr, 0, h->dinfo, h->stream);
+    e = launch_finish(lam, Vh, n, working, sigma, V, ldv, W, nullptr, nullptr, 0, h->dinfo, h->stream,
+                      dd_eig ? U_DD : U_FP64);
     if (e != cudaSuccess) return from_cuda(e);
     if (timed) record(h, 2);
     if (U) {
@@ -330,14 +378,18 @@ tsvd_status tsvd_solve(tsvd_handle h, const void* A, int64_t m, int64_t n, int64
     if (!h || !A || !sigma || !V || n < 1 || m < n || lda < m || ldv < n || (U && ldu < m) ||
         !valid_prec_pair(working, higher))
         return TSVD_ERR_ARG;
-    if (!(working == TSVD_FP32 && higher == TSVD_FP64)) return TSVD_ERR_UNSUPPORTED;
+    // FP32 working: FP64 n x n stage.  FP64 working: double-double Gram, then a
+    // double-double (higher = DD) or FP64 (higher = FP64) n x n stage; the plain
+    // FP64 Gram (gram_variant 1) has no double-double form.
+    if (working == TSVD_FP32 && higher != TSVD_FP64) return TSVD_ERR_UNSUPPORTED;
+    if (higher == TSVD_DD && h->opts.gram_variant == 1) return TSVD_ERR_UNSUPPORTED;
     if (!gram_supported(h, A, working, n, lda)) return TSVD_ERR_UNSUPPORTED;
     DeviceGuard g(h->device);
     const Layout L = layout_for(n, part_bytes_for(h, A, working, m, (int)n, lda), working);
     tsvd_status st = ensure_ws(h, L.total);
     if (st != TSVD_OK) return st;
     h->have_times = false;
-    return solve_one(h, A, m, (int)n, lda, working, sigma, V, ldv, U, ldu, info, true);
+    return solve_one(h, A, m, (int)n, lda, working, higher, sigma, V, ldv, U, ldu, info, true);
 }
 
 tsvd_status tsvd_batch_solve(tsvd_handle h, int32_t count, const void* const* A, const int64_t* m,
@@ -364,7 +416,7 @@ tsvd_status tsvd_batch_solve(tsvd_handle h, int32_t count, const void* const* A,
     h->have_times = false;
     for (int32_t i = 0; i < count; ++i) {
         const bool want_u = U && U[i];
-        st = solve_one(h, A[i], m[i], (int)n[i], lda[i], working, sigma[i], V[i], ldv[i],
+        st = solve_one(h, A[i], m[i], (int)n[i], lda[i], working, higher, sigma[i], V[i], ldv[i],
                        want_u ? U[i] : nullptr, want_u ? ldu[i] : 0, info ? info + i : nullptr, false);
         if (st != TSVD_OK) return st;
     }

@@ -290,6 +290,125 @@ def test_batch_ragged_workload_matches_oracle():
         assert rel.max() <= 1e-5, (k, m, n, rel.max())
 
 
+# ------------------------------------------------------------------ FP64 working (double-double Gram and n x n stage)
+def gpu_gram64(A, m, n, lda, higher=T.TSVD_DD):
+    h = handle()
+    G = torch.zeros(2 * n * n, dtype=torch.float64, device="cuda")
+    T.tsvd_gram(h, A, m, n, lda, T.TSVD_FP64, higher, G, n)
+    st = T.tsvd_sync_status(h)
+    T.tsvd_destroy(h)
+    return G[: n * n].view(n, n).T.cpu().numpy(), G[n * n:].view(n, n).T.cpu().numpy(), st
+
+
+def pow2_above(A):
+    """2^e_j with e_j the least integer such that max_r |a_rj| < 2^e_j (1 for a zero column)."""
+    mx = np.abs(A).max(axis=0).astype(np.float64)
+    return np.where(mx > 0, np.ldexp(1.0, np.frexp(mx)[1]), 1.0)
+
+
+def check_gram64(A_np, Gh, Gl, m):
+    """|G - S| <= 2^-88 m 2^(e_i + e_j): the 23-bit pieces' remainder (< 2^-92 of 2^e per entry) and the
+    six piece pairs p + q >= 4 that are left out, each at most 2^-92 m 2^(e_i + e_j), plus the
+    double-double roundings.  A missing pair with p + q <= 3 is at least ~2^-69 sqrt(m) 2^(e_i + e_j)."""
+    S_hi, S_lo, _ = oracle.gram(A_np)
+    err = np.abs((Gh - S_hi) + (Gl - S_lo))
+    p2 = pow2_above(A_np)
+    bound = 2.0 ** -88 * m * np.outer(p2, p2)
+    assert np.all(err <= bound), float(np.max(err / bound))
+    diag = np.sqrt(np.outer(np.diag(S_hi), np.diag(S_hi)))
+    return float(np.max(np.where(diag > 0, err / np.where(diag > 0, diag, 1.0), 0.0)))
+
+
+@pytest.mark.parametrize("m,n", [(1000, 1), (5003, 7), (20000, 32), (131077, 33), (70001, 64)])
+def test_gram_fp64_is_double_double(m, n):
+    A, _ = workloads.small_case(m, n, kappa_sigma=1e6, logd=6.0, seed=3 * m + n, dtype=torch.float64,
+                                device="cuda")
+    Gh, Gl, st = gpu_gram64(A, m, n, m)
+    assert st == T.TSVD_OK
+    A_np = workloads.to_numpy_colmajor(A, m)
+    worst = check_gram64(A_np, Gh, Gl, m)
+    assert worst <= 2.0 ** -80, worst
+    assert np.array_equal(Gh, Gh.T) and np.array_equal(Gl, Gl.T)
+    # FP64 output: the high part alone
+    Gh2, _, st = gpu_gram64(A, m, n, m, higher=T.TSVD_FP64)
+    assert st == T.TSVD_OK and np.array_equal(Gh2, Gh)
+
+
+def test_gram_fp64_graded_columns_zero_column_and_lda():
+    """Entries spread over 200 binades inside one column, a late large entry (the tensor-core
+    kernel's scales grow during the pass), a zero column, and lda > m."""
+    m, n, lda = 9001, 5, 9010
+    rng = np.random.default_rng(11)
+    A = np.zeros((lda, n))
+    A[:m, 0] = rng.standard_normal(m) * np.ldexp(1.0, rng.integers(-100, 100, m))
+    A[:m, 1] = rng.standard_normal(m) * 1e-3
+    A[m - 7, 1] = 5e4
+    A[:m, 3] = rng.standard_normal(m)
+    A[:m, 4] = -A[:m, 3] + rng.standard_normal(m) * 2.0 ** -40  # nearly cancelling pair
+    At = torch.from_numpy(A.T.copy()).to("cuda").T  # column-major (lda, n)
+    Gh, Gl, st = gpu_gram64(At, m, n, lda)
+    assert st == T.TSVD_OK
+    check_gram64(A[:m], Gh, Gl, m)
+    assert Gh[2].tolist() == [0.0] * n and Gl[2].tolist() == [0.0] * n
+
+
+def gpu_solve64(A, m, n, lda, higher=T.TSVD_DD, want_u=True):
+    h = handle()
+    sigma = torch.zeros(n, dtype=torch.float64, device="cuda")
+    V = colmajor(n, n, torch.float64)
+    U = colmajor(max(m, 1), n, torch.float64) if want_u else None
+    info = torch.zeros(6, dtype=torch.int32, device="cuda")
+    T.tsvd_solve(h, A, m, n, lda, T.TSVD_FP64, higher, sigma, V, n, U, m if want_u else 0, info)
+    torch.cuda.synchronize()
+    T.tsvd_destroy(h)
+    inf = info.cpu().numpy()
+    return (sigma.cpu().numpy(), V.cpu().numpy(), None if U is None else U[:m].cpu().numpy(), int(inf[0]),
+            int(inf[1]))
+
+
+@pytest.mark.parametrize("m,n,kappa,logd", [(4000, 8, 1e6, 6.0), (20000, 32, 1e6, 6.0), (50001, 17, 1e4, 3.0),
+                                            (3000, 64, 1e5, 4.0), (64, 1, 1.0, 0.0)])
+def test_solve_fp64_matches_double_double_oracle(m, n, kappa, logd):
+    """sigma within 1e-12 relative of the oracle's double-double Algorithm 1 (exact Gram, DD Jacobi)
+    at kappa(B) up to ~1e6; V within 1e-10 (well separated geometric spectra); U against the
+    exact product with the same W = RN_64(V / sigma), componentwise (n + 1) u_64 (|A| |W|)."""
+    A, _ = workloads.small_case(m, n, kappa_sigma=kappa, logd=logd, seed=5 * m + n, dtype=torch.float64,
+                                device="cuda")
+    sig, V, U, st, sweeps = gpu_solve64(A, m, n, m)
+    assert st == T.TSVD_OK, st
+    A_np = workloads.to_numpy_colmajor(A, m)
+    ref = oracle.svd(A_np, higher=2)
+    assert ref["status"] == 0
+    s_ref = ref["sigma_h"] + ref["sigma_h_lo"]
+    rel = np.abs(sig - ref["sigma_h"] - ref["sigma_h_lo"]) / s_ref
+    assert rel.max() <= 1e-12, rel.max()
+    assert np.abs(V - ref["V_h"]).max() <= 1e-10
+    W = V / sig[None, :]
+    rows = np.unique(np.linspace(0, m - 1, 257).astype(np.int64))
+    U_ref = oracle.rows_times(A_np, W, rows, 53)
+    bound = (n + 1) * UH * (np.abs(A_np[rows]) @ np.abs(W))
+    assert np.all(np.abs(U[rows] - U_ref) <= bound)
+
+
+def test_solve_fp64_with_fp64_stage_and_statuses():
+    """higher = FP64 runs the FP64 n x n stage on the double-double Gram's high part (C11's
+    literal reading); rank deficiency and the plain Gram's missing double-double form are reported."""
+    m, n = 6000, 12
+    A, _ = workloads.small_case(m, n, kappa_sigma=1e2, logd=1.0, seed=77, dtype=torch.float64, device="cuda")
+    sig, V, U, st, _ = gpu_solve64(A, m, n, m, higher=T.TSVD_FP64, want_u=False)
+    assert st == T.TSVD_OK
+    ref = oracle.svd(workloads.to_numpy_colmajor(A, m), higher=2)
+    assert (np.abs(sig - ref["sigma_h"]) / ref["sigma_h"]).max() <= 1e-12
+    C = A.clone()
+    C[:, 4] = 0.0
+    assert gpu_solve64(C, m, n, m, want_u=False)[3] == T.TSVD_ERR_NOT_FULL_RANK
+    h = handle(gram_variant=1)
+    sigma = torch.zeros(n, dtype=torch.float64, device="cuda")
+    Vt = colmajor(n, n, torch.float64)
+    assert T.tsvd_solve(h, A, m, n, m, T.TSVD_FP64, T.TSVD_DD, sigma, Vt, n, check=False) == T.TSVD_ERR_UNSUPPORTED
+    T.tsvd_destroy(h)
+
+
 # ------------------------------------------------------------------ statuses and arguments
 def test_status_nonfinite_rank_convergence_and_args():
     m, n = 4096, 8
