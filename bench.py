@@ -126,15 +126,17 @@ def max_over_ranks(x, world, device):
 
 
 def cpu_baseline(A_cpu, m, n, rows, reps=1):
-    """The oracle as it stands (single thread) on the first `rows` rows."""
+    """The oracle as it stands (single thread) on the first `rows` rows: FP64 n x n stage for
+    FP32 inputs, double-double for FP64 inputs."""
     import numpy as np
     import oracle
     from paper_2603_11953_gb300 import workloads
     An = workloads.to_numpy_colmajor(A_cpu, rows)
+    fp64 = An.dtype == np.float64
     t0 = time.perf_counter()
     for _ in range(reps):
-        r = oracle.svd(An, higher=1)
-        oracle.rows_times(An, r["W_w"], np.arange(rows), 24)
+        r = oracle.svd(An, higher=2 if fp64 else 1)
+        oracle.rows_times(An, r["W_w"], np.arange(rows), 53 if fp64 else 24)
     dt = (time.perf_counter() - t0) / reps
     gbs = rows * n * An.itemsize / dt / 1e9
     return gbs, dt
@@ -160,11 +162,13 @@ def run_reference(args):
     gbs = args.steps * rows * spec.n * A.element_size() / tot / 1e9
     line = {"impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "fp32",
-            "data": "synthetic",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "fp32" if spec.dtype == torch.float32 else "fp64", "data": "synthetic",
             "config": {"workload": spec.name, "m_sample": rows, "n": spec.n, "m_full": spec.m},
             "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
-                             "sample": f"first {rows} rows of {spec.name}: exact Gram + FP64 Jacobi + exact U rows"},
+                             "sample": f"first {rows} rows of {spec.name}: exact Gram + "
+                                       f"{'FP64' if spec.dtype == torch.float32 else 'double-double'} "
+                                       "Jacobi + exact U rows"},
             "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -277,14 +281,15 @@ def main():
     # the all-FP64 plain form of the same method (FP64 DFMA Gram, same Jacobi / U)
     plain = None
     if not args.no_plain and n <= 64:
+        # FP64 Gram and FP64 n x n stage (the plain form has no double-double Gram)
         hp, _ = T.tsvd_create(local, stream.cuda_stream, T.tsvd_opts(timing=1, gram_variant=1))
-        T.tsvd_solve(hp, A, m, n, m, working, higher, sigma, V, n, U, m, info)
+        T.tsvd_solve(hp, A, m, n, m, working, T.TSVD_FP64, sigma, V, n, U, m, info)
         torch.cuda.synchronize(dev)
         kp = 3
         p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         p0.record(stream)
         for _ in range(kp):
-            T.tsvd_solve(hp, A, m, n, m, working, higher, sigma, V, n, U, m, info)
+            T.tsvd_solve(hp, A, m, n, m, working, T.TSVD_FP64, sigma, V, n, U, m, info)
         p1.record(stream)
         torch.cuda.synchronize(dev)
         pst = T.tsvd_last_stage_ms(hp)
@@ -308,15 +313,30 @@ def main():
     # FP64 peak of the SMs the n x n stage uses: a 16-CTA cluster (8 for n <= 32), one CTA per
     # SM, at the measured 1.68 DFMA lanes per clock per SM (2 flops each)
     eig_sms = 16 if n > 32 else 8 if n > 16 else 2 if n > 8 else 1
-    fp64_peak = eig_sms * 2 * FP64_DFMA_PER_CLK_SM * pk["sm_max_mhz"] * 1e6 / 1e9
+    sm_fp64 = 2 * FP64_DFMA_PER_CLK_SM * pk["sm_max_mhz"] * 1e6 / 1e9
+    fp64_peak = eig_sms * sm_fp64
+    launches = KERNELS_PER_STEP
+    u_cand = {"bound": "hbm", "achieved": u_bytes / (u_ms * 1e-3) / 1e9, "peak": pk["hbm"], "unit": "GB/s"}
+    if working == T.TSVD_FP64:
+        # pieces Gram: one 64-column tensor-core pass per needed 32-column block pair of the
+        # m x 4NB piece matrix; double-double n x n stage on one SM (about 20 FP64 operations per
+        # double-double multiply-add); U = A W in FP64 on every SM
+        nbp = ((n + 31) // 32 * 32) // 32
+        npass = sum(1 for b1 in range(4 * nbp) for b2 in range(b1 + 1, 4 * nbp) if b1 // nbp + b2 // nbp <= 3)
+        gram_flops = npass * 16 * 2.0 * m * 64 * 64
+        jac_flops = 20.0 * (n ** 3 / 3.0 + sweeps * (n * (n - 1) // 2) * 8 * n)
+        fp64_peak = sm_fp64
+        u_cand = {"bound": "alu", "achieved": 2.0 * m * n * n / (u_ms * 1e-3) / 1e9,
+                  "peak": 152 * sm_fp64, "unit": "GFLOP/s", "hbm_gbs": u_bytes / (u_ms * 1e-3) / 1e9}
+        # colmax, split, npass x (gram_tc + combine), fold, eig_dd, finish, compute_u, finalize
+        launches = 2 + 2 * npass + 5
     cands = {
         "gram": (gram_ms, {"bound": "tensor", "achieved": gram_flops / (gram_ms * 1e-3) / 1e12,
                            "peak": pk["bf16_sus"], "unit": "TFLOP/s",
                            "hbm_gbs": gram_bytes / (gram_ms * 1e-3) / 1e9}),
         "jacobi": (eig_ms, {"bound": "alu", "achieved": jac_flops / (eig_ms * 1e-3) / 1e9,
                             "peak": fp64_peak, "unit": "GFLOP/s"}),
-        "compute_u": (u_ms, {"bound": "hbm", "achieved": u_bytes / (u_ms * 1e-3) / 1e9,
-                             "peak": pk["hbm"], "unit": "GB/s"}),
+        "compute_u": (u_ms, u_cand),
     }
     dom = max(cands, key=lambda k: cands[k][0])
     rl = dict(cands[dom][1])
@@ -336,17 +356,19 @@ def main():
         A_cpu = A[:rows].cpu()
         gbs, dt = cpu_baseline(A_cpu, rows, n, rows)
         cpu = {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
-               "sample": f"first {rows} rows of {spec.name}: exact Gram + FP64 Jacobi + exact U rows ({dt:.1f} s)"}
+               "sample": f"first {rows} rows of {spec.name}: exact Gram + "
+                         f"{'FP64' if working == T.TSVD_FP32 else 'double-double'} Jacobi + exact U rows "
+                         f"({dt:.1f} s)"}
 
     line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "fp32", "data": "synthetic",
+            "vs_baseline": None, "dtype": "fp32" if working == T.TSVD_FP32 else "fp64", "data": "synthetic",
             "config": {"workload": spec.name, "m": m, "n": n, "working": "fp32" if working == 0 else "fp64",
                        "higher": "fp64" if higher == 1 else "dd", "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (A is %.2f GB > 129 MB)" % (bytes_A / 1e9),
                        "status": T.tsvd_status_string(status)},
             "roofline": rl, "stages": stages, "fp64_plain": plain, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": KERNELS_PER_STEP * args.steps, "clocks": clocks,
+            "gpu_launches": launches * args.steps, "clocks": clocks,
             "hbm_frac_of_A_stream": (bytes_A / (ms_step * 1e-3) / 1e9) / pk["hbm"]}
     T.tsvd_destroy(h)
     if rank == 0:

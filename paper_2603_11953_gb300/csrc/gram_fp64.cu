@@ -4,7 +4,8 @@
 //
 // Column j is scaled by 2^-e_j (exact), e_j the least integer with
 // max_k |a_kj| < 2^e_j, and the scaled entry s (|s| < 1) is cut into four
-// 23-bit fixed-point pieces by truncation toward zero:
+// 23-bit fixed-point pieces by truncation toward zero (formed from the IEEE
+// bit pattern with integer shifts):
 //     s = x_0 + x_1 + x_2 + x_3 + r,   x_p an integer times 2^-23(p+1),
 //     |x_p| < 2^-23p,  |r| < 2^-92.
 // Every x_p is exact in FP32.  The pieces go to an m x 4NB FP32 matrix X
@@ -25,21 +26,22 @@ constexpr int PIECES = 4;
 constexpr int PIECE_BITS = 23;
 
 // per column: the largest |a| as a bit pattern (non-negative doubles order like
-// their patterns)
+// their patterns); blocks over (row range, column), one atomicMax per block
+// into cmax (zeroed by the caller)
 __global__ void __launch_bounds__(256) colmax_kernel(const double* __restrict__ A, int64_t m, int64_t lda,
                                                      unsigned long long* __restrict__ cmax) {
-    const int j = blockIdx.x;
-    const double* col = A + (size_t)j * lda;
+    const int j = blockIdx.y;
+    const long long* col = reinterpret_cast<const long long*>(A) + (size_t)j * lda;
     unsigned long long mx = 0;
-    for (int64_t r = threadIdx.x; r < m; r += blockDim.x)
-        mx = max(mx, (unsigned long long)__double_as_longlong(col[r]) & 0x7fffffffffffffffull);
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < m; r += (int64_t)gridDim.x * blockDim.x)
+        mx = max(mx, (unsigned long long)col[r] & 0x7fffffffffffffffull);
     for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     __shared__ unsigned long long s[8];
     if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = mx;
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = max(mx, s[w]);
-        cmax[j] = mx;
+        if (mx) atomicMax(&cmax[j], mx);
     }
 }
 
@@ -52,6 +54,32 @@ __device__ __forceinline__ int col_exponent(unsigned long long mb) {
     return ex;
 }
 
+// |a| 2^(92 - e) truncated to an integer F < 2^92, as (hi, lo) 64-bit words,
+// from the bit pattern of a (integer arithmetic only: the FP64 pipe is narrow)
+__device__ __forceinline__ void fixed92(unsigned long long bits, int e, unsigned long long& hi,
+                                        unsigned long long& lo) {
+    const int eb = (int)((bits >> 52) & 0x7ff);
+    unsigned long long M = bits & 0xfffffffffffffull;
+    int q = -1074;  // |a| = M 2^q
+    if (eb != 0) {
+        M |= 1ull << 52;
+        q = eb - 1075;
+    }
+    const int sh = q + 92 - e;  // <= 91; F = M 2^sh < 2^92 because |a| < 2^e
+    hi = 0ull;
+    lo = 0ull;
+    if (eb == 0x7ff || M == 0ull) return;
+    if (sh >= 64) {
+        hi = M << (sh - 64);
+    } else if (sh > 0) {
+        lo = M << sh;
+        hi = M >> (64 - sh);
+    } else if (sh > -64) {
+        lo = M >> (-sh);
+    }
+}
+
+// piece p of column j -> X[:, p NB + j]: bits [69 - 23p, 92 - 23p) of F, times 2^-23(p+1), with a's sign
 __global__ void __launch_bounds__(256) split_kernel(const double* __restrict__ A, int64_t m, int n, int64_t lda,
                                                     const unsigned long long* __restrict__ cmax, int NB,
                                                     float* __restrict__ X, int64_t ldx, int* __restrict__ e_out,
@@ -66,19 +94,19 @@ __global__ void __launch_bounds__(256) split_kernel(const double* __restrict__ A
             if (mb >= 0x7ff0000000000000ull) atomicOr(&info->flags, FLAG_NONFINITE);
         }
     }
-    const double* col = A + (size_t)j * lda;
+    const long long* col = reinterpret_cast<const long long*>(A) + (size_t)j * lda;
+    constexpr unsigned MASK = (1u << PIECE_BITS) - 1u;
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < ldx; r += (int64_t)gridDim.x * blockDim.x) {
         float x[PIECES] = {0.f, 0.f, 0.f, 0.f};
         if (j < n && r < m) {
-            double s = ldexp(col[r], -ex);
-            if (!isfinite(s)) s = 0.0;
-#pragma unroll
-            for (int p = 0; p < PIECES; ++p) {
-                const int sh = PIECE_BITS * (p + 1);
-                const double q = ldexp(trunc(ldexp(s, sh)), -sh);  // leading bits of s, exact
-                x[p] = (float)q;                                     // exact: < 2^23 units of 2^-sh
-                s -= q;                                              // exact
-            }
+            const unsigned long long bits = (unsigned long long)col[r];
+            unsigned long long hi, lo;
+            fixed92(bits, ex, hi, lo);
+            const float sg = (bits >> 63) ? -1.f : 1.f;
+            x[0] = sg * __uint2float_rn((unsigned)(hi >> 5) & MASK) * 0x1p-23f;
+            x[1] = sg * __uint2float_rn((unsigned)((lo >> 46) | (hi << 18)) & MASK) * 0x1p-46f;
+            x[2] = sg * __uint2float_rn((unsigned)(lo >> 23) & MASK) * 0x1p-69f;
+            x[3] = sg * __uint2float_rn((unsigned)lo & MASK) * 0x1p-92f;
         }
 #pragma unroll
         for (int p = 0; p < PIECES; ++p) X[r + (size_t)(p * NB + j) * ldx] = x[p];
@@ -158,12 +186,14 @@ cudaError_t launch_fp64_split(const double* A, int64_t m, int n, int64_t lda, vo
     const Fp64Layout L = fp64_layout(m, n);
     char* p = static_cast<char*>(extra);
     unsigned long long* cmax = reinterpret_cast<unsigned long long*>(p + L.cmax);
-    colmax_kernel<<<n, 256, 0, s>>>(A, m, lda, cmax);
-    cudaError_t err = cudaGetLastError();
-    if (err != cudaSuccess) return err;
     const int64_t ldx = fp64_split_ld(m);
     int64_t bx = (ldx + 255) / 256;
     if (bx > 148) bx = 148;
+    cudaError_t err = cudaMemsetAsync(cmax, 0, sizeof(unsigned long long) * n, s);
+    if (err != cudaSuccess) return err;
+    colmax_kernel<<<dim3((unsigned)bx, (unsigned)n), 256, 0, s>>>(A, m, lda, cmax);
+    err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
     const int NB = fp64_block_cols(n);
     split_kernel<<<dim3((unsigned)bx, (unsigned)NB), 256, 0, s>>>(A, m, n, lda, cmax, NB,
                                                                    reinterpret_cast<float*>(p + L.X), ldx,

@@ -620,7 +620,8 @@ GramPlan gram_tc_plan(int64_t m, int n, int sm_count, int split_k_opt) {
     const int64_t subs = (m + TC_SUB - 1) / TC_SUB;
     int64_t P = split_k_opt > 0 ? split_k_opt : sm_count;
     const int64_t min_P = (m + GRAM_MAX_ROWS_PER_CTA - 1) / GRAM_MAX_ROWS_PER_CTA;
-    if (P < min_P) P = min_P;
+    // more CTAs than SMs (one CTA per SM at a time): whole waves of equal row counts
+    if (P < min_P) P = split_k_opt > 0 ? min_P : (min_P + sm_count - 1) / sm_count * sm_count;
     if (P > subs) P = subs;
     if (P < 1) P = 1;
     p.rows_per_cta = (subs + P - 1) / P * TC_SUB;

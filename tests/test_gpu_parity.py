@@ -473,3 +473,42 @@ def test_full_size_sampled(name):
     Ut = torch.from_numpy(U).cuda()
     orth = (Ut.T @ Ut - torch.eye(n, dtype=torch.float64, device="cuda")).abs().max().item()
     assert orth <= 1e-3, orth
+
+
+def test_full_size_sampled_fp64_stress():
+    """The 16,777,216 x 32 FP64 workload (geometric 1 -> 1e-6, D = 10^U(-6, 6)) in the launch
+    configuration the benchmark times: sampled Gram entries against the exact oracle (column pairs
+    one by one), the double-double n x n stage on the GPU's own Gram against the oracle's
+    double-double Jacobi, and sampled U rows against the exact product."""
+    spec = workloads.CONFIGS["stress_16777216x32_fp64"]
+    A, _ = workloads.make_config(spec, device="cuda")
+    m, n = spec.m, spec.n
+    h = handle()
+    G = torch.zeros(2 * n * n, dtype=torch.float64, device="cuda")
+    T.tsvd_gram(h, A, m, n, m, T.TSVD_FP64, T.TSVD_DD, G, n)
+    T.tsvd_destroy(h)
+    sig, V, U, st, _ = gpu_solve64(A, m, n, m)
+    assert st == T.TSVD_OK
+    Gh = G[: n * n].view(n, n).T.cpu().numpy()
+    Gl = G[n * n:].view(n, n).T.cpu().numpy()
+    rng = np.random.default_rng(1)
+    pairs = [(0, 0), (n - 1, n - 1), (0, n - 1)] + [tuple(sorted(rng.integers(0, n, 2))) for _ in range(3)]
+    for i, j in pairs:
+        cols = sorted({i, j})
+        Ac = np.asfortranarray(A[:m, cols].cpu().numpy())
+        S_hi, S_lo, _ = oracle.gram(Ac)
+        a, b = cols.index(i), cols.index(j)
+        p2 = pow2_above(Ac)
+        err = abs((Gh[i, j] - S_hi[a, b]) + (Gl[i, j] - S_lo[a, b]))
+        assert err <= 2.0 ** -88 * m * p2[a] * p2[b], (i, j, err)
+    lh, ll, _, _, _, st_o = oracle.jacobi_dd(Gh, Gl)
+    assert st_o == 0
+    lam_o = np.sort(lh + ll)[::-1]
+    sig_o = np.sqrt(lam_o)
+    assert np.all(np.abs(sig - sig_o) <= 1e-12 * sig_o), float(np.max(np.abs(sig - sig_o) / sig_o))
+    W = V / sig[None, :]
+    rows = np.unique(np.concatenate([[0, 1, m - 1], rng.integers(0, m, 61)]))
+    A_rows = A[torch.from_numpy(rows).cuda()].cpu().numpy()
+    U_ref = oracle.rows_times(np.asfortranarray(A_rows), W, np.arange(len(rows)), 53)
+    bound = (n + 1) * UH * (np.abs(A_rows) @ np.abs(W))
+    assert np.all(np.abs(U[rows] - U_ref) <= bound)
