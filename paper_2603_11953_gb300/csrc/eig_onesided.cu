@@ -212,6 +212,11 @@ __global__ void __launch_bounds__(512) onesided_jacobi_kernel(OsParams prm) {
     __shared__ int s_rot;
     __shared__ int s_cnt[2];                 // used in CTA 0: per-sweep cluster totals
     __shared__ int s_total;
+    __shared__ int s_lmax;                   // this CTA's largest scaled |g| of the sweep (float bits)
+    __shared__ int s_mx[2];                  // used in CTA 0: per-sweep cluster maxima (float bits)
+    __shared__ int s_mx_total;
+    __shared__ int s_fail[2];                // used in CTA 0: failed pairs of a convergence check
+    __shared__ int s_fail_total;
     __shared__ int s_timeout;
     __shared__ float s_off[32];              // per warp: the largest scaled |g| left in the sweep
     __shared__ float s_off_cta;
@@ -230,6 +235,10 @@ __global__ void __launch_bounds__(512) onesided_jacobi_kernel(OsParams prm) {
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_cnt[0] = 0;
         s_cnt[1] = 0;
+        s_mx[0] = 0;
+        s_mx[1] = 0;
+        s_fail[0] = 0;
+        s_fail[1] = 0;
         s_timeout = 0;
     }
     // initial placement: local top u <- column cP+u, bottom u <- column np-1-cP-u
@@ -252,10 +261,13 @@ __global__ void __launch_bounds__(512) onesided_jacobi_kernel(OsParams prm) {
     bool converged = false;
     unsigned K = 0;  // global step counter (parity of buffers and mbarrier phases)
     float best_off = 0.0f;
+    float sweep_mx = 0.0f;  // lane 0 of a pair warp: the largest scaled |g| met in the sweep
+    int checks = 0;
     while (sweep < prm.max_sweeps) {
         ++sweep;
-        if (tid == 0) s_rot = 0;
+        if (tid == 0) { s_rot = 0; s_lmax = 0; }
         best_off = 0.0f;
+        sweep_mx = 0.0f;
         // exact squared norms at the start of the sweep
         for (int u = warp; u < 2 * P; u += blockDim.x / 32) {
             double* b = bufs + (size_t)u * LD;
@@ -296,6 +308,7 @@ __global__ void __launch_bounds__(512) onesided_jacobi_kernel(OsParams prm) {
                     if (in_range && rr > 2.0f * tl) rot = true;
                     else if (!in_range || rr > 0.5f * tl) rot = g * g > tol2 * (app * aqq);
                     if (!rot && lane == 0) best_off = fmaxf(best_off, rr);
+                    if (lane == 0) sweep_mx = fmaxf(sweep_mx, in_range ? rr : (rot ? 1.0f : 0.0f));
                 }
                 if (rot) {
                     // Rotation angle from Rutishauser's t = sgn(zeta)/(|zeta| + sqrt(1 + zeta^2)),
@@ -402,21 +415,70 @@ __global__ void __launch_bounds__(512) onesided_jacobi_kernel(OsParams prm) {
             }
             __syncthreads();
         }
-        // cluster-wide rotation count of this sweep
+        // cluster-wide rotation count and largest scaled |g| of this sweep
         const int sp = sweep & 1;
+        if (lane == 0 && warp < P) atomicMax(&s_lmax, __float_as_int(sweep_mx));
+        __syncthreads();
         if (tid == 0) {
-            int* cnt0 = cluster.map_shared_rank(s_cnt, 0);
-            atomicAdd(&cnt0[sp], s_rot);
+            atomicAdd(&cluster.map_shared_rank(s_cnt, 0)[sp], s_rot);
+            atomicMax(&cluster.map_shared_rank(s_mx, 0)[sp], s_lmax);
         }
         cluster.sync();
         if (tid == 0) {
-            int* cnt0 = cluster.map_shared_rank(s_cnt, 0);
-            s_total = cnt0[sp];
+            s_total = cluster.map_shared_rank(s_cnt, 0)[sp];
+            s_mx_total = cluster.map_shared_rank(s_mx, 0)[sp];
         }
         __syncthreads();
         const int total = s_total;
-        if (c == 0 && tid == 0) s_cnt[sp ^ 1] = 0;
+        const float mx = __int_as_float(s_mx_total);
+        if (c == 0 && tid == 0) { s_cnt[sp ^ 1] = 0; s_mx[sp ^ 1] = 0; }
         if (total == 0) { converged = true; break; }
+        // Jacobi converges quadratically: after a sweep in which every pair's scaled |g| was
+        // below 2^-20, the next sweep would normally only confirm convergence.  Instead, every
+        // pair of the current columns is tested at once (the same scaled test, exact norms);
+        // the sweep runs only if some pair fails.
+        if (mx < 0x1p-20f && sweep < prm.max_sweeps) {
+            for (int u = warp; u < 2 * P; u += blockDim.x / 32) {
+                double* b = bufs + (size_t)u * LD;
+                double s2 = 0.0;
+                for (int r = lane; r < n; r += 32) s2 += b[r] * b[r];
+                s2 = warp_sum(s2);
+                if (lane == 0) b[n + 1] = s2;
+            }
+            cluster.sync();
+            int fails = 0;
+            const int slots = 2 * P;
+            const int items = slots * slots * C;
+            for (int it = tid; it < items; it += blockDim.x) {
+                const int u = it % slots, w = (it / slots) % slots, rk = it / (slots * slots);
+                const double* bu = bufs + (size_t)u * LD;
+                const double* bv = cluster.map_shared_rank(bufs, rk) + (size_t)w * LD;
+                const long long iu = __double_as_longlong(bu[n]), iv = __double_as_longlong(bv[n]);
+                if (!(iu < iv && iv < n)) continue;
+                const double au = bu[n + 1], av = bv[n + 1];
+                if (!(au > 0.0 && av > 0.0)) continue;
+                double g0 = 0.0, g1 = 0.0, g2 = 0.0, g3 = 0.0;
+                int r = 0;
+                for (; r + 3 < n; r += 4) {
+                    g0 = fma(bu[r], bv[r], g0);
+                    g1 = fma(bu[r + 1], bv[r + 1], g1);
+                    g2 = fma(bu[r + 2], bv[r + 2], g2);
+                    g3 = fma(bu[r + 3], bv[r + 3], g3);
+                }
+                for (; r < n; ++r) g0 = fma(bu[r], bv[r], g0);
+                const double g = (g0 + g1) + (g2 + g3);
+                if (g * g > tol2 * (au * av)) ++fails;
+            }
+            const int cp = checks & 1;
+            ++checks;
+            if (fails) atomicAdd(&cluster.map_shared_rank(s_fail, 0)[cp], fails);
+            cluster.sync();
+            if (tid == 0) s_fail_total = cluster.map_shared_rank(s_fail, 0)[cp];
+            __syncthreads();
+            const int f = s_fail_total;
+            if (c == 0 && tid == 0) s_fail[cp ^ 1] = 0;
+            if (f == 0) { converged = true; break; }
+        }
     }
     // outputs: lambda_j = ||x_j||^2, v_j = P^T x_j / ||x_j||
     for (int u = warp; u < 2 * P; u += blockDim.x / 32) {
