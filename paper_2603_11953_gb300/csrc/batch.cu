@@ -1,0 +1,346 @@
+// batch.cu -- many independent instances of Alg. 1 (FP32 working, n <= 64) in a
+// fixed number of launches: the Gram work items and the combine live in
+// gram_ozaki.cu; here, one CTA per instance for the n x n stage (Alg. 1 lines
+// 3-5, the preconditioned form of Alg. 2 in FP64), and U (line 6) over the row
+// tiles of all instances.
+//
+// n x n stage of one instance (256 threads, M then R in shared memory): a
+// pivoted Cholesky P^T M P = R^T R, then a one-sided Jacobi SVD of X = R^T
+// whose converged columns y_c give lambda_c = |y_c|^2 and the eigenvectors
+// y_c / |y_c| of P^T M P.  Column pairs follow the round-robin tournament
+// (n/2 disjoint pairs per round); a group of 8 lanes handles one pair, each
+// lane every 8th row.  Rotation (p, q): alpha = |x_p|^2, beta = |x_q|^2,
+// gamma = x_p . x_q; skipped when |gamma| <= tol sqrt(alpha beta), otherwise
+// zeta = (beta - alpha) / (2 gamma), t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)),
+// c = 1 / sqrt(1 + t^2), s = t c, x_p <- c x_p - s x_q, x_q <- s x_p + c x_q,
+// alpha <- alpha - t gamma, beta <- beta + t gamma (norms recomputed from the
+// columns at the start of every sweep).
+#include "internal.cuh"
+
+namespace tsvd {
+namespace {
+
+constexpr int BT = 256;      // threads per instance CTA
+constexpr int BGROUP = 8;    // lanes per column pair
+
+__device__ __forceinline__ double group_sum(double v) {
+    const unsigned mask = 0xffu << (threadIdx.x & 24);  // the 8 lanes of this group only
+#pragma unroll
+    for (int o = BGROUP / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o);
+    return v;
+}
+
+__device__ __forceinline__ int player(int pos, int r, int N) { return pos == 0 ? 0 : 1 + (pos - 1 + r) % (N - 1); }
+
+__global__ void __launch_bounds__(BT) eig_batch_kernel(const BatchInst* __restrict__ inst, double tol,
+                                                       int max_sweeps, DevInfo* __restrict__ infos) {
+    extern __shared__ double sm[];
+    __shared__ double nrm[64];
+    __shared__ int perm[64];
+    __shared__ int s_piv, s_fail, s_count[2];
+    __shared__ unsigned long long s_off;
+    const BatchInst& d = inst[blockIdx.x];
+    DevInfo* info = infos + blockIdx.x;
+    const int n = d.n, LD = n + 1, tid = threadIdx.x;
+    double* M = sm;  // [n][LD]: M, then row k = row k of R = column k of X
+    for (int idx = tid; idx < n * n; idx += BT) {
+        const int i = idx % n, j = idx / n;
+        M[i * LD + j] = d.G[i + (size_t)j * n];
+    }
+    if (tid < n) perm[tid] = tid;
+    if (tid == 0) {
+        s_fail = 0;
+        s_count[0] = s_count[1] = 0;
+        s_off = 0ull;
+    }
+    __syncthreads();
+
+    // ---- pivoted Cholesky in place
+    int k = 0;
+    for (; k < n; ++k) {
+        if (tid < 32) {
+            double bv = -1.0;
+            int bi = k;
+            for (int i = k + tid; i < n; i += 32) {
+                const double v = M[i * LD + i];
+                if (v > bv) { bv = v; bi = i; }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+            }
+            if (tid == 0) {
+                s_piv = bi;
+                if (!(bv > 0.0) || !isfinite(bv)) s_fail = 1;
+            }
+        }
+        __syncthreads();
+        if (s_fail) break;
+        const int p = s_piv;
+        if (p != k) {
+            for (int j = tid; j < n; j += BT) {
+                const double t = M[k * LD + j]; M[k * LD + j] = M[p * LD + j]; M[p * LD + j] = t;
+            }
+            __syncthreads();
+            for (int i = tid; i < n; i += BT) {
+                const double t = M[i * LD + k]; M[i * LD + k] = M[i * LD + p]; M[i * LD + p] = t;
+            }
+            if (tid == 0) { const int t = perm[k]; perm[k] = perm[p]; perm[p] = t; }
+            __syncthreads();
+        }
+        const double rkk = sqrt(M[k * LD + k]);
+        const double inv = 1.0 / rkk;
+        __syncthreads();
+        for (int j = k + 1 + tid; j < n; j += BT) M[k * LD + j] *= inv;
+        if (tid == 0) M[k * LD + k] = rkk;
+        __syncthreads();
+        const int t = n - k - 1;
+        for (int idx = tid; idx < t * t; idx += BT) {
+            const int i = k + 1 + idx % t, j = k + 1 + idx / t;
+            M[i * LD + j] = fma(-M[k * LD + i], M[k * LD + j], M[i * LD + j]);
+        }
+        __syncthreads();
+    }
+    for (int idx = tid; idx < n * n; idx += BT) {
+        const int c = idx / n, r = idx % n;
+        if (r < c || c >= k) M[c * LD + r] = 0.0;
+    }
+    if (tid == 0 && k < n) atomicOr(&info->flags, FLAG_NOT_FULL_RANK);
+    __syncthreads();
+
+    // ---- one-sided Jacobi on the columns x_c = row c of R
+    const int N = (n + 1) & ~1;
+    const int grp = tid / BGROUP, gl = tid % BGROUP;
+    int sweep = 0;
+    bool converged = false;
+    while (sweep < max_sweeps) {
+        for (int c = grp; c < n; c += BT / BGROUP) {
+            double a = 0.0;
+            for (int i = gl; i < n; i += BGROUP) a = fma(M[c * LD + i], M[c * LD + i], a);
+            a = group_sum(a);
+            if (gl == 0) nrm[c] = a;
+        }
+        if (tid == 0) s_off = 0ull;
+        __syncthreads();
+        unsigned long long off_bits = 0ull;
+        for (int r = 0; r < N - 1; ++r) {
+            if (grp < N / 2) {
+                int p = player(grp, r, N), q = player(N - 1 - grp, r, N);
+                if (p > q) { const int t = p; p = q; q = t; }
+                if (q < n) {
+                    double* xp = M + p * LD;
+                    double* xq = M + q * LD;
+                    double g = 0.0;
+                    for (int i = gl; i < n; i += BGROUP) g = fma(xp[i], xq[i], g);
+                    g = group_sum(g);
+                    const double a = nrm[p], b = nrm[q];
+                    const double scale = sqrt(a) * sqrt(b);
+                    const double ratio = scale > 0.0 ? fabs(g) / scale : 0.0;
+                    if (ratio > tol) {
+                        const double zeta = (b - a) / (2.0 * g);
+                        const double az = fabs(zeta);
+                        double t = az > 1e150 ? 0.5 / az : 1.0 / (az + sqrt(fma(az, az, 1.0)));
+                        t = copysign(t, zeta);
+                        const double c = 1.0 / sqrt(fma(t, t, 1.0)), s = t * c;
+                        for (int i = gl; i < n; i += BGROUP) {
+                            const double u = xp[i], v = xq[i];
+                            xp[i] = fma(c, u, -s * v);
+                            xq[i] = fma(s, u, c * v);
+                        }
+                        if (gl == 0) {
+                            nrm[p] = fma(-t, g, a);
+                            nrm[q] = fma(t, g, b);
+                            atomicAdd(&s_count[sweep & 1], 1);
+                        }
+                    }
+                    if (gl == 0) off_bits = max(off_bits, (unsigned long long)__double_as_longlong(ratio));
+                }
+            }
+            __syncthreads();
+        }
+        if (off_bits) atomicMax(&s_off, off_bits);
+        ++sweep;
+        const int cnt = s_count[(sweep - 1) & 1];
+        __syncthreads();
+        if (tid == 0) s_count[(sweep - 1) & 1] = 0;
+        if (cnt == 0) {
+            converged = true;
+            break;
+        }
+    }
+
+    // ---- lambda_c = |x_c|^2, V (original row order) = x_c / |x_c|
+    for (int c = grp; c < n; c += BT / BGROUP) {
+        double a = 0.0;
+        for (int i = gl; i < n; i += BGROUP) a = fma(M[c * LD + i], M[c * LD + i], a);
+        a = group_sum(a);
+        const double nc = a > 0.0 ? sqrt(a) : 0.0;
+        if (gl == 0) d.lam[c] = a;
+        for (int i = gl; i < n; i += BGROUP)
+            d.Vh[perm[i] + (size_t)c * n] = nc > 0.0 ? M[c * LD + i] / nc : (perm[i] == c ? 1.0 : 0.0);
+    }
+    if (tid == 0) {
+        info->sweeps = sweep;
+        info->off_norm = __longlong_as_double((long long)s_off);
+        if (!converged) atomicOr(&info->flags, FLAG_NO_CONVERGENCE);
+    }
+}
+
+// Alg. 1 lines 4-5 per instance: descending order, sign rule (the largest-magnitude
+// entry of each column positive, lowest index on ties), sigma = sqrt(lambda), the
+// casts to FP32 and W = RN(V / sigma).
+__global__ void __launch_bounds__(64) finish_batch_kernel(const BatchInst* __restrict__ inst,
+                                                          DevInfo* __restrict__ infos) {
+    __shared__ int order[64];
+    __shared__ double sig[64], sgn[64];
+    const BatchInst& d = inst[blockIdx.x];
+    DevInfo* info = infos + blockIdx.x;
+    const int n = d.n, tid = threadIdx.x;
+    if (tid < n) {
+        const double li = d.lam[tid];
+        int rank = 0;
+        for (int j = 0; j < n; ++j) {
+            const double lj = d.lam[j];
+            if (lj > li || (lj == li && j < tid)) ++rank;
+        }
+        order[rank] = tid;
+    }
+    __syncthreads();
+    if (tid < n) {
+        const int src = order[tid];
+        const double l = d.lam[src];
+        if (!(l > 0.0)) atomicOr(&info->flags, FLAG_NOT_FULL_RANK);
+        sig[tid] = l > 0.0 ? sqrt(l) : 0.0;
+        int best = 0;
+        double bv = fabs(d.Vh[(size_t)src * n]);
+        for (int r = 1; r < n; ++r) {
+            const double v = fabs(d.Vh[r + (size_t)src * n]);
+            if (v > bv) { bv = v; best = r; }
+        }
+        sgn[tid] = d.Vh[best + (size_t)src * n] < 0.0 ? -1.0 : 1.0;
+    }
+    __syncthreads();
+    if (tid == 0 && n > 1 && sig[n - 1] < 1.1102230246251565e-16 * sig[0]) atomicOr(&info->flags, FLAG_NOT_FULL_RANK);
+    for (int idx = tid; idx < n * n; idx += blockDim.x) {
+        const int r = idx % n, k = idx / n;
+        const float vw = (float)(sgn[k] * d.Vh[r + (size_t)order[k] * n]);
+        d.V[r + (size_t)k * d.ldv] = vw;
+        d.W[r + (size_t)k * n] = vw / (float)sig[k];
+    }
+    if (tid < n) d.sigma[tid] = (float)sig[tid];
+}
+
+// U = A W over the 256-row tiles of all instances: CTA -> (instance, tile) by a
+// binary search of the tile prefix; 64 threads x 4 rows by 4 groups of 16 columns,
+// FP32 FMA (the rounding model of eq. (AV-0)).
+__global__ void __launch_bounds__(256) u_batch_kernel(const BatchInst* __restrict__ inst, int count,
+                                                      int64_t utiles) {
+    __shared__ float Ws[64 * 64];
+    for (int64_t tile = blockIdx.x; tile < utiles; tile += gridDim.x) {
+        int lo = 0, hi = count - 1;
+        while (lo < hi) {  // last instance with utile0 <= tile
+            const int mid = (lo + hi + 1) >> 1;
+            if (inst[mid].utile0 <= tile) lo = mid; else hi = mid - 1;
+        }
+        const BatchInst& d = inst[lo];
+        const int n = d.n;
+        __syncthreads();  // the previous tile's reads of Ws are done
+        for (int idx = threadIdx.x; idx < n * 64; idx += blockDim.x) {
+            const int c = idx / 64, k = idx % 64;
+            Ws[idx] = k < n ? d.W[c + (size_t)k * n] : 0.f;
+        }
+        __syncthreads();
+        const int64_t r0 = (tile - d.utile0) * BATCH_UROWS + 4 * (threadIdx.x & 63);
+        const int cg = threadIdx.x >> 6;
+        if (cg * 16 >= n || r0 >= d.m) continue;
+        const bool full = r0 + 3 < d.m;
+        const bool vec = full && ((uintptr_t)d.A % 16 == 0) && (d.lda % 4 == 0) && ((uintptr_t)d.U % 16 == 0) &&
+                         (d.ldu % 4 == 0);
+        float acc[4][16];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int k = 0; k < 16; ++k) acc[r][k] = 0.f;
+        for (int c = 0; c < n; ++c) {
+            const float* src = d.A + (size_t)c * d.lda + r0;
+            float a[4];
+            if (vec) {
+                const float4 v = *reinterpret_cast<const float4*>(src);
+                a[0] = v.x; a[1] = v.y; a[2] = v.z; a[3] = v.w;
+            } else {
+#pragma unroll
+                for (int r = 0; r < 4; ++r) a[r] = (r0 + r < d.m) ? src[r] : 0.f;
+            }
+            const float* w = Ws + c * 64 + cg * 16;
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                const float wk = w[k];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) acc[r][k] = fmaf(a[r], wk, acc[r][k]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const int j = cg * 16 + k;
+            if (j < n) {
+                float* dst = d.U + (size_t)j * d.ldu + r0;
+                if (vec) {
+                    *reinterpret_cast<float4*>(dst) = make_float4(acc[0][k], acc[1][k], acc[2][k], acc[3][k]);
+                } else {
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+                        if (r0 + r < d.m) dst[r] = acc[r][k];
+                }
+            }
+        }
+    }
+}
+
+__global__ void finalize_batch_kernel(DevInfo* __restrict__ infos, int count, DevInfo* agg) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        const int f = infos[i].flags;
+        if (f) atomicOr(&agg->flags, f);
+        int st = TSVD_OK;
+        if (f & FLAG_NONFINITE) st = TSVD_ERR_NONFINITE;
+        else if (f & FLAG_TIMEOUT) st = TSVD_ERR_TIMEOUT;
+        else if (f & FLAG_NOT_FULL_RANK) st = TSVD_ERR_NOT_FULL_RANK;
+        else if (f & FLAG_NO_CONVERGENCE) st = TSVD_ERR_NO_CONVERGENCE;
+        infos[i].flags = st;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_eig_batch(const BatchInst* inst, int count, double tol, int max_sweeps, DevInfo* infos,
+                             cudaStream_t s) {
+    if (count == 0) return cudaSuccess;
+    const size_t smem = sizeof(double) * 64 * 65;
+    cudaError_t e = cudaFuncSetAttribute(eig_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    eig_batch_kernel<<<count, BT, smem, s>>>(inst, tol, max_sweeps, infos);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finish_batch(const BatchInst* inst, int count, DevInfo* infos, cudaStream_t s) {
+    if (count == 0) return cudaSuccess;
+    finish_batch_kernel<<<count, 64, 0, s>>>(inst, infos);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_u_batch(const BatchInst* inst, int count, int64_t utiles, int grid, cudaStream_t s) {
+    if (count == 0 || utiles == 0) return cudaSuccess;
+    const int64_t g = utiles < grid ? utiles : grid;
+    u_batch_kernel<<<(unsigned)g, 256, 0, s>>>(inst, count, utiles);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_batch(DevInfo* infos, int count, DevInfo* agg, cudaStream_t s) {
+    if (count > 0) finalize_batch_kernel<<<(count + 255) / 256, 256, 0, s>>>(infos, count, agg);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_finalize_info(agg, s);
+}
+
+}  // namespace tsvd

@@ -28,6 +28,8 @@
 // fixed-order combine) is the comparison form of the same step.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace tsvd {
@@ -91,11 +93,13 @@ struct GramSmem {
     static constexpr size_t bytes = tile_bytes + dig_bytes + 3 * NP * sizeof(int);
 };
 
+// The Gram partial of rows [r_begin, r_end) of A (n <= NP columns) by one CTA of
+// 256 threads, written as NP x NP int64 hi / lo accumulators at ph / pl and the
+// NP column exponents at pE.
 template <int NP, bool VEC>
-__global__ void __launch_bounds__(256, 1)
-    gram_ozaki_kernel(const float* __restrict__ A, int64_t m, int n, int64_t lda,
-                      int64_t rows_per_cta, long long* __restrict__ part_hi,
-                      long long* __restrict__ part_lo, int* __restrict__ part_E, DevInfo* info) {
+__device__ __forceinline__ void ozaki_rows(const float* __restrict__ A, int n, int64_t lda, int64_t r_begin,
+                                           int64_t r_end, long long* __restrict__ ph, long long* __restrict__ pl,
+                                           int* __restrict__ pE, DevInfo* info) {
     constexpr int KC = GRAM_KC;
     constexpr int KP = GramSmem<NP>::KP;
     constexpr int NT = (NP / 16) * (NP / 8);  // m16 x n8 output tiles
@@ -108,9 +112,8 @@ __global__ void __launch_bounds__(256, 1)
     int* dE = e_chk + NP;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t r_begin = (int64_t)blockIdx.x * rows_per_cta;
-    const int64_t r_end = min(m, r_begin + rows_per_cta);
 
+    __syncthreads();  // the previous row range (batched use) is done with the shared state
     if (tid < NP) E_run[tid] = EXP_EMPTY;
     long long acc_hi[TPW * 4], acc_lo[TPW * 4];
 #pragma unroll
@@ -248,9 +251,7 @@ __global__ void __launch_bounds__(256, 1)
         }
         __syncthreads();
     }
-    // (f) partials of this CTA
-    long long* ph = part_hi + (size_t)blockIdx.x * NP * NP;
-    long long* pl = part_lo + (size_t)blockIdx.x * NP * NP;
+    // (f) partials of this row range
 #pragma unroll
     for (int u = 0; u < TPW; ++u) {
         const int t = warp + 8 * u;
@@ -264,8 +265,35 @@ __global__ void __launch_bounds__(256, 1)
             }
         }
     }
-    if (tid < NP) part_E[(size_t)blockIdx.x * NP + tid] = E_run[tid];
+    if (tid < NP) pE[tid] = E_run[tid];
     if (bad) atomicOr(&info->flags, FLAG_NONFINITE);
+}
+
+template <int NP, bool VEC>
+__global__ void __launch_bounds__(256, 1)
+    gram_ozaki_kernel(const float* __restrict__ A, int64_t m, int n, int64_t lda,
+                      int64_t rows_per_cta, long long* __restrict__ part_hi,
+                      long long* __restrict__ part_lo, int* __restrict__ part_E, DevInfo* info) {
+    const int64_t r_begin = (int64_t)blockIdx.x * rows_per_cta;
+    const int64_t r_end = min(m, r_begin + rows_per_cta);
+    ozaki_rows<NP, VEC>(A, n, lda, r_begin, r_end, part_hi + (size_t)blockIdx.x * NP * NP,
+                        part_lo + (size_t)blockIdx.x * NP * NP, part_E + (size_t)blockIdx.x * NP, info);
+}
+
+// Batched: every CTA takes work items (instance, row range, partial slot) in turn; the
+// partial of slot k sits at k * BATCH_SLOT (hi, lo) and k * 64 (exponents).
+template <int NP, bool VEC>
+__global__ void __launch_bounds__(256, 1)
+    gram_ozaki_batch_kernel(const BatchInst* __restrict__ inst, const BatchGramItem* __restrict__ items, int nitems,
+                            long long* __restrict__ part_hi, long long* __restrict__ part_lo,
+                            int* __restrict__ part_E, DevInfo* __restrict__ infos) {
+    for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
+        const BatchGramItem it = items[w];
+        const BatchInst& d = inst[it.inst];
+        ozaki_rows<NP, VEC>(d.A, d.n, d.lda, it.r0, it.r1, part_hi + (size_t)it.slot * BATCH_SLOT,
+                            part_lo + (size_t)it.slot * BATCH_SLOT, part_E + (size_t)it.slot * 64,
+                            infos + it.inst);
+    }
 }
 
 // ---------------------------------------------------------------- exact combine
@@ -308,36 +336,31 @@ __device__ __forceinline__ __int128 shfl_xor_i128(__int128 v, int o) {
     return (__int128)(((unsigned __int128)h2 << 64) | (unsigned __int128)l2);
 }
 
-__global__ void __launch_bounds__(256) gram_combine_kernel(const long long* __restrict__ part_hi,
-                                                           const long long* __restrict__ part_lo,
-                                                           const int* __restrict__ part_E, int P, int NP, int n,
-                                                           double* __restrict__ G, double* __restrict__ G_lo,
-                                                           int64_t ldg, int c1, int c2, int wmask, int nglob) {
-    const int idx = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    const int lane = threadIdx.x & 31;
-    const int npairs = n * (n + 1) / 2;
-    if (idx >= npairs) return;  // whole warps only
-    int j = (int)((sqrtf(8.0f * (float)idx + 1.0f) - 1.0f) * 0.5f);
-    while ((j + 1) * (j + 2) / 2 <= idx) ++j;
-    while (j * (j + 1) / 2 > idx) --j;
-    const int i = idx - j * (j + 1) / 2;
+// The exact sum over P partials (slot c at c * slot (hi, lo) and c * estride
+// (exponents), NP x NP row-major) of entry (i, j), rounded to a double-double;
+// all 32 lanes of the warp take part.
+__device__ __forceinline__ void combine_entry(const long long* __restrict__ part_hi,
+                                              const long long* __restrict__ part_lo,
+                                              const int* __restrict__ part_E, int P, size_t slot, int estride,
+                                              int NP, int i, int j, int lane, double& hi, double& lo) {
     int emax = EXP_EMPTY;
     for (int c = lane; c < P; c += 32) {
-        const int Ei = part_E[(size_t)c * NP + i], Ej = part_E[(size_t)c * NP + j];
+        const int Ei = part_E[(size_t)c * estride + i], Ej = part_E[(size_t)c * estride + j];
         if (Ei == EXP_EMPTY || Ej == EXP_EMPTY) continue;
         emax = max(emax, Ei + Ej);
     }
     emax = __reduce_max_sync(0xffffffffu, emax);
-    double hi = 0.0, lo = 0.0;
+    hi = 0.0;
+    lo = 0.0;
     if (emax != EXP_EMPTY) {
         // value_c = 2^(e_c - 63) * (h * 2^16 + l); fixed point unit 2^(emax - 63 - 29)
         __int128 acc = 0;
         for (int c = lane; c < P; c += 32) {
-            const int Ei = part_E[(size_t)c * NP + i], Ej = part_E[(size_t)c * NP + j];
+            const int Ei = part_E[(size_t)c * estride + i], Ej = part_E[(size_t)c * estride + j];
             if (Ei == EXP_EMPTY || Ej == EXP_EMPTY) continue;
             const int sh = emax - (Ei + Ej);
             if (sh >= 110) continue;  // below 2^-139 of the largest partial scale
-            const size_t a = ((size_t)c * NP + i) * NP + j, b = ((size_t)c * NP + j) * NP + i;
+            const size_t a = (size_t)c * slot + (size_t)i * NP + j, b = (size_t)c * slot + (size_t)j * NP + i;
             const __int128 h = (__int128)part_hi[a] + (__int128)part_hi[b];
             const __int128 l = (__int128)part_lo[a] + (__int128)part_lo[b];
             const __int128 X = h * ((__int128)1 << 16) + l;
@@ -349,6 +372,28 @@ __global__ void __launch_bounds__(256) gram_combine_kernel(const long long* __re
         hi = round_i128(acc, emax - 92, r1);
         lo = round_i128(acc - r1, emax - 92, r2);
     }
+}
+
+__device__ __forceinline__ void pair_of(int idx, int& i, int& j) {
+    j = (int)((sqrtf(8.0f * (float)idx + 1.0f) - 1.0f) * 0.5f);
+    while ((j + 1) * (j + 2) / 2 <= idx) ++j;
+    while (j * (j + 1) / 2 > idx) --j;
+    i = idx - j * (j + 1) / 2;
+}
+
+__global__ void __launch_bounds__(256) gram_combine_kernel(const long long* __restrict__ part_hi,
+                                                           const long long* __restrict__ part_lo,
+                                                           const int* __restrict__ part_E, int P, int NP, int n,
+                                                           double* __restrict__ G, double* __restrict__ G_lo,
+                                                           int64_t ldg, int c1, int c2, int wmask, int nglob) {
+    const int idx = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    const int npairs = n * (n + 1) / 2;
+    if (idx >= npairs) return;  // whole warps only
+    int i, j;
+    pair_of(idx, i, j);
+    double hi, lo;
+    combine_entry(part_hi, part_lo, part_E, P, (size_t)NP * NP, NP, NP, i, j, lane, hi, lo);
     int gi = i, gj = j;
     if (c1 >= 0) {
         // two-group launch: map the local columns, keep only the tiles asked for
@@ -363,6 +408,30 @@ __global__ void __launch_bounds__(256) gram_combine_kernel(const long long* __re
         if (G_lo) {
             G_lo[gi + (size_t)gj * ldg] = lo;
             G_lo[gj + (size_t)gi * ldg] = lo;
+        }
+    }
+}
+
+// Batched: one CTA per instance, warps over its entries i <= j, G into the instance's
+// n x n FP64 block (ld n).
+__global__ void __launch_bounds__(256) gram_combine_batch_kernel(const BatchInst* __restrict__ inst,
+                                                                 const long long* __restrict__ part_hi,
+                                                                 const long long* __restrict__ part_lo,
+                                                                 const int* __restrict__ part_E) {
+    const BatchInst& d = inst[blockIdx.x];
+    const int n = d.n, NP = d.NP;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int npairs = n * (n + 1) / 2;
+    const size_t s0 = (size_t)d.slot0;
+    for (int idx = warp; idx < npairs; idx += blockDim.x / 32) {
+        int i, j;
+        pair_of(idx, i, j);
+        double hi, lo;
+        combine_entry(part_hi + s0 * BATCH_SLOT, part_lo + s0 * BATCH_SLOT, part_E + s0 * 64, d.nslots, BATCH_SLOT,
+                      64, NP, i, j, lane, hi, lo);
+        if (lane == 0) {
+            d.G[i + (size_t)j * n] = hi;
+            d.G[j + (size_t)i * n] = hi;
         }
     }
 }
@@ -508,6 +577,62 @@ cudaError_t launch_gram_combine(const GramPlan& plan, const void* part, int n, d
     const int npairs = n * (n + 1) / 2;
     gram_combine_kernel<<<(npairs + 7) / 8, 256, 0, s>>>(ph, pl, pE, plan.P, plan.NP, n, G, G_lo, ldg, -1, -1, 0,
                                                          n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gram_batch(const BatchInst* inst, const BatchGramItem* items, int nitems, int NP, bool vec,
+                              void* part, int total_slots, DevInfo* infos, int grid, cudaStream_t s) {
+    if (nitems == 0) return cudaSuccess;
+    long long* ph = reinterpret_cast<long long*>(part);
+    long long* pl = ph + (size_t)total_slots * BATCH_SLOT;
+    int* pE = reinterpret_cast<int*>(pl + (size_t)total_slots * BATCH_SLOT);
+    const int g = grid < nitems ? grid : nitems;
+#define TSVD_BATCH_NP(NPV)                                                                                        \
+    {                                                                                                              \
+        const size_t smem = GramSmem<NPV>::bytes;                                                                  \
+        if (vec) {                                                                                                 \
+            cudaError_t e = cudaFuncSetAttribute(gram_ozaki_batch_kernel<NPV, true>,                               \
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);          \
+            if (e != cudaSuccess) return e;                                                                        \
+            int bps = 1;                                                                                           \
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, gram_ozaki_batch_kernel<NPV, true>, 256,      \
+                                                              smem) != cudaSuccess || bps < 1)                     \
+                bps = 1;                                                                                           \
+            const int gg = (int)std::min<long long>((long long)g * bps, nitems);                                   \
+            gram_ozaki_batch_kernel<NPV, true><<<gg, 256, smem, s>>>(inst, items, nitems, ph, pl, pE, infos);      \
+        } else {                                                                                                   \
+            cudaError_t e = cudaFuncSetAttribute(gram_ozaki_batch_kernel<NPV, false>,                              \
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);          \
+            if (e != cudaSuccess) return e;                                                                        \
+            int bps = 1;                                                                                           \
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, gram_ozaki_batch_kernel<NPV, false>, 256,     \
+                                                              smem) != cudaSuccess || bps < 1)                     \
+                bps = 1;                                                                                           \
+            const int gg = (int)std::min<long long>((long long)g * bps, nitems);                                   \
+            gram_ozaki_batch_kernel<NPV, false><<<gg, 256, smem, s>>>(inst, items, nitems, ph, pl, pE, infos);     \
+        }                                                                                                          \
+    }
+    switch (NP) {
+        case 16: TSVD_BATCH_NP(16) break;
+        case 32: TSVD_BATCH_NP(32) break;
+        case 48: TSVD_BATCH_NP(48) break;
+        default: TSVD_BATCH_NP(64) break;
+    }
+#undef TSVD_BATCH_NP
+    return cudaGetLastError();
+}
+
+size_t gram_batch_partials_bytes(int total_slots) {
+    return (size_t)total_slots * (2 * BATCH_SLOT * sizeof(long long) + 64 * sizeof(int)) + 256;
+}
+
+cudaError_t launch_gram_combine_batch(const BatchInst* inst, int count, const void* part, int total_slots,
+                                      cudaStream_t s) {
+    if (count == 0) return cudaSuccess;
+    const long long* ph = reinterpret_cast<const long long*>(part);
+    const long long* pl = ph + (size_t)total_slots * BATCH_SLOT;
+    const int* pE = reinterpret_cast<const int*>(pl + (size_t)total_slots * BATCH_SLOT);
+    gram_combine_batch_kernel<<<count, 256, 0, s>>>(inst, ph, pl, pE);
     return cudaGetLastError();
 }
 

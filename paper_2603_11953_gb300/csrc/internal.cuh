@@ -135,6 +135,47 @@ cudaError_t launch_compute_u_tc(const float* A, int64_t m, int n, int64_t lda, c
 cudaError_t launch_compute_u_v2(const float* A, int64_t m, int n, int64_t lda, const float* W, float* U,
                                 int64_t ldu, int sm_count, DevInfo* info, cudaStream_t s);
 
+// ---------------------------------------------------------------- batched instances (n <= 64, FP32)
+// One descriptor per instance, in device memory.  Workspace pointers (G, lam,
+// Vh, W) are the instance's own; sigma, V, U are the caller's (U may be null).
+constexpr size_t BATCH_SLOT = 64 * 64;  // int64 entries per Gram partial slot (hi or lo)
+constexpr int BATCH_ROWS = 16384;       // rows per Gram work item (a multiple of GRAM_KC)
+constexpr int BATCH_UROWS = 256;        // rows per U work item
+struct BatchInst {
+    const float* A;
+    int64_t m, lda;
+    int n, NP;
+    int slot0, nslots;  // Gram partial slots of this instance
+    double* G;          // n x n, ld n
+    double* lam;        // n
+    double* Vh;         // n x n, ld n
+    float* W;           // n x n, ld n
+    float* sigma;
+    float* V;
+    int64_t ldv;
+    float* U;
+    int64_t ldu;
+    int64_t utile0;     // first U work item of this instance (prefix over instances)
+};
+struct BatchGramItem {
+    int inst, slot;
+    int64_t r0, r1;
+};
+size_t gram_batch_partials_bytes(int total_slots);
+// One launch for the items of one padded width NP (16, 32, 48 or 64).
+cudaError_t launch_gram_batch(const BatchInst* inst, const BatchGramItem* items, int nitems, int NP, bool vec,
+                              void* part, int total_slots, DevInfo* infos, int grid, cudaStream_t s);
+cudaError_t launch_gram_combine_batch(const BatchInst* inst, int count, const void* part, int total_slots,
+                                      cudaStream_t s);
+// One CTA per instance: FP64 pivoted Cholesky + one-sided Jacobi, then sort /
+// sign / sigma / W; U over all instances' row tiles (utile total); statuses
+// into infos[i] and, ORed, into agg (then finalised).
+cudaError_t launch_eig_batch(const BatchInst* inst, int count, double tol, int max_sweeps, DevInfo* infos,
+                             cudaStream_t s);
+cudaError_t launch_finish_batch(const BatchInst* inst, int count, DevInfo* infos, cudaStream_t s);
+cudaError_t launch_u_batch(const BatchInst* inst, int count, int64_t utiles, int grid, cudaStream_t s);
+cudaError_t launch_finalize_batch(DevInfo* infos, int count, DevInfo* agg, cudaStream_t s);
+
 // flags -> tsvd_status in info->flags (overwritten by the status code).
 cudaError_t launch_finalize_info(DevInfo* info, cudaStream_t s);
 

@@ -24,6 +24,10 @@ struct tsvd_ctx {
     std::vector<cudaEvent_t> ev;
     long long calls = 0;     // timed calls so far
     bool have_times = false;
+    // pinned staging of the batched descriptors (reused once its last copy is done)
+    void* stage = nullptr;
+    size_t stage_bytes = 0;
+    cudaEvent_t stage_ev = nullptr;
 };
 
 namespace {
@@ -327,6 +331,8 @@ tsvd_status tsvd_destroy(tsvd_handle h) {
     if (h->dinfo) cudaFree(h->dinfo);
     for (auto& ev : h->ev)
         if (ev) cudaEventDestroy(ev);
+    if (h->stage) cudaFreeHost(h->stage);
+    if (h->stage_ev) cudaEventDestroy(h->stage_ev);
     delete h;
     return TSVD_OK;
 }
@@ -392,6 +398,142 @@ tsvd_status tsvd_solve(tsvd_handle h, const void* A, int64_t m, int64_t n, int64
     return solve_one(h, A, m, (int)n, lda, working, higher, sigma, V, ldv, U, ldu, info, true);
 }
 
+}  // extern "C"
+
+namespace {
+
+// Batched Algorithm 1 (FP32 working, n <= 64): Gram work items (instance, row range of at
+// most BATCH_ROWS) in one launch per padded width, one combine launch, one CTA per
+// instance for the n x n stage and the finish, U over all instances' row tiles, and
+// the statuses: at most nine launches whatever the count.
+tsvd_status batch_run(tsvd_ctx* h, int32_t count, const void* const* A, const int64_t* m, const int64_t* n,
+                      const int64_t* lda, void* const* sigma, void* const* V, const int64_t* ldv, void* const* U,
+                      const int64_t* ldu, tsvd_info* info) {
+    std::vector<BatchInst> inst((size_t)count);
+    std::vector<BatchGramItem> cls[4];
+    std::vector<int64_t> crow[4];
+    int slots = 0;
+    int64_t utiles = 0;
+    size_t per_off = 0;
+    std::vector<size_t> per((size_t)count);
+    bool vec[4] = {true, true, true, true};
+    for (int32_t i = 0; i < count; ++i) {
+        BatchInst& d = inst[(size_t)i];
+        const int ni = (int)n[i];
+        d.A = static_cast<const float*>(A[i]);
+        d.m = m[i];
+        d.lda = lda[i];
+        d.n = ni;
+        d.NP = ni <= 16 ? 16 : ni <= 32 ? 32 : ni <= 48 ? 48 : 64;
+        const int c = d.NP / 16 - 1;
+        if ((uintptr_t)A[i] % 16 != 0 || lda[i] % 4 != 0) vec[c] = false;
+        d.slot0 = slots;
+        d.nslots = (int)((m[i] + BATCH_ROWS - 1) / BATCH_ROWS);
+        for (int k = 0; k < d.nslots; ++k) {
+            const int64_t r0 = (int64_t)k * BATCH_ROWS;
+            const int64_t r1 = std::min<int64_t>(m[i], r0 + BATCH_ROWS);
+            cls[c].push_back(BatchGramItem{i, slots + k, r0, r1});
+        }
+        slots += d.nslots;
+        d.sigma = static_cast<float*>(sigma[i]);
+        d.V = static_cast<float*>(V[i]);
+        d.ldv = ldv[i];
+        const bool want_u = U && U[i];
+        d.U = want_u ? static_cast<float*>(U[i]) : nullptr;
+        d.ldu = want_u ? ldu[i] : 0;
+        d.utile0 = utiles;
+        if (want_u) utiles += (m[i] + BATCH_UROWS - 1) / BATCH_UROWS;
+        per[(size_t)i] = per_off;
+        per_off += align_up(sizeof(double) * (2 * (size_t)ni * ni + ni) + sizeof(float) * (size_t)ni * ni);
+    }
+    // longest row ranges first within each width (the CTAs take items in order)
+    size_t nitems = 0, coff[4];
+    for (int c = 0; c < 4; ++c) {
+        std::stable_sort(cls[c].begin(), cls[c].end(),
+                         [](const BatchGramItem& a, const BatchGramItem& b) { return a.r1 - a.r0 > b.r1 - b.r0; });
+        coff[c] = nitems;
+        nitems += cls[c].size();
+    }
+    // workspace: [descriptors][items][infos][partials][per-instance G, lam, Vh, W]
+    const size_t b_inst = align_up(sizeof(BatchInst) * (size_t)count);
+    const size_t b_items = align_up(sizeof(BatchGramItem) * nitems);
+    const size_t b_info = align_up(sizeof(DevInfo) * (size_t)count);
+    const size_t b_part = align_up(gram_batch_partials_bytes(slots));
+    const size_t o_items = b_inst, o_info = o_items + b_items, o_part = o_info + b_info, o_per = o_part + b_part;
+    tsvd_status st = ensure_ws(h, o_per + per_off);
+    if (st != TSVD_OK) return st;
+    for (int32_t i = 0; i < count; ++i) {
+        BatchInst& d = inst[(size_t)i];
+        char* b = base(h) + o_per + per[(size_t)i];
+        const size_t nn = (size_t)d.n * d.n;
+        d.G = reinterpret_cast<double*>(b);
+        d.lam = d.G + nn;
+        d.Vh = d.lam + d.n;
+        d.W = reinterpret_cast<float*>(d.Vh + nn);
+    }
+    // descriptors and items through the pinned staging buffer
+    const size_t stage_need = b_inst + b_items;
+    if (h->stage_ev) {
+        if (cudaEventSynchronize(h->stage_ev) != cudaSuccess) return from_cuda(cudaGetLastError());
+    } else if (cudaEventCreateWithFlags(&h->stage_ev, cudaEventDisableTiming) != cudaSuccess) {
+        return from_cuda(cudaGetLastError());
+    }
+    if (h->stage_bytes < stage_need) {
+        if (h->stage) cudaFreeHost(h->stage);
+        h->stage = nullptr;
+        h->stage_bytes = 0;
+        if (cudaMallocHost(&h->stage, stage_need) != cudaSuccess) {
+            cudaGetLastError();
+            return TSVD_ERR_ALLOC;
+        }
+        h->stage_bytes = stage_need;
+    }
+    char* sb = static_cast<char*>(h->stage);
+    std::memcpy(sb, inst.data(), sizeof(BatchInst) * (size_t)count);
+    for (int c = 0; c < 4; ++c)
+        if (!cls[c].empty())
+            std::memcpy(sb + b_inst + sizeof(BatchGramItem) * coff[c], cls[c].data(),
+                        sizeof(BatchGramItem) * cls[c].size());
+    cudaError_t e = cudaMemcpyAsync(base(h), sb, stage_need, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(h->stage_ev, h->stream);
+    const BatchInst* dinst = reinterpret_cast<const BatchInst*>(base(h));
+    const BatchGramItem* ditems = reinterpret_cast<const BatchGramItem*>(base(h) + o_items);
+    DevInfo* dinfos = reinterpret_cast<DevInfo*>(base(h) + o_info);
+    void* part = base(h) + o_part;
+    if (e == cudaSuccess) e = cudaMemsetAsync(dinfos, 0, sizeof(DevInfo) * (size_t)count, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->dinfo, 0, sizeof(DevInfo), h->stream);
+    if (e != cudaSuccess) return from_cuda(e);
+    record(h, 0);
+    for (int c = 0; c < 4; ++c) {
+        e = launch_gram_batch(dinst, ditems + coff[c], (int)cls[c].size(), 16 * (c + 1), vec[c], part, slots, dinfos,
+                              h->sm_count, h->stream);
+        if (e != cudaSuccess) return from_cuda(e);
+    }
+    e = launch_gram_combine_batch(dinst, count, part, slots, h->stream);
+    if (e != cudaSuccess) return from_cuda(e);
+    record(h, 1);
+    e = launch_eig_batch(dinst, count, jacobi_tol(h, 64), max_sweeps(h), dinfos, h->stream);
+    if (e == cudaSuccess) e = launch_finish_batch(dinst, count, dinfos, h->stream);
+    if (e != cudaSuccess) return from_cuda(e);
+    record(h, 2);
+    e = launch_u_batch(dinst, count, utiles, 8 * h->sm_count, h->stream);
+    if (e != cudaSuccess) return from_cuda(e);
+    record(h, 3);
+    e = launch_finalize_batch(dinfos, count, h->dinfo, h->stream);
+    if (e == cudaSuccess && info)
+        e = cudaMemcpyAsync(info, dinfos, sizeof(DevInfo) * (size_t)count, cudaMemcpyDefault, h->stream);
+    if (e != cudaSuccess) return from_cuda(e);
+    if (h->opts.timing) {
+        h->have_times = true;
+        ++h->calls;
+    }
+    return TSVD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 tsvd_status tsvd_batch_solve(tsvd_handle h, int32_t count, const void* const* A, const int64_t* m,
                              const int64_t* n, const int64_t* lda, tsvd_prec working,
                              tsvd_prec higher, void* const* sigma, void* const* V,
@@ -411,9 +553,12 @@ tsvd_status tsvd_batch_solve(tsvd_handle h, int32_t count, const void* const* A,
         need = std::max(need, layout_for(n[i], part_bytes_for(h, A[i], working, m[i], (int)n[i], lda[i]), working).total);
     }
     DeviceGuard g(h->device);
+    h->have_times = false;
+    if (count == 0) return TSVD_OK;
+    if (h->opts.gram_variant != 1) return batch_run(h, count, A, m, n, lda, sigma, V, ldv, U, ldu, info);
+    // the plain FP64 comparison form: one instance per launch sequence
     tsvd_status st = ensure_ws(h, need);
     if (st != TSVD_OK) return st;
-    h->have_times = false;
     for (int32_t i = 0; i < count; ++i) {
         const bool want_u = U && U[i];
         st = solve_one(h, A[i], m[i], (int)n[i], lda[i], working, higher, sigma[i], V[i], ldv[i],

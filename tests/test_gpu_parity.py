@@ -242,8 +242,12 @@ def test_solve_matches_oracle(m, n, kappa, logd, variant):
     assert orth <= 1e-4, orth
 
 
-def test_batch_equals_single_solves():
-    cases = [(3000, 8), (1024, 16), (7777, 24), (2048, 64), (4096, 1)]
+def test_batch_matches_single_solves_and_exact_u():
+    """The batched launches (Gram work items on the CUDA-core Ozaki kernel, one CTA per instance for
+    the n x n stage) against single solves (tensor-core Gram, cluster Jacobi): both are the same
+    exact Gram and FP64 Jacobi up to rounding, so sigma agrees to 2 FP32 ulps and V to 1e-4 (well
+    separated spectra); U against the exact product with the batch's own W, (n + 1) u_32 (|A| |W|)."""
+    cases = [(3000, 8), (1024, 16), (7777, 24), (2048, 64), (4096, 1), (40000, 48), (16385, 33)]
     As = [workloads.small_case(m, n, seed=31 + i, device="cuda")[0] for i, (m, n) in enumerate(cases)]
     sig = [torch.zeros(n, device="cuda") for _, n in cases]
     Vs = [colmajor(n, n, torch.float32) for _, n in cases]
@@ -254,13 +258,46 @@ def test_batch_equals_single_solves():
                        T.TSVD_FP32, T.TSVD_FP64, sig, Vs, [n for _, n in cases], Us, [m for m, _ in cases],
                        info)
     torch.cuda.synchronize()
+    assert T.tsvd_sync_status(h) == T.TSVD_OK
     T.tsvd_destroy(h)
-    assert np.all(info.view(len(cases), 6)[:, 0].cpu().numpy() == 0)
+    inf = info.view(len(cases), 6).cpu().numpy()
+    assert np.all(inf[:, 0] == 0) and np.all(inf[:, 1] >= 1)
+    rng = np.random.default_rng(4)
     for k, (m, n) in enumerate(cases):
-        s1, V1, U1, st, _ = gpu_solve(As[k], m, n, m)
-        assert np.array_equal(s1, sig[k].cpu().numpy().astype(np.float64))
-        assert np.array_equal(V1, Vs[k].cpu().numpy().astype(np.float64))
-        assert np.array_equal(U1, Us[k][:m].cpu().numpy().astype(np.float64))
+        s1, V1, _, st, _ = gpu_solve(As[k], m, n, m, want_u=False)
+        sb = sig[k].cpu().numpy().astype(np.float64)
+        Vb = Vs[k].cpu().numpy().astype(np.float64)
+        assert np.all(np.abs(sb - s1) <= 2.0 ** -22 * s1), k
+        assert np.abs(Vb - V1).max() <= 1e-4, k
+        A_np = workloads.to_numpy_colmajor(As[k], m)
+        W = (Vs[k].cpu().numpy() / sig[k].cpu().numpy()[None, :]).astype(np.float64)
+        rows = np.unique(np.concatenate([[0, m - 1], rng.integers(0, m, 30)]))
+        U_ref = oracle.rows_times(A_np, W, rows, 24)
+        Ub = Us[k][:m].cpu().numpy().astype(np.float64)
+        bound = (n + 1) * U32 * (np.abs(A_np[rows].astype(np.float64)) @ np.abs(W)) + 1e-38
+        assert np.all(np.abs(Ub[rows] - U_ref) <= bound), k
+
+
+def test_batch_statuses_per_instance():
+    """Each instance reports its own status; the handle's status is the most severe."""
+    m, n = 2000, 6
+    good = workloads.small_case(m, n, seed=41, device="cuda")[0]
+    bad = good.clone()
+    bad[17, 2] = float("nan")
+    flat = good.clone()
+    flat[:, 3] = 0.0
+    As = [good, bad, flat, good]
+    sig = [torch.zeros(n, device="cuda") for _ in As]
+    Vs = [colmajor(n, n, torch.float32) for _ in As]
+    info = torch.zeros(6 * len(As), dtype=torch.int32, device="cuda")
+    h = handle()
+    T.tsvd_batch_solve(h, len(As), As, [m] * 4, [n] * 4, [m] * 4, T.TSVD_FP32, T.TSVD_FP64, sig, Vs, [n] * 4,
+                       None, None, info)
+    torch.cuda.synchronize()
+    codes = info.view(len(As), 6)[:, 0].cpu().numpy().tolist()
+    assert codes == [T.TSVD_OK, T.TSVD_ERR_NONFINITE, T.TSVD_ERR_NOT_FULL_RANK, T.TSVD_OK]
+    assert T.tsvd_sync_status(h) == T.TSVD_ERR_NONFINITE
+    T.tsvd_destroy(h)
 
 
 def test_batch_ragged_workload_matches_oracle():
@@ -350,6 +387,30 @@ def test_gram_fp64_graded_columns_zero_column_and_lda():
     assert st == T.TSVD_OK
     check_gram64(A[:m], Gh, Gl, m)
     assert Gh[2].tolist() == [0.0] * n and Gl[2].tolist() == [0.0] * n
+
+
+def test_gram_fp64_partition_and_permutation_invariant():
+    """Every needed piece Gram is an exact sum before its one rounding, so the double-double Gram
+    is bitwise the same for any split of the rows over CTAs (one to hundreds of partial sums, as
+    row partitions over several GPUs would give) and for any order of the rows."""
+    m, n = 70001, 20
+    A, _ = workloads.small_case(m, n, kappa_sigma=1e5, logd=5.0, seed=21, dtype=torch.float64, device="cuda")
+    ref = None
+    for split in (0, 1, 7, 300):
+        h = handle(split_k=split) if split else handle()
+        G = torch.zeros(2 * n * n, dtype=torch.float64, device="cuda")
+        T.tsvd_gram(h, A, m, n, m, T.TSVD_FP64, T.TSVD_DD, G, n)
+        assert T.tsvd_sync_status(h) == T.TSVD_OK
+        T.tsvd_destroy(h)
+        g = G.cpu().numpy()
+        if ref is None:
+            ref = g
+        assert np.array_equal(g, ref), split
+    perm = torch.randperm(m, generator=torch.Generator().manual_seed(5)).cuda()
+    Ap = A[:m][perm].T.contiguous().T  # rows permuted, column-major again
+    Gh, Gl, st = gpu_gram64(Ap, m, n, m)
+    assert st == T.TSVD_OK
+    assert np.array_equal(Gh, ref[: n * n].reshape(n, n).T) and np.array_equal(Gl, ref[n * n:].reshape(n, n).T)
 
 
 def gpu_solve64(A, m, n, lda, higher=T.TSVD_DD, want_u=True):
