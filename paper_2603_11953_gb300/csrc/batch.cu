@@ -232,11 +232,13 @@ __global__ void __launch_bounds__(64) finish_batch_kernel(const BatchInst* __res
     if (tid < n) d.sigma[tid] = (float)sig[tid];
 }
 
-// U = A W over the 256-row tiles of all instances: CTA -> (instance, tile) by a
-// binary search of the tile prefix; 64 threads x 4 rows by 4 groups of 16 columns,
-// FP32 FMA (the rounding model of eq. (AV-0)).
-__global__ void __launch_bounds__(256) u_batch_kernel(const BatchInst* __restrict__ inst, int count,
-                                                      int64_t utiles) {
+// U = A W over the row tiles of all instances: CTA -> (instance, tile) by a binary
+// search of the tile prefix.  A thread owns 4 rows by 16 columns; the 256 threads
+// cover batch_u_rows(n) rows (more rows when fewer 16-column groups are needed),
+// load four columns of A ahead of their FMAs, and accumulate in FP32 (the rounding
+// model of eq. (AV-0)).
+__global__ void __launch_bounds__(256, 2) u_batch_kernel(const BatchInst* __restrict__ inst, int count,
+                                                         int64_t utiles) {
     __shared__ float Ws[64 * 64];
     for (int64_t tile = blockIdx.x; tile < utiles; tile += gridDim.x) {
         int lo = 0, hi = count - 1;
@@ -252,8 +254,9 @@ __global__ void __launch_bounds__(256) u_batch_kernel(const BatchInst* __restric
             Ws[idx] = k < n ? d.W[c + (size_t)k * n] : 0.f;
         }
         __syncthreads();
-        const int64_t r0 = (tile - d.utile0) * BATCH_UROWS + 4 * (threadIdx.x & 63);
-        const int cg = threadIdx.x >> 6;
+        const int R = batch_u_rows(n) / 256;  // 4, 2 or 1 row groups of 256
+        const int rg = threadIdx.x % (64 * R), cg = threadIdx.x / (64 * R);
+        const int64_t r0 = (tile - d.utile0) * batch_u_rows(n) + 4 * rg;
         if (cg * 16 >= n || r0 >= d.m) continue;
         const bool full = r0 + 3 < d.m;
         const bool vec = full && ((uintptr_t)d.A % 16 == 0) && (d.lda % 4 == 0) && ((uintptr_t)d.U % 16 == 0) &&
@@ -263,22 +266,31 @@ __global__ void __launch_bounds__(256) u_batch_kernel(const BatchInst* __restric
         for (int r = 0; r < 4; ++r)
 #pragma unroll
             for (int k = 0; k < 16; ++k) acc[r][k] = 0.f;
-        for (int c = 0; c < n; ++c) {
-            const float* src = d.A + (size_t)c * d.lda + r0;
-            float a[4];
-            if (vec) {
-                const float4 v = *reinterpret_cast<const float4*>(src);
-                a[0] = v.x; a[1] = v.y; a[2] = v.z; a[3] = v.w;
-            } else {
+        for (int c0 = 0; c0 < n; c0 += 4) {
+            float a[4][4];
 #pragma unroll
-                for (int r = 0; r < 4; ++r) a[r] = (r0 + r < d.m) ? src[r] : 0.f;
+            for (int cc = 0; cc < 4; ++cc) {
+                const int c = c0 + cc;
+                const float* src = d.A + (size_t)c * d.lda + r0;
+                if (c < n && vec) {
+                    const float4 v = __ldcs(reinterpret_cast<const float4*>(src));
+                    a[cc][0] = v.x; a[cc][1] = v.y; a[cc][2] = v.z; a[cc][3] = v.w;
+                } else {
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) a[cc][r] = (c < n && r0 + r < d.m) ? src[r] : 0.f;
+                }
             }
-            const float* w = Ws + c * 64 + cg * 16;
 #pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                const float wk = w[k];
+            for (int cc = 0; cc < 4; ++cc) {
+                if (c0 + cc < n) {
+                    const float* w = Ws + (c0 + cc) * 64 + cg * 16;
 #pragma unroll
-                for (int r = 0; r < 4; ++r) acc[r][k] = fmaf(a[r], wk, acc[r][k]);
+                    for (int k = 0; k < 16; ++k) {
+                        const float wk = w[k];
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) acc[r][k] = fmaf(a[cc][r], wk, acc[r][k]);
+                    }
+                }
             }
         }
 #pragma unroll
@@ -287,7 +299,7 @@ __global__ void __launch_bounds__(256) u_batch_kernel(const BatchInst* __restric
             if (j < n) {
                 float* dst = d.U + (size_t)j * d.ldu + r0;
                 if (vec) {
-                    *reinterpret_cast<float4*>(dst) = make_float4(acc[0][k], acc[1][k], acc[2][k], acc[3][k]);
+                    __stcs(reinterpret_cast<float4*>(dst), make_float4(acc[0][k], acc[1][k], acc[2][k], acc[3][k]));
                 } else {
 #pragma unroll
                     for (int r = 0; r < 4; ++r)

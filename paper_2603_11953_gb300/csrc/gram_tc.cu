@@ -45,6 +45,8 @@
 // issuing work, drains what it started and frees its TMEM.
 #include <cuda_bf16.h>
 
+#include <cstring>
+
 #include "internal.cuh"
 #include "tma_util.cuh"
 
@@ -309,11 +311,22 @@ __device__ __forceinline__ void tc_drain(const TcRecord& R, uint32_t tmem, int q
     else tc_fold_all<1>(trow, hi, lo);            // lanes 64..127: second digit
 }
 
+// partial slot and status block of this CTA (batched use: those of its item)
+template <bool BATCH>
+__device__ __forceinline__ int64_t tc_slot(const TcBatchItem* items) {
+    return BATCH ? (int64_t)items[blockIdx.x].slot : (int64_t)blockIdx.x;
+}
+template <bool BATCH>
+__device__ __forceinline__ DevInfo* tc_info(DevInfo* info, const TcBatchItem* items) {
+    return BATCH ? info + items[blockIdx.x].inst : info;
+}
+
+template <bool BATCH>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     gram_tc_kernel(const __grid_constant__ CUtensorMap tmapA, const __grid_constant__ CUtensorMap tmapB, int64_t m,
                    int n, int split, int64_t rows_per_cta,
                    long long* __restrict__ part_hi, long long* __restrict__ part_lo, int* __restrict__ part_E,
-                   DevInfo* info) {
+                   DevInfo* info, const TcBatchItem* __restrict__ items) {
     extern __shared__ unsigned char tc_dyn[];
     // 1024-byte alignment for the swizzled operand atoms
     unsigned char* base = tc_dyn + ((1024 - (smem_addr(tc_dyn) & 1023)) & 1023);
@@ -325,9 +338,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // sub-chunks are dealt round-robin (CTA b takes b, b + P, b + 2P, ...): at any time the
     // CTAs stream neighbouring 256-byte pieces of every column.  A CTA takes at most
     // rows_per_cta rows (the fixed-point bounds need <= 2^15).
-    const int64_t subs = (m + TC_SUB - 1) / TC_SUB;
-    const int64_t P = gridDim.x;
-    const int G = (int64_t)blockIdx.x < subs ? (int)((subs - 1 - blockIdx.x) / P + 1) : 0;
+    // Batched use (items != null): CTA b streams the rows [r0, r1) of one instance alone
+    // (a multiple of 64 rows apart from the instance's last row), through that instance's
+    // tensor map in global memory, into partial slot items[b].slot.
+    // (The slot and the status block are re-read where they are used, so that they hold no
+    // registers through the main loop.)
+    const CUtensorMap* mapA = &tmapA;
+    int64_t first = blockIdx.x, P = gridDim.x;
+    int G;
+    if (BATCH) {
+        const TcBatchItem it = items[blockIdx.x];
+        mapA = static_cast<const CUtensorMap*>(it.tmap);
+        n = it.n;
+        split = 0;
+        first = it.r0 / TC_SUB;
+        P = 1;
+        G = (int)((it.r1 - it.r0 + TC_SUB - 1) / TC_SUB);
+    } else {
+        const int64_t subs = (m + TC_SUB - 1) / TC_SUB;
+        G = (int64_t)blockIdx.x < subs ? (int)((subs - 1 - blockIdx.x) / P + 1) : 0;
+    }
     (void)rows_per_cta;
 
     if (tid == 0) {
@@ -356,7 +386,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         asm volatile("setmaxnreg.dec.sync.aligned.u32 32;");
         if (warp == 0 && lane == 0) {
             // ---------------- TMA producer
-            tma_prefetch_desc(&tmapA);
+            tma_prefetch_desc(mapA);
             if (split) tma_prefetch_desc(&tmapB);
             // split: two 32-column groups (FP columns 0..31 and 32..63) from two maps
             const unsigned bytes = (unsigned)(TC_SUB * (split ? 64 : n) * 4);
@@ -369,8 +399,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
                 if (S.abort) break;
                 mbar_expect_tx(&S.fp_full[f], bytes);
-                const int row0 = (int)(((int64_t)blockIdx.x + (int64_t)g * P) * TC_SUB);
-                tma_load_2d(fpb + (size_t)f * 64 * TC_SUB, &tmapA, row0, 0, &S.fp_full[f]);
+                const int row0 = (int)((first + (int64_t)g * P) * TC_SUB);
+                tma_load_2d(fpb + (size_t)f * 64 * TC_SUB, mapA, row0, 0, &S.fp_full[f]);
                 if (split) tma_load_2d(fpb + (size_t)f * 64 * TC_SUB + 32 * TC_SUB, &tmapB, row0, 0, &S.fp_full[f]);
                 issued = g + 1;
             }
@@ -481,8 +511,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&S.dec_full[r]);
             }
-            if (bad) atomicOr(&info->flags, FLAG_NONFINITE);
-            part_E[(size_t)blockIdx.x * 64 + j] = Eacc;
+            if (bad) atomicOr(&tc_info<BATCH>(info, items)->flags, FLAG_NONFINITE);
+            part_E[(size_t)tc_slot<BATCH>(items) * 64 + j] = Eacc;
         }
     } else {
         // ---------------- 16 worker warps.  Per sub-chunk: take the record, write the 7 digit
@@ -577,8 +607,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // partials of this CTA: W = sum over blocks (s < t) + 1/2 (s = s); G = W + W^T later.
         // The two digit halves of row i add into the same W(i, j): half 0 first, then half 1.
         const int lanei = quad * 32 + lane, h = lanei >> 6, i = lanei & 63;
-        long long* ph = part_hi + (size_t)blockIdx.x * 64 * 64;
-        long long* pl = part_lo + (size_t)blockIdx.x * 64 * 64;
+        long long* ph = part_hi + (size_t)tc_slot<BATCH>(items) * 64 * 64;
+        long long* pl = part_lo + (size_t)tc_slot<BATCH>(items) * 64 * 64;
         for (int hh = 0; hh < 2; ++hh) {
             if (h == hh) {
 #pragma unroll
@@ -596,7 +626,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_fence_before();
     __syncthreads();
     if (S.abort && tid == 0) {
-        atomicOr(&info->flags, FLAG_TIMEOUT);
+        atomicOr(&tc_info<BATCH>(info, items)->flags, FLAG_TIMEOUT);
         // no TMA write may land after the CTA exits: wait (bounded) for the last loads
         for (int g = (tma_issued > TC_SF ? tma_issued - TC_SF : 0); g < tma_issued; ++g)
             (void)mbar_wait(&S.fp_full[g % TC_SF], (g / TC_SF) & 1);
@@ -659,10 +689,33 @@ cudaError_t launch_gram_tc2(const void* A, int64_t m, int n, int64_t lda, int c1
     long long* ph = reinterpret_cast<long long*>(part);
     long long* pl = ph + (size_t)plan.P * 64 * 64;
     int* pE = reinterpret_cast<int*>(pl + (size_t)plan.P * 64 * 64);
-    e = cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    e = cudaFuncSetAttribute(gram_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
     if (e != cudaSuccess) return e;
-    gram_tc_kernel<<<plan.P, TC_THREADS, TC_SMEM, s>>>(tmapA, tmapB, m, split ? 64 : n, split ? 1 : 0,
-                                                       plan.rows_per_cta, ph, pl, pE, info);
+    gram_tc_kernel<false><<<plan.P, TC_THREADS, TC_SMEM, s>>>(tmapA, tmapB, m, split ? 64 : n, split ? 1 : 0,
+                                                       plan.rows_per_cta, ph, pl, pE, info, nullptr);
+    return cudaGetLastError();
+}
+
+bool gram_tc_batch_ok(const void* A, int64_t lda) { return ((uintptr_t)A % 16 == 0) && (lda % 4 == 0); }
+
+size_t tc_tmap_bytes() { return sizeof(CUtensorMap); }
+
+cudaError_t make_tc_batch_tmap(void* map, const float* A, int64_t m, int n, int64_t lda) {
+    return make_tmap_2d(static_cast<CUtensorMap*>(map), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, sizeof(float), A,
+                        (uint64_t)m, (uint64_t)n, (uint64_t)lda, TC_SUB, (uint32_t)n, CU_TENSOR_MAP_SWIZZLE_NONE);
+}
+
+cudaError_t launch_gram_tc_batch(const TcBatchItem* items, int nitems, void* part, int total_slots, DevInfo* infos,
+                                 cudaStream_t s) {
+    if (nitems == 0) return cudaSuccess;
+    long long* ph = reinterpret_cast<long long*>(part);
+    long long* pl = ph + (size_t)total_slots * 64 * 64;
+    int* pE = reinterpret_cast<int*>(pl + (size_t)total_slots * 64 * 64);
+    cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    if (e != cudaSuccess) return e;
+    CUtensorMap unused;
+    std::memset(&unused, 0, sizeof(unused));
+    gram_tc_kernel<true><<<nitems, TC_THREADS, TC_SMEM, s>>>(unused, unused, 0, 64, 0, 0, ph, pl, pE, infos, items);
     return cudaGetLastError();
 }
 

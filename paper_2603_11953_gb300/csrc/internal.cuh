@@ -140,7 +140,8 @@ cudaError_t launch_compute_u_v2(const float* A, int64_t m, int n, int64_t lda, c
 // Vh, W) are the instance's own; sigma, V, U are the caller's (U may be null).
 constexpr size_t BATCH_SLOT = 64 * 64;  // int64 entries per Gram partial slot (hi or lo)
 constexpr int BATCH_ROWS = 16384;       // rows per Gram work item (a multiple of GRAM_KC)
-constexpr int BATCH_UROWS = 256;        // rows per U work item
+// rows per U work item: 256 threads x 4 rows, spread over ceil(n / 16) column groups
+__host__ __device__ inline int batch_u_rows(int n) { return n <= 16 ? 1024 : n <= 32 ? 512 : 256; }
 struct BatchInst {
     const float* A;
     int64_t m, lda;
@@ -161,6 +162,19 @@ struct BatchGramItem {
     int inst, slot;
     int64_t r0, r1;
 };
+// Tensor-core items: one CTA streams rows [r0, r1) (r0 a multiple of 64, at most
+// 2^15 rows) of one instance through its tensor map (tc_tmap_bytes() bytes,
+// 64-byte aligned, in device memory; made by make_tc_batch_tmap on the host).
+struct TcBatchItem {
+    const void* tmap;
+    int64_t r0, r1;
+    int n, slot, inst, pad;
+};
+bool gram_tc_batch_ok(const void* A, int64_t lda);
+size_t tc_tmap_bytes();
+cudaError_t make_tc_batch_tmap(void* map, const float* A, int64_t m, int n, int64_t lda);
+cudaError_t launch_gram_tc_batch(const TcBatchItem* items, int nitems, void* part, int total_slots, DevInfo* infos,
+                                 cudaStream_t s);
 size_t gram_batch_partials_bytes(int total_slots);
 // One launch for the items of one padded width NP (16, 32, 48 or 64).
 cudaError_t launch_gram_batch(const BatchInst* inst, const BatchGramItem* items, int nitems, int NP, bool vec,

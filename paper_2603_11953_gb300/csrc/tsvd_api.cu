@@ -411,7 +411,9 @@ tsvd_status batch_run(tsvd_ctx* h, int32_t count, const void* const* A, const in
                       const int64_t* ldu, tsvd_info* info) {
     std::vector<BatchInst> inst((size_t)count);
     std::vector<BatchGramItem> cls[4];
-    std::vector<int64_t> crow[4];
+    std::vector<TcBatchItem> tci;  // tensor-core items (tmap filled in once the offsets are known)
+    std::vector<int> tcmap((size_t)count, -1);
+    int ntc = 0;
     int slots = 0;
     int64_t utiles = 0;
     size_t per_off = 0;
@@ -424,15 +426,20 @@ tsvd_status batch_run(tsvd_ctx* h, int32_t count, const void* const* A, const in
         d.m = m[i];
         d.lda = lda[i];
         d.n = ni;
-        d.NP = ni <= 16 ? 16 : ni <= 32 ? 32 : ni <= 48 ? 48 : 64;
+        // the tensor-core Gram where the instance can be TMA-loaded (gram_variant 2 forces the
+        // CUDA-core Ozaki kernel); its partials are 64 x 64
+        const bool tc = h->opts.gram_variant == 0 && gram_tc_batch_ok(A[i], lda[i]);
+        d.NP = tc ? 64 : ni <= 16 ? 16 : ni <= 32 ? 32 : ni <= 48 ? 48 : 64;
         const int c = d.NP / 16 - 1;
-        if ((uintptr_t)A[i] % 16 != 0 || lda[i] % 4 != 0) vec[c] = false;
+        if (!tc && ((uintptr_t)A[i] % 16 != 0 || lda[i] % 4 != 0)) vec[c] = false;
+        if (tc) tcmap[(size_t)i] = ntc++;
         d.slot0 = slots;
         d.nslots = (int)((m[i] + BATCH_ROWS - 1) / BATCH_ROWS);
         for (int k = 0; k < d.nslots; ++k) {
             const int64_t r0 = (int64_t)k * BATCH_ROWS;
             const int64_t r1 = std::min<int64_t>(m[i], r0 + BATCH_ROWS);
-            cls[c].push_back(BatchGramItem{i, slots + k, r0, r1});
+            if (tc) tci.push_back(TcBatchItem{nullptr, r0, r1, ni, slots + k, i, 0});
+            else cls[c].push_back(BatchGramItem{i, slots + k, r0, r1});
         }
         slots += d.nslots;
         d.sigma = static_cast<float*>(sigma[i]);
@@ -442,7 +449,7 @@ tsvd_status batch_run(tsvd_ctx* h, int32_t count, const void* const* A, const in
         d.U = want_u ? static_cast<float*>(U[i]) : nullptr;
         d.ldu = want_u ? ldu[i] : 0;
         d.utile0 = utiles;
-        if (want_u) utiles += (m[i] + BATCH_UROWS - 1) / BATCH_UROWS;
+        if (want_u) utiles += (m[i] + batch_u_rows(ni) - 1) / batch_u_rows(ni);
         per[(size_t)i] = per_off;
         per_off += align_up(sizeof(double) * (2 * (size_t)ni * ni + ni) + sizeof(float) * (size_t)ni * ni);
     }
@@ -454,12 +461,18 @@ tsvd_status batch_run(tsvd_ctx* h, int32_t count, const void* const* A, const in
         coff[c] = nitems;
         nitems += cls[c].size();
     }
-    // workspace: [descriptors][items][infos][partials][per-instance G, lam, Vh, W]
+    std::stable_sort(tci.begin(), tci.end(),
+                     [](const TcBatchItem& a, const TcBatchItem& b) { return a.r1 - a.r0 > b.r1 - b.r0; });
+    // workspace: [descriptors][items][tensor-core items][tensor maps][infos][partials]
+    //            [per-instance G, lam, Vh, W]; the first four come through the staging buffer
     const size_t b_inst = align_up(sizeof(BatchInst) * (size_t)count);
     const size_t b_items = align_up(sizeof(BatchGramItem) * nitems);
+    const size_t b_tci = align_up(sizeof(TcBatchItem) * tci.size());
+    const size_t b_maps = align_up(tc_tmap_bytes() * (size_t)ntc);
     const size_t b_info = align_up(sizeof(DevInfo) * (size_t)count);
     const size_t b_part = align_up(gram_batch_partials_bytes(slots));
-    const size_t o_items = b_inst, o_info = o_items + b_items, o_part = o_info + b_info, o_per = o_part + b_part;
+    const size_t o_items = b_inst, o_tci = o_items + b_items, o_maps = o_tci + b_tci, o_info = o_maps + b_maps;
+    const size_t o_part = o_info + b_info, o_per = o_part + b_part;
     tsvd_status st = ensure_ws(h, o_per + per_off);
     if (st != TSVD_OK) return st;
     for (int32_t i = 0; i < count; ++i) {
@@ -472,7 +485,7 @@ tsvd_status batch_run(tsvd_ctx* h, int32_t count, const void* const* A, const in
         d.W = reinterpret_cast<float*>(d.Vh + nn);
     }
     // descriptors and items through the pinned staging buffer
-    const size_t stage_need = b_inst + b_items;
+    const size_t stage_need = o_info;
     if (h->stage_ev) {
         if (cudaEventSynchronize(h->stage_ev) != cudaSuccess) return from_cuda(cudaGetLastError());
     } else if (cudaEventCreateWithFlags(&h->stage_ev, cudaEventDisableTiming) != cudaSuccess) {
@@ -494,6 +507,15 @@ tsvd_status batch_run(tsvd_ctx* h, int32_t count, const void* const* A, const in
         if (!cls[c].empty())
             std::memcpy(sb + b_inst + sizeof(BatchGramItem) * coff[c], cls[c].data(),
                         sizeof(BatchGramItem) * cls[c].size());
+    for (int32_t i = 0; i < count; ++i) {
+        const int k = tcmap[(size_t)i];
+        if (k < 0) continue;
+        if (make_tc_batch_tmap(sb + o_maps + tc_tmap_bytes() * (size_t)k, static_cast<const float*>(A[i]), m[i],
+                               (int)n[i], lda[i]) != cudaSuccess)
+            return TSVD_ERR_UNSUPPORTED;
+    }
+    for (auto& it : tci) it.tmap = base(h) + o_maps + tc_tmap_bytes() * (size_t)tcmap[(size_t)it.inst];
+    if (!tci.empty()) std::memcpy(sb + o_tci, tci.data(), sizeof(TcBatchItem) * tci.size());
     cudaError_t e = cudaMemcpyAsync(base(h), sb, stage_need, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaEventRecord(h->stage_ev, h->stream);
     const BatchInst* dinst = reinterpret_cast<const BatchInst*>(base(h));
@@ -504,6 +526,9 @@ tsvd_status batch_run(tsvd_ctx* h, int32_t count, const void* const* A, const in
     if (e == cudaSuccess) e = cudaMemsetAsync(h->dinfo, 0, sizeof(DevInfo), h->stream);
     if (e != cudaSuccess) return from_cuda(e);
     record(h, 0);
+    e = launch_gram_tc_batch(reinterpret_cast<const TcBatchItem*>(base(h) + o_tci), (int)tci.size(), part, slots,
+                             dinfos, h->stream);
+    if (e != cudaSuccess) return from_cuda(e);
     for (int c = 0; c < 4; ++c) {
         e = launch_gram_batch(dinst, ditems + coff[c], (int)cls[c].size(), 16 * (c + 1), vec[c], part, slots, dinfos,
                               h->sm_count, h->stream);
