@@ -14,7 +14,9 @@
 // zeta = (beta - alpha) / (2 gamma), t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)),
 // c = 1 / sqrt(1 + t^2), s = t c, x_p <- c x_p - s x_q, x_q <- s x_p + c x_q,
 // alpha <- alpha - t gamma, beta <- beta + t gamma (norms recomputed from the
-// columns at the start of every sweep).
+// columns at the start of every sweep).  The angle and the clear-cut tests are
+// evaluated in FP32 (they only set how fast the off-diagonal shrinks); the
+// columns, the applied rotation and the borderline tests are FP64.
 #include "internal.cuh"
 
 namespace tsvd {
@@ -23,14 +25,35 @@ namespace {
 constexpr int BT = 256;      // threads per instance CTA
 constexpr int BGROUP = 8;    // lanes per column pair
 
+__device__ __forceinline__ unsigned group_mask() { return 0xffu << (threadIdx.x & 24); }
 __device__ __forceinline__ double group_sum(double v) {
-    const unsigned mask = 0xffu << (threadIdx.x & 24);  // the 8 lanes of this group only
+    const unsigned mask = group_mask();  // the 8 lanes of this group only
 #pragma unroll
     for (int o = BGROUP / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o);
     return v;
 }
 
 __device__ __forceinline__ int player(int pos, int r, int N) { return pos == 0 ? 0 : 1 + (pos - 1 + r) % (N - 1); }
+
+// double <-> float by integer bit operations (GB300's FP64 pipe is narrow).  to_f32
+// truncates the significand and maps magnitudes outside the normal float range to 0 or
+// FLT_MAX: it only feeds angles and tests whose accuracy sets the convergence speed.
+__device__ __forceinline__ float to_f32(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int ex = (int)((b >> 52) & 0x7ff) - 1023;
+    const unsigned sg = (unsigned)(b >> 63) << 31;
+    if (ex < -126) return __uint_as_float(sg);
+    if (ex > 127) return __uint_as_float(sg | 0x7f7fffffu);
+    return __uint_as_float(sg | ((unsigned)(ex + 127) << 23) | (unsigned)((b >> 29) & 0x7fffffu));
+}
+__device__ __forceinline__ double to_f64(float x) {  // exact for normal floats and zero
+    const unsigned b = __float_as_uint(x);
+    const unsigned ex = (b >> 23) & 0xff;
+    if (ex == 0) return 0.0;
+    return __longlong_as_double((long long)(((unsigned long long)(b >> 31) << 63) |
+                                            ((unsigned long long)(ex + 896) << 52) |
+                                            ((unsigned long long)(b & 0x7fffffu) << 29)));
+}
 
 __global__ void __launch_bounds__(BT) eig_batch_kernel(const BatchInst* __restrict__ inst, double tol,
                                                        int max_sweeps, DevInfo* __restrict__ infos) {
@@ -42,6 +65,8 @@ __global__ void __launch_bounds__(BT) eig_batch_kernel(const BatchInst* __restri
     const BatchInst& d = inst[blockIdx.x];
     DevInfo* info = infos + blockIdx.x;
     const int n = d.n, LD = n + 1, tid = threadIdx.x;
+    const double tol2 = tol * tol;
+    const float tol_f = (float)tol;
     double* M = sm;  // [n][LD]: M, then row k = row k of R = column k of X
     for (int idx = tid; idx < n * n; idx += BT) {
         const int i = idx % n, j = idx / n;
@@ -136,26 +161,74 @@ __global__ void __launch_bounds__(BT) eig_batch_kernel(const BatchInst* __restri
                     for (int i = gl; i < n; i += BGROUP) g = fma(xp[i], xq[i], g);
                     g = group_sum(g);
                     const double a = nrm[p], b = nrm[q];
-                    const double scale = sqrt(a) * sqrt(b);
-                    const double ratio = scale > 0.0 ? fabs(g) / scale : 0.0;
-                    if (ratio > tol) {
-                        const double zeta = (b - a) / (2.0 * g);
-                        const double az = fabs(zeta);
-                        double t = az > 1e150 ? 0.5 / az : 1.0 / (az + sqrt(fma(az, az, 1.0)));
-                        t = copysign(t, zeta);
-                        const double c = 1.0 / sqrt(fma(t, t, 1.0)), s = t * c;
+                    // the scaled test |g| > tol sqrt(a b): in FP32 when the ratio is clearly on one
+                    // side (factor 2), exactly in FP64 otherwise
+                    const float af = to_f32(a), bf = to_f32(b), gf = fabsf(to_f32(g));
+                    const bool in_range = af > 1e-30f && af < 1e30f && bf > 1e-30f && bf < 1e30f && gf < 1e30f;
+                    const float rr = in_range ? gf * rsqrtf(af) * rsqrtf(bf) : 0.0f;
+                    bool rot;
+                    if (in_range && rr > 2.0f * tol_f) rot = true;
+                    else if (in_range && rr < 0.5f * tol_f) rot = false;
+                    else rot = g != 0.0 && a > 0.0 && b > 0.0 && g * g > tol2 * (a * b);
+                    if (rot) {
+                        // Rutishauser's t = sgn(zeta) / (|zeta| + sqrt(1 + zeta^2)), zeta = (b - a) / 2g,
+                        // in FP32 from ratios <= 1, and c0 = 1 / sqrt(1 + t^2), s0 = t c0; then
+                        // (c, s) = (c0, s0) f with f = 1 - e/2 + 3e^2/8, e = c0^2 + s0^2 - 1
+                        // (|e| ~ 2^-24): orthogonal to FP64 precision.
+                        double c, s, t;
+                        if (in_range) {  // then rr > 0: g is a normal float, hf != 0
+                            const float df = bf - af, hf = 2.0f * to_f32(g);
+                            const float adf = fabsf(df), ahf = fabsf(hf);
+                            const float sz = (df == 0.0f || (df > 0.0f) == (hf > 0.0f)) ? 1.0f : -1.0f;
+                            float tf;
+                            if (adf >= ahf) {
+                                const float z = ahf / adf;
+                                tf = sz * z / (1.0f + sqrtf(fmaf(z, z, 1.0f)));
+                            } else {
+                                const float w = adf / ahf;
+                                tf = sz / (w + sqrtf(fmaf(w, w, 1.0f)));
+                            }
+                            const float cf = rsqrtf(fmaf(tf, tf, 1.0f));
+                            const double c0 = to_f64(cf), s0 = to_f64(tf * cf);
+                            const double e = fma(c0, c0, fma(s0, s0, -1.0));
+                            const double f = fma(e, fma(e, 0.375, -0.5), 1.0);
+                            c = c0 * f;
+                            s = s0 * f;
+                            t = to_f64(tf);
+                        } else {  // norms or g outside the float range: the angle in FP64
+                            const double zeta = (b - a) / (2.0 * g);
+                            const double az = fabs(zeta);
+                            t = az > 1e150 ? 0.5 / az : 1.0 / (az + sqrt(fma(az, az, 1.0)));
+                            t = copysign(t, zeta);
+                            c = 1.0 / sqrt(fma(t, t, 1.0));
+                            s = t * c;
+                        }
                         for (int i = gl; i < n; i += BGROUP) {
                             const double u = xp[i], v = xq[i];
                             xp[i] = fma(c, u, -s * v);
                             xq[i] = fma(s, u, c * v);
                         }
+                        // norms follow a - t g, b + t g; one that dropped 16-fold is recomputed
+                        const double tg = t * g;
+                        double na = a - tg, nb = b + tg;
+                        __syncwarp(group_mask());
+                        if (na < 0.0625 * a) {
+                            double r = 0.0;
+                            for (int i = gl; i < n; i += BGROUP) r = fma(xp[i], xp[i], r);
+                            na = group_sum(r);
+                        }
+                        if (nb < 0.0625 * b) {
+                            double r = 0.0;
+                            for (int i = gl; i < n; i += BGROUP) r = fma(xq[i], xq[i], r);
+                            nb = group_sum(r);
+                        }
                         if (gl == 0) {
-                            nrm[p] = fma(-t, g, a);
-                            nrm[q] = fma(t, g, b);
+                            nrm[p] = na;
+                            nrm[q] = nb;
                             atomicAdd(&s_count[sweep & 1], 1);
                         }
                     }
-                    if (gl == 0) off_bits = max(off_bits, (unsigned long long)__double_as_longlong(ratio));
+                    if (gl == 0 && !rot) off_bits = max(off_bits, (unsigned long long)__float_as_uint(rr));
                 }
             }
             __syncthreads();
@@ -183,7 +256,7 @@ __global__ void __launch_bounds__(BT) eig_batch_kernel(const BatchInst* __restri
     }
     if (tid == 0) {
         info->sweeps = sweep;
-        info->off_norm = __longlong_as_double((long long)s_off);
+        info->off_norm = (double)__uint_as_float((unsigned)s_off);  // largest FP32 ratio left unrotated
         if (!converged) atomicOr(&info->flags, FLAG_NO_CONVERGENCE);
     }
 }
