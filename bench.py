@@ -32,6 +32,18 @@ DEFAULT_WORKLOAD = "ozaki_4194304x64_fp32"
 # gram_tc, gram_combine, chol_piv, onesided_jacobi, finish, compute_u_tc, finalize_info
 KERNELS_PER_STEP = 7
 FP64_DFMA_PER_CLK_SM = 1.68  # measured on GB300: 16 warps x independent DFMA chains, one SM
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of each stage's kernels, from
+# the ncu --set full summaries in profiles/ (captured at m = 1,048,576 rows); stages whose traffic
+# grows with m are scaled by m / 1,048,576.  None where no capture covers the stage.
+NCU_TRAFFIC = {
+    "ozaki_4194304x64_fp32": {"gram": (272.706816e6, True),          # gram_tc_kernel (+ combine 10 MB)
+                              "jacobi": (0.222208e6, False),         # chol_piv + onesided_jacobi + finish
+                              "compute_u": (482.628352e6, True)},    # compute_u_tc_kernel
+    "stress_16777216x32_fp64": {"gram": None,
+                                "jacobi": (0.119296e6, False),       # eig_dd_kernel
+                                "compute_u": (491.981568e6, True)},  # compute_u_kernel<double>
+}
+NCU_ROWS = 1048576
 
 
 def peaks():
@@ -476,7 +488,8 @@ def main():
     rl = dict(cands[dom][1])
     rl["kernel"] = dom
     rl["frac"] = rl["achieved"] / rl["peak"]
-    rl["traffic"] = None
+    tr = NCU_TRAFFIC.get(spec.name, {}).get(dom)
+    rl["traffic"] = None if tr is None else tr[0] * (m / NCU_ROWS if tr[1] else 1.0)
     rl["peak_source"] = pk["src"]
     stages = {"gram_ms": gram_ms, "eig_ms": eig_ms, "u_ms": u_ms, "total_ms": stage_ms[3],
               "gram_hbm_frac": (gram_bytes / (gram_ms * 1e-3) / 1e9) / pk["hbm"],
