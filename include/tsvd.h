@@ -151,13 +151,22 @@ TSVD_API tsvd_status tsvd_solve(tsvd_handle h, const void* A, int64_t m, int64_t
                        tsvd_prec working, tsvd_prec higher, void* sigma, void* V, int64_t ldv,
                        void* U, int64_t ldu, tsvd_info* info);
 
-/* Many independent instances (ragged m and n, n <= 64) in one call.  All
- * pointer arrays (A[count], sigma[count], V[count], U[count]) and size arrays
- * (m, n, lda, ldv, ldu) are HOST arrays of device pointers / sizes; U (the
- * array) may be NULL, or any U[i] may be NULL, to skip U for that instance.
- * info: NULL or `count` entries (device or pinned host).
+/* Many independent instances of Alg. 1 (ragged m and n, n <= 64, FP32 working,
+ * FP64 higher) in one call.  All pointer arrays (A[count], sigma[count],
+ * V[count], U[count]) and size arrays (m, n, lda, ldv, ldu) are HOST arrays of
+ * device pointers / sizes; U (the array) may be NULL, or any U[i] may be NULL,
+ * to skip U for that instance.  info: NULL or `count` entries (device or
+ * pinned host), each with that instance's status.
+ * The batch runs in a fixed number of launches whatever the count: Gram work
+ * items of at most 16384 rows (tensor-core Gram through per-instance tensor
+ * maps when A[i] is 16-byte aligned and lda[i] % 4 == 0, else the CUDA-core
+ * Ozaki kernel; gram_variant 2 forces the latter), one combine, one CTA per
+ * instance for a FP64 pivoted Cholesky + one-sided Jacobi and the finish, and
+ * U over all instances' row tiles.  gram_variant 1 (the plain FP64 form)
+ * solves the instances one after another instead.  The handle's status
+ * (tsvd_sync_status) is the most severe of the instances'.
  * Errors: TSVD_ERR_ARG for any bad instance (nothing is enqueued),
- * TSVD_ERR_UNSUPPORTED for n > 64. */
+ * TSVD_ERR_UNSUPPORTED for n > 64 or another precision pair. */
 TSVD_API tsvd_status tsvd_batch_solve(tsvd_handle h, int32_t count, const void* const* A, const int64_t* m,
                              const int64_t* n, const int64_t* lda, tsvd_prec working,
                              tsvd_prec higher, void* const* sigma, void* const* V,
