@@ -339,12 +339,16 @@ __device__ __forceinline__ __int128 shfl_xor_i128(__int128 v, int o) {
 // The exact sum over P partials (slot c at c * slot (hi, lo) and c * estride
 // (exponents), NP x NP row-major) of entry (i, j), rounded to a double-double;
 // all 32 lanes of the warp take part.
+// halves = 2: every slot holds two tiles to add, at (i, j) and (32 + i, 32 + j).
 __device__ __forceinline__ void combine_entry(const long long* __restrict__ part_hi,
                                               const long long* __restrict__ part_lo,
                                               const int* __restrict__ part_E, int P, size_t slot, int estride,
-                                              int NP, int i, int j, int lane, double& hi, double& lo) {
+                                              int NP, int i0, int j0, int lane, double& hi, double& lo,
+                                              int halves = 1) {
+    const int PV = P * halves;
     int emax = EXP_EMPTY;
-    for (int c = lane; c < P; c += 32) {
+    for (int v = lane; v < PV; v += 32) {
+        const int c = v / halves, off = (v % halves) * 32, i = i0 + off, j = j0 + off;
         const int Ei = part_E[(size_t)c * estride + i], Ej = part_E[(size_t)c * estride + j];
         if (Ei == EXP_EMPTY || Ej == EXP_EMPTY) continue;
         emax = max(emax, Ei + Ej);
@@ -355,7 +359,8 @@ __device__ __forceinline__ void combine_entry(const long long* __restrict__ part
     if (emax != EXP_EMPTY) {
         // value_c = 2^(e_c - 63) * (h * 2^16 + l); fixed point unit 2^(emax - 63 - 29)
         __int128 acc = 0;
-        for (int c = lane; c < P; c += 32) {
+        for (int v = lane; v < PV; v += 32) {
+            const int c = v / halves, off = (v % halves) * 32, i = i0 + off, j = j0 + off;
             const int Ei = part_E[(size_t)c * estride + i], Ej = part_E[(size_t)c * estride + j];
             if (Ei == EXP_EMPTY || Ej == EXP_EMPTY) continue;
             const int sh = emax - (Ei + Ej);
@@ -428,7 +433,7 @@ __global__ void __launch_bounds__(256) gram_combine_batch_kernel(const BatchInst
         pair_of(idx, i, j);
         double hi, lo;
         combine_entry(part_hi + s0 * BATCH_SLOT, part_lo + s0 * BATCH_SLOT, part_E + s0 * 64, d.nslots, BATCH_SLOT,
-                      64, NP, i, j, lane, hi, lo);
+                      64, NP, i, j, lane, hi, lo, d.halves);
         if (lane == 0) {
             d.G[i + (size_t)j * n] = hi;
             d.G[j + (size_t)i * n] = hi;

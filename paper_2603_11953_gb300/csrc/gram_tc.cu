@@ -343,17 +343,29 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // tensor map in global memory, into partial slot items[b].slot.
     // (The slot and the status block are re-read where they are used, so that they hold no
     // registers through the main loop.)
+    // An item with a second map (n <= 32) packs two consecutive 64-row blocks side by side as
+    // the two 32-column groups: sub-chunk g covers rows r0 + 128 g .. + 127, and the instance's
+    // Gram is the sum of the two diagonal 32 x 32 tiles.
     const CUtensorMap* mapA = &tmapA;
+    const CUtensorMap* mapB = &tmapB;
     int64_t first = blockIdx.x, P = gridDim.x;
     int G;
     if (BATCH) {
         const TcBatchItem it = items[blockIdx.x];
         mapA = static_cast<const CUtensorMap*>(it.tmap);
-        n = it.n;
-        split = 0;
         first = it.r0 / TC_SUB;
-        P = 1;
-        G = (int)((it.r1 - it.r0 + TC_SUB - 1) / TC_SUB);
+        if (it.tmap2 != nullptr) {
+            mapB = static_cast<const CUtensorMap*>(it.tmap2);
+            n = 64;
+            split = 1;
+            P = 2;
+            G = (int)((it.r1 - it.r0 + 2 * TC_SUB - 1) / (2 * TC_SUB));
+        } else {
+            n = it.n;
+            split = 0;
+            P = 1;
+            G = (int)((it.r1 - it.r0 + TC_SUB - 1) / TC_SUB);
+        }
     } else {
         const int64_t subs = (m + TC_SUB - 1) / TC_SUB;
         G = (int64_t)blockIdx.x < subs ? (int)((subs - 1 - blockIdx.x) / P + 1) : 0;
@@ -387,7 +399,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (warp == 0 && lane == 0) {
             // ---------------- TMA producer
             tma_prefetch_desc(mapA);
-            if (split) tma_prefetch_desc(&tmapB);
+            if (split) tma_prefetch_desc(mapB);
             // split: two 32-column groups (FP columns 0..31 and 32..63) from two maps
             const unsigned bytes = (unsigned)(TC_SUB * (split ? 64 : n) * 4);
             int issued = 0;
@@ -401,7 +413,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 mbar_expect_tx(&S.fp_full[f], bytes);
                 const int row0 = (int)((first + (int64_t)g * P) * TC_SUB);
                 tma_load_2d(fpb + (size_t)f * 64 * TC_SUB, mapA, row0, 0, &S.fp_full[f]);
-                if (split) tma_load_2d(fpb + (size_t)f * 64 * TC_SUB + 32 * TC_SUB, &tmapB, row0, 0, &S.fp_full[f]);
+                if (split) tma_load_2d(fpb + (size_t)f * 64 * TC_SUB + 32 * TC_SUB, mapB, row0, 0, &S.fp_full[f]);
                 issued = g + 1;
             }
             tma_issued = issued;
@@ -700,9 +712,10 @@ bool gram_tc_batch_ok(const void* A, int64_t lda) { return ((uintptr_t)A % 16 ==
 
 size_t tc_tmap_bytes() { return sizeof(CUtensorMap); }
 
-cudaError_t make_tc_batch_tmap(void* map, const float* A, int64_t m, int n, int64_t lda) {
+cudaError_t make_tc_batch_tmap(void* map, const float* A, int64_t m, int n, int64_t lda, int box_cols) {
     return make_tmap_2d(static_cast<CUtensorMap*>(map), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, sizeof(float), A,
-                        (uint64_t)m, (uint64_t)n, (uint64_t)lda, TC_SUB, (uint32_t)n, CU_TENSOR_MAP_SWIZZLE_NONE);
+                        (uint64_t)m, (uint64_t)n, (uint64_t)lda, TC_SUB, (uint32_t)box_cols,
+                        CU_TENSOR_MAP_SWIZZLE_NONE);
 }
 
 cudaError_t launch_gram_tc_batch(const TcBatchItem* items, int nitems, void* part, int total_slots, DevInfo* infos,

@@ -147,6 +147,7 @@ struct BatchInst {
     int64_t m, lda;
     int n, NP;
     int slot0, nslots;  // Gram partial slots of this instance
+    int halves;         // 2: each slot holds two diagonal 32 x 32 tiles to add (packed rows)
     double* G;          // n x n, ld n
     double* lam;        // n
     double* Vh;         // n x n, ld n
@@ -165,14 +166,18 @@ struct BatchGramItem {
 // Tensor-core items: one CTA streams rows [r0, r1) (r0 a multiple of 64, at most
 // 2^15 rows) of one instance through its tensor map (tc_tmap_bytes() bytes,
 // 64-byte aligned, in device memory; made by make_tc_batch_tmap on the host).
+// With tmap2 (n <= 32; tmap and tmap2 map rows 0.. and 64.. of the instance with
+// 32-column boxes) the CTA takes two 64-row blocks per step as the two column
+// groups, and the instance's partial is the sum of the two diagonal tiles.
 struct TcBatchItem {
     const void* tmap;
+    const void* tmap2;
     int64_t r0, r1;
     int n, slot, inst, pad;
 };
 bool gram_tc_batch_ok(const void* A, int64_t lda);
 size_t tc_tmap_bytes();
-cudaError_t make_tc_batch_tmap(void* map, const float* A, int64_t m, int n, int64_t lda);
+cudaError_t make_tc_batch_tmap(void* map, const float* A, int64_t m, int n, int64_t lda, int box_cols);
 cudaError_t launch_gram_tc_batch(const TcBatchItem* items, int nitems, void* part, int total_slots, DevInfo* infos,
                                  cudaStream_t s);
 size_t gram_batch_partials_bytes(int total_slots);

@@ -432,13 +432,17 @@ tsvd_status batch_run(tsvd_ctx* h, int32_t count, const void* const* A, const in
         d.NP = tc ? 64 : ni <= 16 ? 16 : ni <= 32 ? 32 : ni <= 48 ? 48 : 64;
         const int c = d.NP / 16 - 1;
         if (!tc && ((uintptr_t)A[i] % 16 != 0 || lda[i] % 4 != 0)) vec[c] = false;
+        // n <= 32: two 64-row blocks side by side per tensor-core step (two maps, 32-column boxes)
+        const bool pack = tc && ni <= 32 && m[i] >= 128;
         if (tc) tcmap[(size_t)i] = ntc++;
+        if (pack) ++ntc;
+        d.halves = pack ? 2 : 1;
         d.slot0 = slots;
         d.nslots = (int)((m[i] + BATCH_ROWS - 1) / BATCH_ROWS);
         for (int k = 0; k < d.nslots; ++k) {
             const int64_t r0 = (int64_t)k * BATCH_ROWS;
             const int64_t r1 = std::min<int64_t>(m[i], r0 + BATCH_ROWS);
-            if (tc) tci.push_back(TcBatchItem{nullptr, r0, r1, ni, slots + k, i, 0});
+            if (tc) tci.push_back(TcBatchItem{nullptr, pack ? A[i] : nullptr, r0, r1, ni, slots + k, i, 0});
             else cls[c].push_back(BatchGramItem{i, slots + k, r0, r1});
         }
         slots += d.nslots;
@@ -510,11 +514,20 @@ tsvd_status batch_run(tsvd_ctx* h, int32_t count, const void* const* A, const in
     for (int32_t i = 0; i < count; ++i) {
         const int k = tcmap[(size_t)i];
         if (k < 0) continue;
-        if (make_tc_batch_tmap(sb + o_maps + tc_tmap_bytes() * (size_t)k, static_cast<const float*>(A[i]), m[i],
-                               (int)n[i], lda[i]) != cudaSuccess)
-            return TSVD_ERR_UNSUPPORTED;
+        const float* Ai = static_cast<const float*>(A[i]);
+        const bool pack = inst[(size_t)i].halves == 2;
+        cudaError_t em = make_tc_batch_tmap(sb + o_maps + tc_tmap_bytes() * (size_t)k, Ai, m[i], (int)n[i], lda[i],
+                                            pack ? 32 : (int)n[i]);
+        if (em == cudaSuccess && pack)  // rows 64.. of the same instance
+            em = make_tc_batch_tmap(sb + o_maps + tc_tmap_bytes() * (size_t)(k + 1), Ai + 64, m[i] - 64, (int)n[i],
+                                    lda[i], 32);
+        if (em != cudaSuccess) return TSVD_ERR_UNSUPPORTED;
     }
-    for (auto& it : tci) it.tmap = base(h) + o_maps + tc_tmap_bytes() * (size_t)tcmap[(size_t)it.inst];
+    for (auto& it : tci) {
+        const size_t k = (size_t)tcmap[(size_t)it.inst];
+        it.tmap = base(h) + o_maps + tc_tmap_bytes() * k;
+        it.tmap2 = it.tmap2 != nullptr ? base(h) + o_maps + tc_tmap_bytes() * (k + 1) : nullptr;
+    }
     if (!tci.empty()) std::memcpy(sb + o_tci, tci.data(), sizeof(TcBatchItem) * tci.size());
     cudaError_t e = cudaMemcpyAsync(base(h), sb, stage_need, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaEventRecord(h->stage_ev, h->stream);

@@ -247,7 +247,8 @@ def test_batch_matches_single_solves_and_exact_u():
     the n x n stage) against single solves (tensor-core Gram, cluster Jacobi): both are the same
     exact Gram and FP64 Jacobi up to rounding, so sigma agrees to 2 FP32 ulps and V to 1e-4 (well
     separated spectra); U against the exact product with the batch's own W, (n + 1) u_32 (|A| |W|)."""
-    cases = [(3000, 8), (1024, 16), (7777, 24), (2048, 64), (4096, 1), (40000, 48), (16385, 33)]
+    cases = [(3000, 8), (1024, 16), (7777, 24), (2048, 64), (4096, 1), (40000, 48), (16385, 33), (130, 8), (200, 32),
+             (33000, 32)]
     As = [workloads.small_case(m, n, seed=31 + i, device="cuda")[0] for i, (m, n) in enumerate(cases)]
     sig = [torch.zeros(n, device="cuda") for _, n in cases]
     Vs = [colmajor(n, n, torch.float32) for _, n in cases]
