@@ -305,28 +305,54 @@ __global__ void __launch_bounds__(64) finish_batch_kernel(const BatchInst* __res
     if (tid < n) d.sigma[tid] = (float)sig[tid];
 }
 
-// U = A W over the row tiles of all instances: CTA -> (instance, tile) by a binary
-// search of the tile prefix.  A thread owns 4 rows by 16 columns; the 256 threads
-// cover batch_u_rows(n) rows (more rows when fewer 16-column groups are needed),
-// load four columns of A ahead of their FMAs, and accumulate in FP32 (the rounding
-// model of eq. (AV-0)).
+// fma.rn.f32x2: two IEEE FP32 FMAs (a row pair of A times a duplicated W entry)
+__device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b,
+                                                    unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void unpack2(unsigned long long v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+
+// U = A W over the row tiles of all instances.  CTA b takes a contiguous range of tiles
+// (so W, held duplicated {w, w} in shared memory, is reloaded only when the instance
+// changes).  A thread owns 4 rows (two row pairs) by 16 columns; the 256 threads cover
+// batch_u_rows(n) rows (more rows when fewer 16-column groups are needed), load four
+// columns of A ahead of their FMAs, and accumulate with packed FP32 FMAs (the rounding
+// model of eq. (AV-0): each entry is an ordinary FP32 dot product).
 __global__ void __launch_bounds__(256, 2) u_batch_kernel(const BatchInst* __restrict__ inst, int count,
                                                          int64_t utiles) {
-    __shared__ float Ws[64 * 64];
-    for (int64_t tile = blockIdx.x; tile < utiles; tile += gridDim.x) {
-        int lo = 0, hi = count - 1;
-        while (lo < hi) {  // last instance with utile0 <= tile
-            const int mid = (lo + hi + 1) >> 1;
-            if (inst[mid].utile0 <= tile) lo = mid; else hi = mid - 1;
-        }
+    __shared__ unsigned long long Ws[64 * 64];
+    const int64_t per = (utiles + gridDim.x - 1) / gridDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * per, t1 = min(utiles, t0 + per);
+    if (t0 >= t1) return;
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {  // last instance with utile0 <= t0
+        const int mid = (lo + hi + 1) >> 1;
+        if (inst[mid].utile0 <= t0) lo = mid; else hi = mid - 1;
+    }
+    int cur = -1;
+    for (int64_t tile = t0; tile < t1; ++tile) {
+        while (lo + 1 < count && inst[lo + 1].utile0 <= tile) ++lo;
         const BatchInst& d = inst[lo];
         const int n = d.n;
-        __syncthreads();  // the previous tile's reads of Ws are done
-        for (int idx = threadIdx.x; idx < n * 64; idx += blockDim.x) {
-            const int c = idx / 64, k = idx % 64;
-            Ws[idx] = k < n ? d.W[c + (size_t)k * n] : 0.f;
+        if (lo != cur) {
+            __syncthreads();  // the previous instance's reads of Ws are done
+            for (int idx = threadIdx.x; idx < n * 64; idx += blockDim.x) {
+                const int c = idx / 64, k = idx % 64;
+                const float w = k < n ? d.W[c + (size_t)k * n] : 0.f;
+                Ws[idx] = pack2(w, w);
+            }
+            __syncthreads();
+            cur = lo;
         }
-        __syncthreads();
         const int R = batch_u_rows(n) / 256;  // 4, 2 or 1 row groups of 256
         const int rg = threadIdx.x % (64 * R), cg = threadIdx.x / (64 * R);
         const int64_t r0 = (tile - d.utile0) * batch_u_rows(n) + 4 * rg;
@@ -334,34 +360,37 @@ __global__ void __launch_bounds__(256, 2) u_batch_kernel(const BatchInst* __rest
         const bool full = r0 + 3 < d.m;
         const bool vec = full && ((uintptr_t)d.A % 16 == 0) && (d.lda % 4 == 0) && ((uintptr_t)d.U % 16 == 0) &&
                          (d.ldu % 4 == 0);
-        float acc[4][16];
+        unsigned long long acc[2][16];
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
+        for (int r = 0; r < 2; ++r)
 #pragma unroll
-            for (int k = 0; k < 16; ++k) acc[r][k] = 0.f;
+            for (int k = 0; k < 16; ++k) acc[r][k] = 0ull;
         for (int c0 = 0; c0 < n; c0 += 4) {
-            float a[4][4];
+            unsigned long long a[4][2];
 #pragma unroll
             for (int cc = 0; cc < 4; ++cc) {
                 const int c = c0 + cc;
                 const float* src = d.A + (size_t)c * d.lda + r0;
+                float v[4];
                 if (c < n && vec) {
-                    const float4 v = __ldcs(reinterpret_cast<const float4*>(src));
-                    a[cc][0] = v.x; a[cc][1] = v.y; a[cc][2] = v.z; a[cc][3] = v.w;
+                    const float4 q = __ldcs(reinterpret_cast<const float4*>(src));
+                    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
                 } else {
 #pragma unroll
-                    for (int r = 0; r < 4; ++r) a[cc][r] = (c < n && r0 + r < d.m) ? src[r] : 0.f;
+                    for (int r = 0; r < 4; ++r) v[r] = (c < n && r0 + r < d.m) ? src[r] : 0.f;
                 }
+                a[cc][0] = pack2(v[0], v[1]);
+                a[cc][1] = pack2(v[2], v[3]);
             }
 #pragma unroll
             for (int cc = 0; cc < 4; ++cc) {
                 if (c0 + cc < n) {
-                    const float* w = Ws + (c0 + cc) * 64 + cg * 16;
+                    const unsigned long long* w = Ws + (c0 + cc) * 64 + cg * 16;
 #pragma unroll
                     for (int k = 0; k < 16; ++k) {
-                        const float wk = w[k];
-#pragma unroll
-                        for (int r = 0; r < 4; ++r) acc[r][k] = fmaf(a[cc][r], wk, acc[r][k]);
+                        const unsigned long long wk = w[k];
+                        acc[0][k] = ffma2(a[cc][0], wk, acc[0][k]);
+                        acc[1][k] = ffma2(a[cc][1], wk, acc[1][k]);
                     }
                 }
             }
@@ -370,13 +399,16 @@ __global__ void __launch_bounds__(256, 2) u_batch_kernel(const BatchInst* __rest
         for (int k = 0; k < 16; ++k) {
             const int j = cg * 16 + k;
             if (j < n) {
+                float u[4];
+                unpack2(acc[0][k], u[0], u[1]);
+                unpack2(acc[1][k], u[2], u[3]);
                 float* dst = d.U + (size_t)j * d.ldu + r0;
                 if (vec) {
-                    __stcs(reinterpret_cast<float4*>(dst), make_float4(acc[0][k], acc[1][k], acc[2][k], acc[3][k]));
+                    __stcs(reinterpret_cast<float4*>(dst), make_float4(u[0], u[1], u[2], u[3]));
                 } else {
 #pragma unroll
                     for (int r = 0; r < 4; ++r)
-                        if (r0 + r < d.m) dst[r] = acc[r][k];
+                        if (r0 + r < d.m) dst[r] = u[r];
                 }
             }
         }

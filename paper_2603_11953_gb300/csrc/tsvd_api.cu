@@ -554,7 +554,7 @@ tsvd_status batch_run(tsvd_ctx* h, int32_t count, const void* const* A, const in
     if (e == cudaSuccess) e = launch_finish_batch(dinst, count, dinfos, h->stream);
     if (e != cudaSuccess) return from_cuda(e);
     record(h, 2);
-    e = launch_u_batch(dinst, count, utiles, 8 * h->sm_count, h->stream);
+    e = launch_u_batch(dinst, count, utiles, 16 * h->sm_count, h->stream);
     if (e != cudaSuccess) return from_cuda(e);
     record(h, 3);
     e = launch_finalize_batch(dinfos, count, h->dinfo, h->stream);
