@@ -36,9 +36,9 @@ FP64_DFMA_PER_CLK_SM = 1.68  # measured on GB300: 16 warps x independent DFMA ch
 # the ncu --set full summaries in profiles/ (captured at m = 1,048,576 rows); stages whose traffic
 # grows with m are scaled by m / 1,048,576.  None where no capture covers the stage.
 NCU_TRAFFIC = {
-    "ozaki_4194304x64_fp32": {"gram": (272.706816e6, True),          # gram_tc_kernel (+ combine 10 MB)
+    "ozaki_4194304x64_fp32": {"gram": (272.634624e6, True),          # gram_tc_kernel (+ combine 10 MB)
                               "jacobi": (0.222208e6, False),         # chol_piv + onesided_jacobi + finish
-                              "compute_u": (482.628352e6, True)},    # compute_u_tc_kernel
+                              "compute_u": (482.525952e6, True)},    # compute_u_tc_kernel
     "stress_16777216x32_fp64": {"gram": None,
                                 "jacobi": (0.119296e6, False),       # eig_dd_kernel
                                 "compute_u": (491.981568e6, True)},  # compute_u_kernel<double>
@@ -258,8 +258,11 @@ def run_batch(args):
     dom = max(cands, key=lambda k: cands[k][0])
     rl = dict(cands[dom][1])
     rl.update(kernel=dom, frac=rl["achieved"] / rl["peak"], traffic=None, peak_source=pk["src"])
-    widths = {16 if n <= 16 else 32 if n <= 32 else 48 if n <= 48 else 64 for n in ns}
-    launches = len(widths) + 1 + 2 + 1 + 2  # Gram per width, combine, eig + finish, U, statuses
+    # tensor-core Gram for instances TMA can load (16-byte aligned, lda % 4 == 0), else one
+    # CUDA-core launch per padded width; then combine, eig + finish, U, statuses (2)
+    cuda_core = {16 if n <= 16 else 32 if n <= 32 else 48 if n <= 48 else 64
+                 for md, n in zip(metas, ns) if (4 * md["offset"]) % 16 or md["lda"] % 4}
+    launches = 1 + len(cuda_core) + 1 + 2 + 1 + 2
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
