@@ -154,6 +154,44 @@ def cpu_baseline(A_cpu, m, n, rows, reps=1):
     return gbs, dt
 
 
+def run_reference_batch(args):
+    """--impl reference on the batched workload: the oracle over its first instances (the same
+    instances, by seed, as the first ones of the 4096-instance batch) until about --ref-rows rows."""
+    import numpy as np
+    import oracle
+    from paper_2603_11953_gb300 import workloads
+    buf, metas = workloads.make_batch(count=8, device="cpu")
+    picked, rows = [], 0
+    for md in metas:
+        if picked and rows >= args.ref_rows:
+            break
+        A = buf[md["offset"]:md["offset"] + md["lda"] * md["n"]].view(md["n"], md["lda"]).T[:md["m"]]
+        picked.append(np.asfortranarray(A.numpy()))
+        rows += md["m"]
+
+    def one():
+        t0 = time.perf_counter()
+        for A in picked:
+            r = oracle.svd(A, higher=1)
+            oracle.rows_times(A, r["W_w"], np.arange(A.shape[0]), 24)
+        return time.perf_counter() - t0
+
+    for _ in range(args.warmup):
+        one()
+    tot = sum(one() for _ in range(args.steps))
+    nbytes = sum(A.shape[0] * A.shape[1] * 4 for A in picked)
+    gbs = args.steps * nbytes / tot / 1e9
+    sample = f"the first {len(picked)} instances ({rows} rows) of {BATCH_WORKLOAD}: exact Gram + FP64 Jacobi + exact U"
+    line = {"impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "fp32", "data": "synthetic",
+            "config": {"workload": BATCH_WORKLOAD, "instances_sample": len(picked), "rows_sample": rows},
+            "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_reference(args):
     """--impl reference: the CPU oracle on a bounded sample of the workload."""
     world, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
@@ -161,6 +199,8 @@ def run_reference(args):
         return 0
     import torch
     from paper_2603_11953_gb300 import workloads
+    if args.workload == BATCH_WORKLOAD:
+        return run_reference_batch(args)
     spec = workloads.CONFIGS[args.workload]
     rows = args.ref_rows
     A, _ = workloads.make_config(spec, device="cpu", m=rows)

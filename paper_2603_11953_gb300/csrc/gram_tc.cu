@@ -132,7 +132,7 @@ __device__ __forceinline__ int tc_exp_above(float mx) {
     return be == 0 ? -126 : be - 126;
 }
 
-// The deciders' verdict on one sub-chunk, read by the workers and the MMA issuer.
+// The deciders' decision on one sub-chunk, read by the workers and the MMA issuer.
 struct TcRecord {
     int newp;      // the sub-chunk opens a new period (the previous one is drained first)
     int regrid[2]; // per decider warp: some dsh of its columns is non-zero

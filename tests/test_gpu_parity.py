@@ -453,8 +453,9 @@ def test_solve_fp64_matches_double_double_oracle(m, n, kappa, logd):
 
 
 def test_solve_fp64_with_fp64_stage_and_statuses():
-    """higher = FP64 runs the FP64 n x n stage on the double-double Gram's high part (C11's
-    literal reading); rank deficiency and the plain Gram's missing double-double form are reported."""
+    """higher = FP64 runs the FP64 n x n stage on the double-double Gram's high part (the literal
+    reading of the stress configuration); rank deficiency and the plain Gram's missing double-double
+    form are reported."""
     m, n = 6000, 12
     A, _ = workloads.small_case(m, n, kappa_sigma=1e2, logd=1.0, seed=77, dtype=torch.float64, device="cuda")
     sig, V, U, st, _ = gpu_solve64(A, m, n, m, higher=T.TSVD_FP64, want_u=False)

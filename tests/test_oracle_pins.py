@@ -272,3 +272,29 @@ def test_dd_jacobi_reaches_double_double_accuracy():
     for k in range(3):
         got = sympy.Float(res["sigma_h"][k], 45) + sympy.Float(res["sigma_h_lo"][k], 45)
         assert float(abs(got - exact[k]) / exact[k]) < 1e-29
+
+
+def test_dd_jacobi_graded_relative_accuracy():
+    """The double-double Algorithm 1 on a strongly graded FP64 matrix (columns scaled over 12
+    decades, sigma_n / sigma_1 ~ 1e-6 after scaling): every sigma, the smallest included, to a
+    relative 1e-18 of the exact value (exact rational Gram, exact root isolation).  This is the
+    truth the FP64-working GPU tests compare against at kappa(B) up to 1e6."""
+    sympy = pytest.importorskip("sympy")
+    rng = np.random.default_rng(33)
+    m, n = 10, 4
+    B = rng.standard_normal((m, n))
+    B[:, 3] = B[:, 2] + 1e-6 * rng.standard_normal(m)  # nearly dependent pair: kappa(B) ~ 1e6
+    A = np.asfortranarray(B * np.array([1e6, 1e2, 1.0, 1e-6]))
+    S = exact_gram(A)
+    Ms = sympy.Matrix(n, n, lambda i, j: sympy.Rational(S[i][j].numerator, S[i][j].denominator))
+    lam = sympy.Symbol("lam")
+    roots = sympy.Poly(Ms.charpoly(lam).as_expr(), lam).real_roots()
+    exact = sorted([sympy.sqrt(r).evalf(50) for r in roots], reverse=True)
+    res = oracle.svd(A, higher=2)
+    assert res["status"] == 0
+    for k in range(n):
+        got = sympy.Float(res["sigma_h"][k], 50) + sympy.Float(res["sigma_h_lo"][k], 50)
+        assert float(abs(got - exact[k]) / exact[k]) < 1e-18, (k, float(abs(got - exact[k]) / exact[k]))
+    # the FP64 n x n stage on the same exact Gram loses ~u kappa(B)^2 on the smallest sigma
+    res1 = oracle.svd(A, higher=1)
+    assert float(abs(sympy.Float(res1["sigma_h"][n - 1], 50) - exact[n - 1]) / exact[n - 1]) > 1e-15
