@@ -518,7 +518,10 @@ def main():
     jac_flops = n ** 3 / 3.0 + sweeps * (n * (n - 1) // 2) * 8 * n
     # FP64 peak of the SMs the n x n stage uses: a 16-CTA cluster (8 for n <= 32), one CTA per
     # SM, at the measured 1.68 DFMA lanes per clock per SM (2 flops each)
-    eig_sms = 16 if n > 32 else 8 if n > 16 else 2 if n > 8 else 1
+    eig_sms = 1 if n > 64 else 16 if n > 32 else 8 if n > 16 else 2 if n > 8 else 1  # n > 64: one-CTA two-sided
+    if n > 64 and working == T.TSVD_FP32:
+        nb = (n + 31) // 32
+        gram_flops = nb * (nb - 1) // 2 * 16 * 2.0 * m * 64 * 64  # one 64-column pass per block pair
     sm_fp64 = 2 * FP64_DFMA_PER_CLK_SM * pk["sm_max_mhz"] * 1e6 / 1e9
     fp64_peak = eig_sms * sm_fp64
     launches = KERNELS_PER_STEP

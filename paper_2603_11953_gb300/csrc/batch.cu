@@ -177,7 +177,9 @@ __global__ void __launch_bounds__(BT) eig_batch_kernel(const BatchInst* __restri
                         // (|e| ~ 2^-24): orthogonal to FP64 precision.
                         double c, s, t;
                         if (in_range) {  // then rr > 0: g is a normal float, hf != 0
-                            const float df = bf - af, hf = 2.0f * to_f32(g);
+                            // b - a in FP64 first: for nearly equal norms (clustered sigma) the difference
+                            // of two FP32 roundings would be noise and the angle would not shrink g
+                            const float df = to_f32(b - a), hf = 2.0f * to_f32(g);
                             const float adf = fabsf(df), ahf = fabsf(hf);
                             const float sz = (df == 0.0f || (df > 0.0f) == (hf > 0.0f)) ? 1.0f : -1.0f;
                             float tf;

@@ -317,7 +317,9 @@ __global__ void __launch_bounds__(512) onesided_jacobi_kernel(OsParams prm) {
                     // s0 = t c0 in FP32.  The applied rotation (c0, s0) f is orthogonal to FP64
                     // precision: with e = c0^2 + s0^2 - 1 (exact in FP64, |e| ~ 2^-24),
                     // f = 1 - e/2 + 3e^2/8 = (1 + e)^(-1/2) + O(e^3).
-                    const float df = os_to_float(aqq) - os_to_float(app);
+                    // a_qq - a_pp in FP64 first: for nearly equal norms (clustered sigma) the difference of
+                    // two FP32 roundings would be noise and the angle would not shrink g
+                    const float df = os_to_float(aqq - app);
                     const float hf = 2.0f * os_to_float(g);
                     const float adf = fabsf(df), ahf = fabsf(hf);
                     const float sz = (df == 0.0f || (df > 0.0f) == (hf > 0.0f)) ? 1.0f : -1.0f;

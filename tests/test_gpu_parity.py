@@ -15,6 +15,7 @@ Tolerances (each derived in the design doc):
     is held to (n + 1) u_32.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -575,3 +576,81 @@ def test_full_size_sampled_fp64_stress():
     U_ref = oracle.rows_times(np.asfortranarray(A_rows), W, np.arange(len(rows)), 53)
     bound = (n + 1) * UH * (np.abs(A_rows) @ np.abs(W))
     assert np.all(np.abs(U[rows] - U_ref) <= bound)
+
+
+# ------------------------------------------------------------------ accuracy experiment grid (Sec. 4, Fig. 1)
+# (MODE of D, MODE of Sigma) of the 16 test-matrix types; the modes are the five diagonal
+# distributions (clustered at 1/kappa, clustered at 1, geometric, arithmetic, log-random).
+FIG1_TYPES = [(1, 2), (1, 3), (1, 4), (1, 5), (2, 3), (2, 4), (2, 5), (3, 2), (3, 4), (3, 5), (4, 2), (4, 3), (4, 5),
+              (5, 2), (5, 3), (5, 4)]
+
+
+def test_accuracy_sweep_fig1_grid():
+    """The accuracy experiment's grid: n = 64, m = 16 n, kappa(B) in {1e1, ..., 1e5}, kappa(D) in
+    {1, 1e2, 1e4, 1e6, 1e8}, the 16 matrix types: 400 matrices A = Q diag(sigma) W^T D (FP32), solved
+    in one batched call.  Reference: the oracle's double-double Algorithm 1 on the same FP32
+    matrices.  Bound per matrix: 2 u_32 (the cast of sigma) + 16 * 2^-50 kappa(C), C the
+    column-scaled exact Gram: the Gram's 2^-50 componentwise error carried through the scaled
+    eigenvalue perturbation bound (the u_h kappa(B)^2 term of the analysis)."""
+    from concurrent.futures import ThreadPoolExecutor
+    m, n = 1024, 64
+    gen = torch.Generator().manual_seed(20260311)
+    grid = []
+    for kB in (1e1, 1e2, 1e3, 1e4, 1e5):
+        for kD in (1.0, 1e2, 1e4, 1e6, 1e8):
+            for mD, mS in FIG1_TYPES:
+                sig = workloads.latm1_mode(mS, n, kB, gen)
+                d = workloads.latm1_mode(mD, n, kD, gen)
+                grid.append((kB, kD, mD, mS, workloads.make_matrix(m, n, sig, d, 1000 + len(grid), torch.float32)))
+    count = len(grid)
+    buf = torch.stack([A.T.contiguous() for *_, A in grid]).cuda()  # [count][n][m]: column-major blocks
+    As = [buf[k] for k in range(count)]
+    sig = [torch.zeros(n, device="cuda") for _ in range(count)]
+    Vs = [colmajor(n, n, torch.float32) for _ in range(count)]
+    info = torch.zeros(6 * count, dtype=torch.int32, device="cuda")
+    h = handle()
+    T.tsvd_batch_solve(h, count, As, [m] * count, [n] * count, [m] * count, T.TSVD_FP32, T.TSVD_FP64, sig, Vs,
+                       [n] * count, None, None, info)
+    torch.cuda.synchronize()
+    T.tsvd_destroy(h)
+    assert np.all(info.view(count, 6)[:, 0].cpu().numpy() == 0)
+
+    def ref(k):
+        A_np = np.asfortranarray(grid[k][4].cpu().numpy()[:m])
+        r = oracle.svd(A_np, higher=2)
+        G = oracle.gram(A_np)[0]
+        dd = np.sqrt(np.diag(G))
+        return r["status"], r["sigma_h"] + r["sigma_h_lo"], np.linalg.cond(G / np.outer(dd, dd))
+
+    with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+        refs = list(ex.map(ref, range(count)))
+    worst = {}
+    for k, (st, s_ref, kC) in enumerate(refs):
+        assert st == 0
+        got = sig[k].cpu().numpy().astype(np.float64)
+        rel = float(np.max(np.abs(got - s_ref) / s_ref))
+        assert rel <= 2.0 ** -23 + 16 * 2.0 ** -50 * kC, (grid[k][:4], rel, kC)
+        kB = grid[k][0]
+        worst[kB] = max(worst.get(kB, 0.0), rel)
+    print("fig1 grid: max relative sigma error per kappa(B):",
+          ", ".join(f"{kB:.0e}: {worst[kB]:.2e}" for kB in sorted(worst)))
+
+
+@pytest.mark.parametrize("mode_s,kD", [(1, 1.0), (2, 1.0), (2, 1e6), (1, 1e8)])
+def test_solve_clustered_spectra(mode_s, kD):
+    """Single solves (tensor-core Gram, cluster Jacobi) on spectra clustered at 1/kappa or at 1
+    (63 equal singular values): the Jacobi converges and sigma meets the grid test's bound."""
+    m, n, kB = 4096, 64, 1e3
+    gen = torch.Generator().manual_seed(77 + mode_s)
+    sig_t = workloads.latm1_mode(mode_s, n, kB, gen)
+    d = workloads.latm1_mode(3, n, kD, gen)
+    A = workloads.make_matrix(m, n, sig_t, d, 4242 + mode_s, torch.float32, device="cuda")
+    s, V, U, st, sweeps = gpu_solve(A, m, n, m, want_u=False)
+    assert st == T.TSVD_OK, (st, sweeps)
+    A_np = workloads.to_numpy_colmajor(A, m)
+    r = oracle.svd(A_np, higher=2)
+    G = oracle.gram(A_np)[0]
+    dd = np.sqrt(np.diag(G))
+    kC = np.linalg.cond(G / np.outer(dd, dd))
+    s_ref = r["sigma_h"] + r["sigma_h_lo"]
+    assert np.max(np.abs(s - s_ref) / s_ref) <= 2.0 ** -23 + 16 * 2.0 ** -50 * kC
