@@ -69,7 +69,8 @@ typedef struct {
     int slices;            /* Ozaki digit count k (default 7: 55 bits per entry) */
     int chunk_rows;        /* rows per exact INT chunk (default 128; must be 128) */
     int split_k;           /* CTAs over m for the Gram (default: from m and the SM count) */
-    double jacobi_tol;     /* skip test |m_pq| <= tol*sqrt(m_pp m_qq) (default n * 2^-53) */
+    double jacobi_tol;     /* skip test |m_pq| <= tol*sqrt(m_pp m_qq) (default n * 2^-53; n * 2^-104
+                              for the double-double n x n stage of FP64 working precision) */
     int max_sweeps;        /* Jacobi sweep limit (default 40) */
     int eig_variant;       /* 0 = default (2 for n <= 64, else 1); 1 = two-sided
                               Jacobi on M_h (Sec. 2.1); 2 = pivoted Cholesky of M_h
@@ -77,8 +78,10 @@ typedef struct {
     int autotune;          /* reserved (0) */
     long long timeout_cycles; /* reserved: limit for device spin-waits (0 = default) */
     int gram_variant;      /* 0 = Ozaki-BF16 Gram on tcgen05/TMEM (mma.sync when the
-                              input cannot be TMA-loaded), 1 = plain FP64 Gram,
-                              2 = Ozaki-BF16 Gram on mma.sync (comparison) */
+                              input cannot be TMA-loaded; FP64 input through exact
+                              23-bit pieces), 1 = plain FP64 Gram (the comparison
+                              form; no double-double), 2 = Ozaki-BF16 Gram on
+                              mma.sync (comparison; FP32 input only) */
     int timing;            /* k >= 1: record per-stage CUDA events of the last k calls
                               (k <= TSVD_MAX_TIMED; tsvd_last_stage_ms, tsvd_stage_ms_mean) */
     int u_variant;         /* 0 = U = A W on tcgen05 in a 3-term TF32 split when the input
