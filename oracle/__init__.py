@@ -15,6 +15,7 @@ Functions (all matrices column-major, numpy ``order='F'``):
   svd(A, higher)                 -> dict with sigma_h, V_h, sigma_w, V_w, W_w, status
   rows_times(A, W, rows, p)      -> RN_p of exact A[rows] @ W        (Alg. 1 l.6)
   rows_explicit_u(A, V_hi, V_lo, sig_hi, sig_lo, rows) -> exact A V_h / sigma_h (DD)
+  round_dd(hi, lo, p)            -> RN_p(hi + lo) by one exact rounding (Alg. 1 l.4-5)
 """
 from __future__ import annotations
 
@@ -65,9 +66,10 @@ def _load():
             lib.oracle_jacobi_dd.argtypes = [P, P, I, D, I, P, P, P, P, P]
             lib.oracle_sort_sign.argtypes = [I, P, P, P, P, P, P]
             lib.oracle_svd.argtypes = [P, I64, I64, I64, I, I, D, I, P, P, P, P, P, P, P, P]
+            lib.oracle_round_dd.argtypes = [P, P, I64, I, P]
             for f in (lib.oracle_gram, lib.oracle_rows_times, lib.oracle_rows_explicit_u,
                       lib.oracle_jacobi_fp64, lib.oracle_jacobi_dd, lib.oracle_sort_sign,
-                      lib.oracle_svd):
+                      lib.oracle_svd, lib.oracle_round_dd):
                 f.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -134,6 +136,18 @@ def rows_explicit_u(A, V_hi, V_lo, sig_hi, sig_lo, rows):
     if st != OK:
         raise ValueError(f"oracle_rows_explicit_u status {st}")
     return oh, ol
+
+
+def round_dd(hi, lo, p):
+    """RN-even of the exact values hi + lo to p significant bits (p <= 53), one rounding."""
+    lib = _load()
+    hi = np.ascontiguousarray(np.asarray(hi, dtype=np.float64)).ravel()
+    lo = None if lo is None else np.ascontiguousarray(np.asarray(lo, dtype=np.float64)).ravel()
+    out = np.zeros_like(hi)
+    st = lib.oracle_round_dd(_ptr(hi), _ptr(lo), hi.size, int(p), _ptr(out))
+    if st != OK:
+        raise ValueError(f"oracle_round_dd status {st}")
+    return out
 
 
 def jacobi_fp64(M, tol=U_H_FP64, max_sweeps=100):

@@ -18,11 +18,12 @@
  *                     eigensolver, Remark 1), row-cyclic order, Rutishauser's
  *                     rotation formulas, in FP64 or in double-double.
  *   Alg. 1 lines 4-5  sigma = sqrt(lambda) sorted descending; V permuted and
- *                     sign-normalised; both rounded (RN-even) to working.
+ *                     sign-normalised; both rounded (RN-even) to working,
+ *                     once, from the exact value of the (hi, lo) pair.
  *   Alg. 1 line 6     U = A (V Sigma^{-1}): W = RN_w(V_w / sigma_w) and every
  *                     entry of A*W summed exactly then rounded once.
  *
- * Readings of points the paper leaves open (listed in the design doc):
+ * Readings of points the paper leaves open:
  *   - the Jacobi skip test is |m_pq| <= tol * sqrt(m_pp * m_qq) (scaled by the
  *     column norms D of A = B D, Section 3); zeta = 0 takes sgn = +1;
  *   - sweeps stop after a sweep with no rotation; failure after max_sweeps;
@@ -170,6 +171,25 @@ static double sa_round(superacc* s, int p) {
     if (e2 < -1000 || e2 > 960) abort();
     double v = ldexp((double)mant, (int)e2);
     return negative ? -v : v;
+}
+
+/* RN-even of the exact value hi + lo to p significant bits (p <= 53), by one
+ * rounding of the exact sum (no intermediate rounding to FP64).  This is the
+ * cast of Alg. 1 lines 4-5 from the higher precision to the working one. */
+static double round_dd_exact(superacc* s, double hi, double lo, int p) {
+    sa_clear(s);
+    sa_add_double(s, hi);
+    sa_add_double(s, lo);
+    return sa_round(s, p);
+}
+
+int oracle_round_dd(const double* hi, const double* lo, int64_t count, int p, double* out) {
+    if (!hi || !out || count < 0 || p < 2 || p > 53) return ORC_BAD_ARG;
+    superacc* s = (superacc*)malloc(sizeof(superacc));
+    if (!s) return ORC_BAD_ARG;
+    for (int64_t k = 0; k < count; ++k) out[k] = round_dd_exact(s, hi[k], lo ? lo[k] : 0.0, p);
+    free(s);
+    return ORC_OK;
 }
 
 /* ------------------------------------------------------------------------- */
@@ -555,16 +575,22 @@ int oracle_svd(const void* A, int64_t m, int64_t n, int64_t lda, int working, in
     if (st == ORC_OK || st == ORC_NO_CONVERGENCE) {
         int st2 = oracle_sort_sign((int)n, lh, ll, Vh, Vl, sig_hi, sig_lo);
         if (st == ORC_OK) st = st2;
-        for (int64_t i = 0; i < n; ++i) {
-            double sh = sig_hi[i] + (sig_lo ? sig_lo[i] : 0.0);
-            sig_w[i] = working == 0 ? (double)(float)sh : sh;
-        }
+        /* Alg. 1 lines 4-5: one RN-even rounding of the exact (hi, lo) value to the working
+         * precision's p bits */
+        const int p = working == 0 ? 24 : 53;
+        superacc* sa = (superacc*)malloc(sizeof(superacc));
+        if (!sa) return ORC_BAD_ARG;
+        for (int64_t i = 0; i < n; ++i) sig_w[i] = round_dd_exact(sa, sig_hi[i], sig_lo ? sig_lo[i] : 0.0, p);
         for (size_t k = 0; k < nn; ++k) {
-            double v = Vh[k] + Vl[k];
-            V_w[k] = working == 0 ? (double)(float)v : v;
+            V_w[k] = round_dd_exact(sa, Vh[k], Vl[k], p);
             if (V_hi) V_hi[k] = Vh[k];
             if (V_lo) V_lo[k] = Vl[k];
         }
+        free(sa);
+        /* W = RN_w(V_w / sigma_w), the IEEE division in working precision.  For FP32 the
+         * quotient is formed in FP64 and rounded to FP32: with 53 >= 2*24 + 2 bits that double
+         * rounding equals the correctly rounded FP32 quotient (the classical result on
+         * innocuous double rounding for +, -, *, / and sqrt). */
         for (int64_t j = 0; j < n; ++j)
             for (int64_t i = 0; i < n; ++i) {
                 double q = V_w[i + j * n] / sig_w[j];

@@ -1,6 +1,6 @@
 """GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
 
-Tolerances (each derived in the design doc):
+Tolerances:
   * Gram (Alg. 1 l.2, eq. (ATA) with eps_M = 2^-50): |G - S| <= 2^-50 (|A|^T|A|)
     componentwise, S the exact sum; plus the deterministic any-size bound
     |G - S|_ij <= m * 2^-50 * 2^(E_i + E_j) with 2^E_j <= 2 max_r |a_rj|.

@@ -147,6 +147,72 @@ def test_explicit_u_orthonormal_columns():
     np.testing.assert_array_equal(np.abs(uh), np.abs(Q))
 
 
+def test_explicit_u_is_exact_rational_quotient():
+    """Alg. 1 line 6 / eq. (AV-0) with the higher-precision factors: u_rj = (sum_c a_rc v_cj) / sigma_j
+    with v = V_hi + V_lo and sigma = sig_hi + sig_lo, against exact rationals.  V is a full,
+    non-symmetric matrix (a transposed index changes the answer), V_lo and sig_lo are non-zero (a
+    dropped low part changes it by ~2^-60 relative, far above the 2^-98 tolerance) and sigma is not
+    a power of two."""
+    rng = np.random.default_rng(17)
+    m, n = 9, 5
+    A = np.asfortranarray(rng.standard_normal((m, n)).astype(np.float32))
+    V_hi = np.asfortranarray(rng.standard_normal((n, n)))
+    V_lo = np.asfortranarray(V_hi * rng.uniform(0.25, 0.5, (n, n)) * 2.0 ** -58)
+    sig_hi = rng.uniform(0.3, 3.0, n)
+    sig_lo = sig_hi * rng.uniform(-0.5, 0.5, n) * 2.0 ** -56
+    rows = np.array([0, 4, 8, 2])
+    oh, ol = oracle.rows_explicit_u(A, V_hi, V_lo, sig_hi, sig_lo, rows)
+    for k, r in enumerate(rows):
+        for j in range(n):
+            dot = sum(Fraction(float(A[r, c])) * (Fraction(V_hi[c, j]) + Fraction(V_lo[c, j])) for c in range(n))
+            u = dot / (Fraction(sig_hi[j]) + Fraction(sig_lo[j]))
+            got = Fraction(oh[k, j]) + Fraction(ol[k, j])
+            assert abs(got - u) <= abs(u) * Fraction(1, 2 ** 98), (r, j)
+            assert oh[k, j] == round_frac(u, 53) or abs(Fraction(oh[k, j]) - u) <= abs(u) * Fraction(1, 2 ** 52)
+    # the low parts matter at this tolerance: leaving them out moves the result
+    oh0, ol0 = oracle.rows_explicit_u(A, V_hi, None, sig_hi, None, rows)
+    assert not (np.array_equal(oh0, oh) and np.array_equal(ol0, ol))
+
+
+def test_round_dd_single_rounding():
+    """Alg. 1 lines 4-5 (cast to the working precision): RN-even of the exact hi + lo, one rounding.
+    The FP32 midpoints are the cases a double rounding (DD -> FP64 -> FP32) gets wrong."""
+    one = 1.0
+    mid = one + 2.0 ** -24            # exactly halfway between 1 and 1 + 2^-23 (FP32)
+    his = np.array([mid, mid, mid, -mid, 3.0 + 2.0 ** -22, 0.1, 1e-3, 2.0 ** -30 * (1 + 2.0 ** -24)])
+    los = np.array([2.0 ** -80, -2.0 ** -80, 0.0, -2.0 ** -80, 2.0 ** -75, 1e-20, -3e-22, 2.0 ** -100])
+    out24 = oracle.round_dd(his, los, 24)
+    out53 = oracle.round_dd(his, los, 53)
+    for h, l, o24, o53 in zip(his, los, out24, out53):
+        x = Fraction(h) + Fraction(l)
+        assert o24 == round_frac(x, 24), (h, l)
+        assert o53 == round_frac(x, 53), (h, l)
+    assert out24[0] == 1.0 + 2.0 ** -23 and out24[1] == 1.0 and out24[2] == 1.0  # above, below, tie to even
+    assert out24[3] == -(1.0 + 2.0 ** -23)
+    assert np.float64(np.float32(mid)) == 1.0  # what a cast through FP64 alone would give for case 0
+
+
+@pytest.mark.parametrize("dtype,higher", [(np.float32, 1), (np.float32, 2), (np.float64, 2), (np.float64, 1)])
+def test_svd_working_precision_casts(dtype, higher):
+    """oracle_svd's sigma_w, V_w and W_w are the single RN-even roundings (to A's precision) of the
+    exact higher-precision sigma_h = sig_hi + sig_lo, V_h = V_hi + V_lo, and of V_w / sigma_w."""
+    A = wide_random(30, 4, 23, dtype, erange=4)
+    res = oracle.svd(A, higher=higher)
+    assert res["status"] == 0
+    p = 24 if dtype == np.float32 else 53
+    n = A.shape[1]
+    for j in range(n):
+        s = Fraction(res["sigma_h"][j]) + Fraction(res["sigma_h_lo"][j])
+        assert res["sigma_w"][j] == round_frac(s, p), j
+        for i in range(n):
+            v = Fraction(res["V_h"][i, j]) + Fraction(res["V_h_lo"][i, j])
+            assert res["V_w"][i, j] == round_frac(v, p), (i, j)
+            q = Fraction(res["V_w"][i, j]) / Fraction(res["sigma_w"][j])
+            assert res["W_w"][i, j] == round_frac(q, p), (i, j)
+    # W is V_w / sigma_w column by column, not row by row (a transposed sigma index fails here)
+    assert not np.allclose(res["W_w"], res["V_w"] / res["sigma_w"][:, None])
+
+
 # ---------------------------------------------------------------- Jacobi (Alg. 1 line 3)
 def test_jacobi_n1_and_2x2_closed_form():
     lam, V, sw, st = oracle.jacobi_fp64(np.array([[7.25]]))
