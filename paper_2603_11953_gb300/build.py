@@ -1,7 +1,8 @@
 """Build libtsvd.so in-tree with nvcc for sm_103a (GB300).
 
 Each .cu file is compiled to an object in parallel, then linked into
-paper_2603_11953_gb300/_build/libtsvd.so (static CUDA runtime).  Run as
+paper_2603_11953_gb300/_build/libtsvd.so (static CUDA runtime), and the peak
+probe (peak_probe.cu) into _build/libtsvd_probe.so.  Run as
 ``python -m paper_2603_11953_gb300.build``.
 """
 from __future__ import annotations
@@ -15,6 +16,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libtsvd.so")
+PROBE_LIB = os.path.join(OUT, "libtsvd_probe.so")
+PROBE_SOURCE = "peak_probe.cu"
 SOURCES = ["tsvd_api.cu", "gram_ozaki.cu", "jacobi.cu", "compute_u.cu", "compute_u_tc.cu", "gram_static.cu", "eig_onesided.cu", "tma_util.cu", "gram_tc.cu", "gram_fp64.cu", "eig_dd.cu", "batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
@@ -37,18 +40,19 @@ def build(force: bool = False, extra: list[str] | None = None) -> str:
     os.makedirs(OUT, exist_ok=True)
     extra = extra or []
     srcs = [os.path.join(CSRC, s) for s in os.listdir(CSRC)] + [os.path.join(HERE, "..", "include", "tsvd.h")]
-    if not force and os.path.exists(LIB):
+    if not force and os.path.exists(LIB) and os.path.exists(PROBE_LIB):
         newest = max(os.path.getmtime(s) for s in srcs)
-        if os.path.getmtime(LIB) >= newest:
+        if min(os.path.getmtime(LIB), os.path.getmtime(PROBE_LIB)) >= newest:
             return LIB
-    with concurrent.futures.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra), SOURCES))
-    tmp = LIB + f".{os.getpid()}.tmp"
-    cmd = [NVCC] + ARCH + ["-shared", "-o", tmp] + objs
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    with concurrent.futures.ThreadPoolExecutor(max_workers=len(SOURCES) + 1) as ex:
+        objs = list(ex.map(lambda s: _compile(s, extra), SOURCES + [PROBE_SOURCE]))
+    for lib, parts in ((LIB, objs[:-1]), (PROBE_LIB, objs[-1:])):
+        tmp = lib + f".{os.getpid()}.tmp"
+        cmd = [NVCC] + ARCH + ["-shared", "-o", tmp] + parts
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, lib)
     return LIB
 
 
