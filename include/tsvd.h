@@ -6,7 +6,11 @@
  * tall-and-skinny A (m >= n), with working precision u and higher precision
  * u_h:
  *   1. M_h = A^T A formed in the higher precision          (Alg. 1 lines 1-2)
- *   2. M_h = V_h Sigma_h^2 V_h^T by the two-sided Jacobi   (Alg. 1 line 3, Sec. 2.1)
+ *   2. M_h = V_h Sigma_h^2 V_h^T in the higher precision   (Alg. 1 line 3): by
+ *      default (n <= 64) a pivoted Cholesky M_h = R^T R followed by a
+ *      one-sided Jacobi SVD of R^T (the factor-then-SVD structure of Alg. 2,
+ *      all in the higher precision); two-sided Jacobi on M_h (Sec. 2.1) for
+ *      n > 64 or on request (tsvd_opts.eig_variant)
  *   3. Sigma, V rounded to working precision               (Alg. 1 lines 4-5)
  *   4. U = A (V Sigma^{-1}) in working precision           (Alg. 1 line 6)
  *
@@ -54,7 +58,8 @@ typedef enum { TSVD_FP32 = 0, TSVD_FP64 = 1, TSVD_DD = 2 } tsvd_prec;
 typedef enum {
     TSVD_OK = 0,
     TSVD_ERR_ARG = 1,            /* bad size, null pointer, bad tag */
-    TSVD_ERR_ALIGN = 2,          /* alignment the chosen path cannot handle */
+    TSVD_ERR_ALIGN = 2,          /* reserved: not returned (every path accepts any alignment;
+                                    unaligned input takes the CUDA-core kernels) */
     TSVD_ERR_NONFINITE = 3,      /* A contains Inf or NaN */
     TSVD_ERR_NOT_FULL_RANK = 4,  /* some eigenvalue of M_h is <= 0 */
     TSVD_ERR_NO_CONVERGENCE = 5, /* Jacobi hit max_sweeps */
@@ -76,7 +81,12 @@ typedef struct {
                               Jacobi on M_h (Sec. 2.1); 2 = pivoted Cholesky of M_h
                               + one-sided Jacobi on R^T, both in FP64 (n <= 64) */
     int autotune;          /* reserved (0) */
-    long long timeout_cycles; /* reserved: limit for device spin-waits (0 = default) */
+    long long timeout_cycles; /* limit, in GPU clock cycles, of each steady-state mbarrier
+                                 wait of the tcgen05 Gram kernel and of the cluster Jacobi
+                                 (0 = default, 2^31, about a second); a wait that runs out
+                                 makes the call report TSVD_ERR_TIMEOUT (outputs undefined).
+                                 Waits for copies and MMAs already in flight before a kernel
+                                 exits keep the default. */
     int gram_variant;      /* 0 = Ozaki-BF16 Gram on tcgen05/TMEM (mma.sync when the
                               input cannot be TMA-loaded; FP64 input through exact
                               23-bit pieces), 1 = plain FP64 Gram (the comparison
@@ -94,7 +104,13 @@ typedef struct {
     int status;       /* tsvd_status of the numeric part */
     int sweeps;       /* Jacobi sweeps performed */
     double off_norm;  /* max_{p<q} |m_pq| / sqrt(m_pp m_qq) at exit */
-    double kappa_B;   /* reserved (0): kappa(B) is reported by the tests */
+    double kappa_B;   /* estimate of kappa(B) = (lambda_max / lambda_min)^(1/2) of the
+                         column-scaled Gram C = D^-1 M_h D^-1 (A = B D, Sec. 3; the
+                         kappa(B) of Theorem 1), from FP32 power and inverse
+                         iterations on the pivoted Cholesky factor of C (an
+                         under-estimate, typically within a few per cent); +Inf when
+                         M_h is not positive definite; 0 where not computed (the
+                         two-sided n x n stage, the double-double stage, batches) */
 } tsvd_info;
 
 /* Create a handle bound to `device` and `stream` (a cudaStream_t; NULL = the
@@ -205,21 +221,30 @@ TSVD_API tsvd_status tsvd_stage_ms_mean(tsvd_handle h, int last, float ms[4]);
  * block live in one fixed device array of TSVD_GRAM_STATIC_SCRATCH_BYTES
  * that every GPU which loads this part of the library holds until exit.
  *   A, m, n, lda, working, higher, G, ldg: as for tsvd_gram (working must be
- *     TSVD_FP32, n <= 64); results are those of tsvd_gram with default
- *     options.  info: NULL or a device / pinned-host tsvd_info.  stream: a
- *     cudaStream_t (NULL = the legacy default stream); the work runs on the
- *     calling thread's current device.
+ *     TSVD_FP32, n <= 64).  Input TMA can load (16-byte aligned A, lda a
+ *     multiple of 4) runs the tcgen05 Gram of tsvd_gram with the same split-K
+ *     plan: bitwise the result of tsvd_gram with default options.  Other
+ *     input runs the mma.sync Ozaki Gram (tsvd_gram's kernel for it), whose
+ *     split-K may be capped by the array: the same error bound, the bits may
+ *     differ.
+ *   info: NULL or a device / pinned-host tsvd_info.  There is no handle and
+ *     so no tsvd_sync_status: info is the only place a data-dependent outcome
+ *     (TSVD_ERR_NONFINITE for Inf or NaN in A; G is then undefined) is
+ *     reported; with info NULL it is not visible.
+ *   stream: a cudaStream_t (NULL = the legacy default stream); the work runs
+ *     on the calling thread's current device.
  *   The first call on each device looks up the array's device address
- *   (cudaGetSymbolAddress, with that device current) and caches it; make
- *   that first call before any stream capture.
+ *   (cudaGetSymbolAddress, with that device current) and caches it with the
+ *   device's current context (a new context, e.g. after cudaDeviceReset, is
+ *   looked up again); make that first call before any stream capture.
  *   Every call reuses the same array and leaves its contents behind (the
  *   status block is cleared at the start of each call); calls that overlap
  *   on the GPU, e.g. on two streams at once, race on it.
  * Errors: TSVD_ERR_ARG as tsvd_gram; TSVD_ERR_UNSUPPORTED when the partials
  * would not fit the array, i.e. m > 32768 * floor((16 MiB - 512) /
- * (16 NP^2 + 4 NP)) with NP = n rounded up to 16, 32, 48 or 64 (for n = 64:
- * m > 8,323,072), or for FP64 working / n > 64; TSVD_ERR_CUDA if the
- * runtime fails. */
+ * (16 NP^2 + 4 NP)) with NP = 64 for TMA-loadable input and NP = n rounded
+ * up to 16, 32, 48 or 64 otherwise (m > 8,323,072 at NP = 64), or for FP64
+ * working / n > 64; TSVD_ERR_CUDA if the runtime fails. */
 TSVD_API tsvd_status tsvd_gram_static(const void* A, int64_t m, int64_t n, int64_t lda,
                                       tsvd_prec working, tsvd_prec higher, double* G, int64_t ldg,
                                       tsvd_info* info, void* stream);

@@ -16,21 +16,37 @@
 //      (Rutishauser's formulas), so this is two-sided Jacobi on X^T X
 //      without forming it and without accumulating V.
 //   3. The pairs are scheduled by the round-robin ("circle") tournament over
-//      a thread-block cluster: each CTA owns P pair slots (one warp per
-//      pair); after each step one column moves to each neighbouring CTA
-//      through distributed shared memory, signalled on the neighbour's
-//      mbarrier (no cluster-wide barrier within a sweep).
+//      a thread-block cluster.
+//
+// GB300 sets the shape of step 3.  Its FP64 unit issues one warp
+// instruction per ~64 cycles per SM sub-partition whatever the number of
+// active lanes, with a dependent latency of ~64 cycles; FP32 is ~60x faster.
+// So (i) the pairs are spread over the 16 SMs of a (non-portable) cluster,
+// two per SM, and each pair over two warps on different sub-partitions (32
+// rows each): a warp issues 1 FP64 multiply for its dot product, 5 + 1 adds
+// to reduce it, ~8 scalar operations for the rotation and the norms, and 4
+// for its half of the rotation; (ii) the angle, the scaled test and the
+// conversions run on the FP32 and integer pipes; (iii) a column that leaves
+// an SM is stored straight from registers into the neighbour's shared
+// memory (st.shared::cluster), into a ring of receive buffers that
+// the tournament maps in place, and signalled on the neighbour's mbarrier
+// (release / acquire at cluster scope): no copy, no cluster-wide barrier
+// within a sweep.
 //
 // The rotation angle and (c0, s0) are computed in FP32 while the applied
 // rotation is made orthogonal to FP64 precision by one FP64 correction
 // factor: an inexact angle only leaves a residual g * O(2^-24) on a pair,
 // which later sweeps remove, whereas a non-orthogonal rotation would change
-// the singular values.  On GB300 a dependent FP64 operation costs about 60
-// cycles and an FP64 reciprocal square root about 350, so every division and
-// square root goes to the FP32 units.  Squared norms are updated within a sweep by the exact quadratic
-// form of the rotation, recomputed at the start of every sweep and whenever
-// a norm drops below 1/16 of its previous value; the stopping test of the
-// final, rotation-free sweep therefore uses exact norms.
+// the singular values.  Squared norms are updated within a sweep by the exact
+// quadratic form of the rotation, recomputed at the start of every sweep and
+// whenever a norm drops below 1/16 of its previous value; the stopping test
+// of the final, rotation-free sweep therefore uses exact norms.
+//
+// kappa_kernel estimates kappa(B) = kappa(C)^(1/2), C = D^-1 M_h D^-1 (the
+// column-scaled Gram of A = B D), from the Cholesky factor: the rows of X
+// scaled by 1/d form a Cholesky factor L of P C P^T, and FP32 power and
+// inverse iterations on L L^T give its extreme eigenvalues.  It runs on a
+// second stream beside the Jacobi.
 #include <climits>
 
 #include <cooperative_groups.h>
@@ -44,85 +60,110 @@ namespace {
 
 // ---------------------------------------------------------------- pivoted Cholesky
 // One CTA.  M (n x n, ldm) -> X = R^T (n x n, ld n, lower triangular, rows in pivot
-// order) and perm (pivot position -> original index).  Nothing is swapped in memory:
-// the trailing matrix stays in the original index order and the pivot order lives
-// in a permutation, so each step needs two barriers.  Every warp finds the pivot
-// itself (the largest remaining diagonal, lowest position on ties).
+// order) and perm (pivot position -> original index).  The trailing Schur complement
+// is kept by original index and only its lower triangle (row index >= column index,
+// original order) is stored and updated: half the FP64 work of a full update, and no
+// rows or columns are swapped.  The remaining indices are a bit mask; their ascending
+// list turns the triangle into contiguous work for the warps.
+__device__ __forceinline__ double chol_S(const double* sa, int n, int x, int y) {
+    return x >= y ? sa[x + (size_t)y * n] : sa[y + (size_t)x * n];
+}
+
 __global__ void __launch_bounds__(256)
     chol_piv_kernel(const double* __restrict__ M, int n, int64_t ldm, double* __restrict__ X,
                     int* __restrict__ perm_out, DevInfo* info) {
-    extern __shared__ double sa[];  // [n][n] trailing Schur complement (original indices), then R rows
+    extern __shared__ double sa[];    // [n][n] Schur complement, lower triangle by original index
     double* Rr = sa + (size_t)n * n;  // [n][n]: row k of R by original column index
-    __shared__ int perm[2][64];
+    __shared__ int s_list[64];        // remaining original indices, ascending
+    __shared__ int s_perm[64];
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
     for (int idx = tid; idx < n * n; idx += nt) {
         const int r = idx % n, c = idx / n;
-        sa[idx] = M[r + (size_t)c * ldm];
+        sa[idx] = r >= c ? M[r + (size_t)c * ldm] : 0.0;
         Rr[idx] = 0.0;
     }
-    if (tid < 64) perm[0][tid] = tid;
     __syncthreads();
+    unsigned long long rem = n == 64 ? ~0ull : ((1ull << n) - 1ull);
     bool deficient = false;
     int kend = n;
     for (int k = 0; k < n; ++k) {
-        const int* pc = perm[k & 1];
-        int* pn = perm[(k & 1) ^ 1];
-        // pivot: largest remaining diagonal.  The bit patterns of non-negative doubles order
-        // like the values; every negative value (rank deficiency) sorts below them.
+        // pivot: the largest remaining diagonal, lowest original index on ties.  Every warp
+        // finds it itself.  Non-negative doubles order like their bit patterns; every
+        // negative value (rank deficiency) sorts below them.
         long long best = LLONG_MIN;
-        int bq = k;
-        for (int q = k + lane; q < n; q += 32) {
-            const int o = pc[q];
+        int bo = n;
+        for (int o = lane; o < n; o += 32) {
+            if (!((rem >> o) & 1ull)) continue;
             const long long dd = __double_as_longlong(sa[o + (size_t)o * n]);
             const long long key = dd < 0 ? LLONG_MIN + 1 : dd;
-            if (key > best) { best = key; bq = q; }
+            if (key > best || (key == best && o < bo)) { best = key; bo = o; }
         }
         for (int off = 16; off > 0; off >>= 1) {
             const long long ob = __shfl_xor_sync(0xffffffffu, best, off);
-            const int oq = __shfl_xor_sync(0xffffffffu, bq, off);
-            if (ob > best || (ob == best && oq < bq)) { best = ob; bq = oq; }
+            const int oo = __shfl_xor_sync(0xffffffffu, bo, off);
+            if (ob > best || (ob == best && oo < bo)) { best = ob; bo = oo; }
         }
-        const int ok = pc[bq];
+        const int ok = bo;
         const double d = sa[ok + (size_t)ok * n];
         if (!(d > 0.0)) { deficient = true; kend = k; break; }
-        // the permutation with positions k and bq exchanged
-        if (tid < n) pn[tid] = (tid == k) ? ok : (tid == bq) ? pc[k] : pc[tid];
+        const unsigned long long rn = rem & ~(1ull << ok);
         const double rinv = rsqrt(d);  // 1 / r_kk
-        // row k of R: R[k][o] = S[ok][o] / r_kk over the remaining original indices o
-        for (int t = tid; t < n - k; t += nt) {
-            const int q = k + t;
-            const int o = (q == k) ? ok : (q == bq) ? pc[k] : pc[q];
-            Rr[(size_t)k * n + o] = (q == k) ? d * rinv : sa[ok + (size_t)o * n] * rinv;
+        // row k of R over the remaining indices, and their ascending list
+        for (int o = tid; o < n; o += nt) {
+            if (o == ok) Rr[(size_t)k * n + o] = d * rinv;
+            else if ((rn >> o) & 1ull) Rr[(size_t)k * n + o] = chol_S(sa, n, o, ok) * rinv;
+            if ((rn >> o) & 1ull) s_list[__popcll(rn & ((1ull << o) - 1ull))] = o;
         }
+        if (tid == 0) s_perm[k] = ok;
         __syncthreads();
-        // trailing update S[a][b] -= R[k][a] R[k][b] over the remaining positions > k
-        const int rem = n - k - 1;
+        // trailing update S(a, b) -= R[k][a] R[k][b] over the remaining lower triangle:
+        // t enumerates pairs (i', j'), j' <= i', row by row; i = rc - 1 - j' and j = rc - 1 - i'
+        // give consecutive i (rows) for consecutive t, so a warp's accesses are contiguous
+        const int rc = __popcll(rn);
+        const int T = rc * (rc + 1) / 2;
         const double* rk = Rr + (size_t)k * n;
-        for (int idx = tid; idx < rem * rem; idx += nt) {
-            const int oa = pn[k + 1 + idx % rem], ob = pn[k + 1 + idx / rem];
-            sa[oa + (size_t)ob * n] -= rk[oa] * rk[ob];
+        for (int t = tid; t < T; t += nt) {
+            int ip = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+            while (ip * (ip + 1) / 2 > t) --ip;
+            while ((ip + 1) * (ip + 2) / 2 <= t) ++ip;
+            const int jp = t - ip * (ip + 1) / 2;
+            const int a = s_list[rc - 1 - jp], b = s_list[rc - 1 - ip];  // a >= b
+            sa[a + (size_t)b * n] -= rk[a] * rk[b];
         }
+        rem = rn;
         __syncthreads();
     }
-    // X = R^T with rows in pivot order: X[pos][c] = R[c][perm[pos]] for pos >= c
-    const int* pf = perm[kend & 1];
+    // X = R^T with rows in pivot order: X[pos][c] = R[c][perm[pos]] for pos >= c.  Past a
+    // rank deficiency the remaining positions take the remaining indices in ascending order.
+    if (tid == 0) {
+        int pos = kend;
+        for (int o = 0; o < n; ++o)
+            if ((rem >> o) & 1ull) s_perm[pos++] = o;
+    }
+    __syncthreads();
     for (int idx = tid; idx < n * n; idx += nt) {
         const int pos = idx % n, c = idx / n;
-        X[idx] = (pos >= c && c < kend) ? Rr[(size_t)c * n + pf[pos]] : 0.0;
+        X[idx] = (pos >= c && c < kend) ? Rr[(size_t)c * n + s_perm[pos]] : 0.0;
     }
-    for (int i = tid; i < n; i += nt) perm_out[i] = pf[i];
+    for (int i = tid; i < n; i += nt) perm_out[i] = s_perm[i];
     if (tid == 0 && deficient) atomicOr(&info->flags, FLAG_NOT_FULL_RANK);
 }
 
 // ---------------------------------------------------------------- cluster one-sided Jacobi
+constexpr int OS_LD = 66;    // a column: 64 rows (zero padded), squared norm, column id (integer bits)
+constexpr int OS_MAXRING = 18;  // receive buffers per side: 2P + 2 for P <= 8
+constexpr int OS_MAXP = 8;   // pairs per CTA
+
 struct OsParams {
     const double* X;  // n x n (ld n): columns to orthogonalise (X = R^T)
     const int* perm;
     int n;            // true size
     int np;           // padded column count (multiple of 4 * clusterSize)
-    int P;            // pairs per CTA
+    int P;            // pairs per CTA (2 <= P <= 8)
+    int H;            // warps per pair: 2 (rows 0..31 and 32..63) for n > 32, else 1
     double tol;
     int max_sweeps;
+    long long wait_limit;
     double* lam;      // [n]  ||x_j||^2
     double* V;        // n x n, column j = P^T x_j / ||x_j||
     DevInfo* info;
@@ -160,25 +201,16 @@ __device__ __forceinline__ uint32_t os_mapa(const void* local, int rank) {
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(raddr) : "r"(os_smem(local)), "r"(rank));
     return raddr;
 }
-// this CTA expects `bytes` more on its own mbarrier (and counts as its one arrival)
-__device__ __forceinline__ void os_arm(uint64_t* bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(os_smem(bar)), "r"(bytes) : "memory");
+// store into another CTA's shared memory (address from os_mapa)
+__device__ __forceinline__ void os_st_remote(uint32_t raddr, double v) {
+    asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(raddr), "d"(v) : "memory");
 }
-// bulk copy of `bytes` from this CTA's shared memory into CTA `rank`'s, completing the
-// transaction on that CTA's mbarrier (no fence on the sender's critical path)
-__device__ __forceinline__ void os_bulk_to(const void* src, const void* dst_local_equiv, const uint64_t* bar_local_equiv,
-                                           int rank, unsigned bytes) {
-    const uint32_t dst = os_mapa(dst_local_equiv, rank), bar = os_mapa(bar_local_equiv, rank);
-    asm volatile(
-        "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-        "r"(os_smem(src)), "r"(bytes), "r"(bar)
-        : "memory");
-    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+// arrive on another CTA's mbarrier; release at cluster scope orders this thread's stores before it
+__device__ __forceinline__ void os_arrive_remote(uint32_t rbar) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(rbar) : "memory");
 }
-// the source of this thread's bulk copies has been read
-__device__ __forceinline__ void os_bulk_read_done() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
-// bounded wait (about 1 s of GPU clock) with cluster-scope acquire
-__device__ __forceinline__ bool os_wait(const uint64_t* bar, unsigned parity) {
+// bounded wait with cluster-scope acquire
+__device__ __forceinline__ bool os_wait(const uint64_t* bar, unsigned parity, long long limit) {
     const long long t0 = clock64();
     for (;;) {
         uint32_t ok;
@@ -189,237 +221,237 @@ __device__ __forceinline__ bool os_wait(const uint64_t* bar, unsigned parity) {
             : "r"(os_smem(bar)), "r"(parity)
             : "memory");
         if (ok) return true;
-        if (clock64() - t0 > (1ll << 31)) return false;
+        if (clock64() - t0 > limit) return false;
     }
 }
+__device__ __forceinline__ void os_bar(int id, int count) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory"); }
 
-// Each step: every warp rotates its pair; then one column moves to each
-// neighbouring CTA (warp 0 owns the link to the right, warp 1 the link to the
-// left): the sender stores it into the neighbour's receive buffer and arrives
-// on the neighbour's mbarrier; the receiver waits only for its two
-// neighbours, so no cluster-wide barrier is needed within a sweep.
+// Column slots of a CTA: top[u] and bot[u] (u < P) hold the two columns of pair u.  A
+// slot maps to one of the CTA's buffers: 2P local ones (the initial columns), then a ring
+// of D buffers for columns arriving from the left neighbour and one for columns
+// from the right.  In the circle tournament, per step, the top row moves right and the
+// bottom row left: top[P-1] leaves to the right neighbour's top[0], bot[0] to the left
+// neighbour's bot[P-1]; the first CTA keeps top[0] and moves bot[0] to top[1], the last
+// moves top[P-1] to bot[P-1].  A received column stays at most 2P steps in a CTA (the
+// last CTA passes it through its top and its bottom row).  A neighbour stores into ring
+// slot K mod D at step K only after it has received this CTA's column of step K - 1,
+// which was sent after this CTA's barrier of step K - 2: so a ring of D = 2P + 2 buffers
+// per side keeps every store causally after the last read of the column it overwrites.
 __global__ void __launch_bounds__(512) onesided_jacobi_kernel(OsParams prm) {
     cg::cluster_group cluster = cg::this_cluster();
     const int C = (int)cluster.num_blocks();
     const int c = (int)cluster.block_rank();
-    const int n = prm.n, np = prm.np, P = prm.P;
-    const int LD = ((n + 2) + 1) & ~1;  // x[0..n-1], idx, nrm
+    const int n = prm.n, np = prm.np, P = prm.P, H = prm.H;
     extern __shared__ __align__(16) double sm[];
-    double* bufs = sm;                       // [2P][LD]
-    double* recv = sm + (size_t)2 * P * LD;  // [2 parity][2 side: 0 from the left, 1 from the right][LD]
-    __shared__ uint64_t rbar[2][2];          // same indexing as recv
-    __shared__ int map_top[2][32], map_bot[2][32];  // slot -> buffer, double-buffered by step parity
+    const int D = 2 * P + 2;  // receive ring depth per side
+    double* bufs = sm;  // [2P + 2D][OS_LD]
+    const int RL0 = 2 * P, RR0 = 2 * P + D;
+    __shared__ uint64_t rbar[2][OS_MAXRING];  // [0]: from the left, [1]: from the right
+    __shared__ int map_top[2][OS_MAXP], map_bot[2][OS_MAXP];  // slot -> buffer, by step parity
+    __shared__ double red[2][OS_MAXP][2];   // per step parity, pair, half: dot products
+    __shared__ double red2[OS_MAXP][2][2];  // norm recomputation: pair, half, column
     __shared__ int s_rot;
-    __shared__ int s_cnt[2];                 // used in CTA 0: per-sweep cluster totals
+    __shared__ int s_cnt[2];                // used in CTA 0: per-sweep cluster totals
     __shared__ int s_total;
-    __shared__ int s_lmax;                   // this CTA's largest scaled |g| of the sweep (float bits)
-    __shared__ int s_mx[2];                  // used in CTA 0: per-sweep cluster maxima (float bits)
+    __shared__ int s_lmax;                  // this CTA's largest scaled |g| of the sweep (float bits)
+    __shared__ int s_mx[2];                 // used in CTA 0: per-sweep cluster maxima (float bits)
     __shared__ int s_mx_total;
-    __shared__ int s_fail[2];                // used in CTA 0: failed pairs of a convergence check
+    __shared__ int s_fail[2];               // used in CTA 0: failed pairs of a convergence check
     __shared__ int s_fail_total;
     __shared__ int s_timeout;
-    __shared__ float s_off[32];              // per warp: the largest scaled |g| left in the sweep
+    __shared__ float s_off[16];             // per warp: the largest scaled |g| left in the sweep
     __shared__ float s_off_cta;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nwarps = (int)(blockDim.x >> 5);
+    const int a = warp % P, h = warp / P;  // pair and row half of this warp
+    const int e = 32 * h + lane;           // this lane's row
+    const int R = 32 * H;                  // rows held per column
     const int N = np - 1;
     const double tol2 = prm.tol * prm.tol;
     const float tol_f = (float)prm.tol;
 
     if (tid == 0) {
-        for (int a = 0; a < 2; ++a)
-            for (int b = 0; b < 2; ++b)
-                asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(os_smem(&rbar[a][b])));
-        // each receive buffer expects one column at steps 0 and 1 (re-armed after every use)
-        for (int a = 0; a < 2; ++a)
-            for (int b = 0; b < 2; ++b) os_arm(&rbar[a][b], (unsigned)(sizeof(double) * LD));
+        for (int s = 0; s < 2; ++s)
+            for (int r = 0; r < D; ++r)
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(os_smem(&rbar[s][r])), "r"(32 * H));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        s_cnt[0] = 0;
-        s_cnt[1] = 0;
-        s_mx[0] = 0;
-        s_mx[1] = 0;
-        s_fail[0] = 0;
-        s_fail[1] = 0;
+        s_cnt[0] = s_cnt[1] = 0;
+        s_mx[0] = s_mx[1] = 0;
+        s_fail[0] = s_fail[1] = 0;
         s_timeout = 0;
     }
     // initial placement: local top u <- column cP+u, bottom u <- column np-1-cP-u
-    for (int u = warp; u < 2 * P; u += blockDim.x / 32) {
+    for (int u = warp; u < 2 * P; u += nwarps) {
         const int col = (u < P) ? c * P + u : np - 1 - c * P - (u - P);
-        double* b = bufs + (size_t)u * LD;
+        double* b = bufs + (size_t)u * OS_LD;
         double s2 = 0.0;
-        for (int r = lane; r < n; r += 32) {
-            const double v = (col < n) ? prm.X[r + (size_t)col * n] : 0.0;
+        for (int r = lane; r < 64; r += 32) {
+            const double v = (col < n && r < n) ? prm.X[r + (size_t)col * n] : 0.0;
             b[r] = v;
-            s2 += v * v;
+            s2 = fma(v, v, s2);
         }
         s2 = warp_sum(s2);
-        if (lane == 0) { b[n] = __longlong_as_double((long long)col); b[n + 1] = s2; }
+        if (lane == 0) { b[64] = s2; b[65] = __longlong_as_double((long long)col); }
     }
     if (tid < P) { map_top[0][tid] = tid; map_bot[0][tid] = P + tid; }
     cluster.sync();
 
     int sweep = 0;
     bool converged = false;
-    unsigned K = 0;  // global step counter (parity of buffers and mbarrier phases)
+    unsigned K = 0;  // global step counter: map parity, ring slot, mbarrier phase
     float best_off = 0.0f;
     float sweep_mx = 0.0f;  // lane 0 of a pair warp: the largest scaled |g| met in the sweep
     int checks = 0;
+    bool timed_out = false;
     while (sweep < prm.max_sweeps) {
         ++sweep;
         if (tid == 0) { s_rot = 0; s_lmax = 0; }
         best_off = 0.0f;
         sweep_mx = 0.0f;
-        // exact squared norms at the start of the sweep
-        for (int u = warp; u < 2 * P; u += blockDim.x / 32) {
-            double* b = bufs + (size_t)u * LD;
-            double s2 = 0.0;
-            for (int r = lane; r < n; r += 32) s2 += b[r] * b[r];
-            s2 = warp_sum(s2);
-            if (lane == 0) b[n + 1] = s2;
+        {   // exact squared norms at the start of the sweep
+            const int par = (int)(K & 1u);
+            for (int u = warp; u < 2 * P; u += nwarps) {
+                double* b = bufs + (size_t)(u < P ? map_top[par][u] : map_bot[par][u - P]) * OS_LD;
+                double s2 = 0.0;
+                for (int r = lane; r < R; r += 32) s2 = fma(b[r], b[r], s2);
+                s2 = warp_sum(s2);
+                if (lane == 0) b[64] = s2;
+            }
         }
         __syncthreads();
         for (int k = 0; k < N; ++k, ++K) {
             const int par = (int)(K & 1u);
-            const int* top = map_top[par];
-            const int* bot = map_bot[par];
-            // one warp per pair: g = x_p^T x_q, the rotation, and its application.  Every FP64
-            // warp instruction holds its SMSP's FP64 pipe for about 64 cycles on GB300, so the
-            // scalar work is kept to the few FP64 operations that set the result.
-            if (warp < P) {
-                double* xp = bufs + (size_t)top[warp] * LD;
-                double* xq = bufs + (size_t)bot[warp] * LD;
-                const double app = xp[n + 1], aqq = xq[n + 1];
-                double g = 0.0;
-                for (int r = lane; r < n; r += 32) g = fma(xp[r], xq[r], g);
-                g = warp_sum(g);
-                // column ids are stored as integer bit patterns; positive doubles have positive
-                // patterns (integer compares keep these tests off the FP64 pipe)
-                const bool live = __double_as_longlong(xp[n]) < n && __double_as_longlong(xq[n]) < n &&
-                                  __double_as_longlong(app) > 0 && __double_as_longlong(aqq) > 0;
-                // the scaled test |g| > tol sqrt(a_pp a_qq): decided in FP32 when the FP32 ratio
-                // is clearly on one side (factor 4), exactly in FP64 otherwise
-                bool rot = false;
-                if (live && g != 0.0) {
-                    const float gf = fabsf(os_to_float(g)), af = os_to_float(app), bf = os_to_float(aqq);
-                    // all three well inside the FP32 range: r = |g| / sqrt(a_pp a_qq) to ~2^-22
-                    const bool in_range = af > 1e-30f && af < 1e30f && bf > 1e-30f && bf < 1e30f &&
-                                          gf > 1e-30f && gf < 1e30f;
-                    const float rr = in_range ? gf * rsqrtf(af) * rsqrtf(bf) : 0.0f;
-                    const float tl = tol_f;
-                    if (in_range && rr > 2.0f * tl) rot = true;
-                    else if (!in_range || rr > 0.5f * tl) rot = g * g > tol2 * (app * aqq);
-                    if (!rot && lane == 0) best_off = fmaxf(best_off, rr);
-                    if (lane == 0) sweep_mx = fmaxf(sweep_mx, in_range ? rr : (rot ? 1.0f : 0.0f));
-                }
-                if (rot) {
-                    // Rotation angle from Rutishauser's t = sgn(zeta)/(|zeta| + sqrt(1 + zeta^2)),
-                    // zeta = (a_qq - a_pp) / 2g, sgn(0) = +1, evaluated in FP32 from ratios <= 1
-                    // (its accuracy only sets how far g is reduced), and c0 = 1/sqrt(1 + t^2),
-                    // s0 = t c0 in FP32.  The applied rotation (c0, s0) f is orthogonal to FP64
-                    // precision: with e = c0^2 + s0^2 - 1 (exact in FP64, |e| ~ 2^-24),
-                    // f = 1 - e/2 + 3e^2/8 = (1 + e)^(-1/2) + O(e^3).
-                    // a_qq - a_pp in FP64 first: for nearly equal norms (clustered sigma) the difference of
-                    // two FP32 roundings would be noise and the angle would not shrink g
-                    const float df = os_to_float(aqq - app);
-                    const float hf = 2.0f * os_to_float(g);
-                    const float adf = fabsf(df), ahf = fabsf(hf);
-                    const float sz = (df == 0.0f || (df > 0.0f) == (hf > 0.0f)) ? 1.0f : -1.0f;
-                    float tf;
-                    if (adf >= ahf) {
-                        const float z = ahf / adf;
-                        tf = sz * z / (1.0f + sqrtf(fmaf(z, z, 1.0f)));
-                    } else {
-                        const float w = adf / ahf;
-                        tf = sz / (w + sqrtf(fmaf(w, w, 1.0f)));
-                    }
-                    const float cf = rsqrtf(fmaf(tf, tf, 1.0f));
-                    const double c0 = os_to_double(cf), s0 = os_to_double(tf * cf);
-                    const double e = fma(c0, c0, fma(s0, s0, -1.0));
-                    const double f = fma(e, fma(e, 0.375, -0.5), 1.0);
-                    const double cs = c0 * f, sn = s0 * f;
-                    for (int r = lane; r < n; r += 32) {
-                        const double a = xp[r], b = xq[r];
-                        xp[r] = fma(cs, a, -sn * b);
-                        xq[r] = fma(sn, a, cs * b);
-                    }
-                    // Within a sweep the squared norms only steer later angles and tests; they
-                    // follow the exact-angle update a_pp - t g, a_qq + t g.  Every sweep starts
-                    // from exact norms, and the final sweep (no rotation) uses only those.
-                    const double tg = os_to_double(tf) * g;
-                    double np2 = app - tg, nq2 = aqq + tg;
-                    __syncwarp();
-                    // a norm that dropped by 16x is recomputed (cancellation in the update)
-                    if (os_hi(np2) < os_hi(app) - (4 << 20)) {
-                        double s2 = 0.0;
-                        for (int r = lane; r < n; r += 32) s2 = fma(xp[r], xp[r], s2);
-                        np2 = warp_sum(s2);
-                    }
-                    if (os_hi(nq2) < os_hi(aqq) - (4 << 20)) {
-                        double s2 = 0.0;
-                        for (int r = lane; r < n; r += 32) s2 = fma(xq[r], xq[r], s2);
-                        nq2 = warp_sum(s2);
-                    }
-                    __syncwarp();
-                    if (lane == 0) {
-                        xp[n + 1] = np2;
-                        xq[n + 1] = nq2;
-                        atomicAdd(&s_rot, 1);
-                    }
-                }
-                // The links: warp P-1 (holding the last top column) moves it to the right
-                // neighbour, warp 0 (holding the first bottom column) moves it to the left one,
-                // each as soon as its own pair is done, by a bulk copy into the neighbour's
-                // receive buffer; each receives into the buffer it sent once that copy has read it.
-                const unsigned ph = (K >> 1) & 1u;
-                const unsigned colb = (unsigned)(sizeof(double) * LD);
-                if (warp == P - 1 && c < C - 1) {
-                    __syncwarp();
-                    if (lane == 0) {
-                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                        os_bulk_to(xp, recv + (size_t)(par * 2 + 0) * LD, &rbar[par][0], c + 1, colb);
-                    }
-                    if (!os_wait(&rbar[par][1], ph)) s_timeout = 1;
-                    if (lane == 0) {
-                        os_arm(&rbar[par][1], colb);  // for step K + 2
-                        os_bulk_read_done();
-                    }
-                    __syncwarp();
-                    const double* rs = recv + (size_t)(par * 2 + 1) * LD;
-                    for (int r = lane; r < n + 2; r += 32) xp[r] = rs[r];
-                }
-                if (warp == 0 && c > 0) {
-                    __syncwarp();
-                    if (lane == 0) {
-                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                        os_bulk_to(xq, recv + (size_t)(par * 2 + 1) * LD, &rbar[par][1], c - 1, colb);
-                    }
-                    if (!os_wait(&rbar[par][0], ph)) s_timeout = 1;
-                    if (lane == 0) {
-                        os_arm(&rbar[par][0], colb);  // for step K + 2
-                        os_bulk_read_done();
-                    }
-                    __syncwarp();
-                    const double* rs = recv + (size_t)(par * 2 + 0) * LD;
-                    for (int r = lane; r < n + 2; r += 32) xq[r] = rs[r];
-                }
+            const int ring = (int)(K % (unsigned)D);
+            const unsigned phase = (K / (unsigned)D) & 1u;
+            double* xp = bufs + (size_t)map_top[par][a] * OS_LD;
+            double* xq = bufs + (size_t)map_bot[par][a] * OS_LD;
+            const double va = xp[e], vb = xq[e];
+            const double app = xp[64], aqq = xq[64];
+            const long long idp = __double_as_longlong(xp[65]), idq = __double_as_longlong(xq[65]);
+            // g = x_p^T x_q over both halves (the same sum in the same order in both warps)
+            double g = warp_sum(va * vb);
+            if (H == 2) {
+                if (lane == 0) red[par][a][h] = g;
+                os_bar(1 + a, 64);
+                g = red[par][a][0] + red[par][a][1];
             }
-            // circle tournament move: slot j -> j+1 (1 <= j <= np-2), slot np-1 -> 1, slot 0 fixed.
-            // The buffer sent away on each link is reused for the column received on it.
-            const int free_a = top[P - 1];  // sent to the right (when there is a right neighbour)
-            const int free_b = bot[0];      // sent to the left
+            // column ids are integer bit patterns; positive doubles have positive patterns
+            // (integer compares keep these tests off the FP64 pipe)
+            const bool live = idp < n && idq < n && __double_as_longlong(app) > 0 && __double_as_longlong(aqq) > 0;
+            // the scaled test |g| > tol sqrt(a_pp a_qq): decided in FP32 when the FP32 ratio
+            // is clearly on one side (factor 2), exactly in FP64 otherwise
+            bool rot = false;
+            float rr = 0.0f;
+            bool in_range = false;
+            if (live && g != 0.0) {
+                const float gf = fabsf(os_to_float(g)), af = os_to_float(app), bf = os_to_float(aqq);
+                in_range = af > 1e-30f && af < 1e30f && bf > 1e-30f && bf < 1e30f && gf > 1e-30f && gf < 1e30f;
+                rr = in_range ? gf * rsqrtf(af) * rsqrtf(bf) : 0.0f;
+                if (in_range && rr > 2.0f * tol_f) rot = true;
+                else if (!in_range || rr > 0.5f * tol_f) rot = g * g > tol2 * (app * aqq);
+                if (!rot) best_off = fmaxf(best_off, rr);
+                sweep_mx = fmaxf(sweep_mx, in_range ? rr : (rot ? 1.0f : 0.0f));
+            }
+            double na = va, nb = vb, np2 = app, nq2 = aqq;
+            if (rot) {
+                // Rutishauser's t = sgn(zeta)/(|zeta| + sqrt(1 + zeta^2)), zeta = (a_qq - a_pp) / 2g,
+                // sgn(0) = +1, in FP32 from ratios <= 1 (its accuracy only sets how far g is
+                // reduced); c0 = 1/sqrt(1 + t^2), s0 = t c0.  The applied rotation (c0, s0) f is
+                // orthogonal to FP64 precision: with e = c0^2 + s0^2 - 1 (exact in FP64,
+                // |e| ~ 2^-24), f = 1 - e/2 + 3e^2/8 = (1 + e)^(-1/2) + O(e^3).  a_qq - a_pp is
+                // formed in FP64 first: for nearly equal norms (clustered sigma) the difference
+                // of two FP32 roundings would be noise and the angle would not shrink g.
+                const float df = os_to_float(aqq - app);
+                const float hf = 2.0f * os_to_float(g);
+                const float adf = fabsf(df), ahf = fabsf(hf);
+                const float sz = (df == 0.0f || (df > 0.0f) == (hf > 0.0f)) ? 1.0f : -1.0f;
+                float tf;
+                if (adf >= ahf) {
+                    const float z = ahf / adf;
+                    tf = sz * z / (1.0f + sqrtf(fmaf(z, z, 1.0f)));
+                } else {
+                    const float w = adf / ahf;
+                    tf = sz / (w + sqrtf(fmaf(w, w, 1.0f)));
+                }
+                const float cf = rsqrtf(fmaf(tf, tf, 1.0f));
+                const double c0 = os_to_double(cf), s0 = os_to_double(tf * cf);
+                const double ee = fma(c0, c0, fma(s0, s0, -1.0));
+                const double f = fma(ee, fma(ee, 0.375, -0.5), 1.0);
+                const double cs = c0 * f, sn = s0 * f;
+                na = fma(cs, va, -sn * vb);
+                nb = fma(sn, va, cs * vb);
+                // Within a sweep the squared norms only steer later angles and tests; they
+                // follow the exact-angle update a_pp - t g, a_qq + t g.  Every sweep starts
+                // from exact norms, and the final sweep (no rotation) uses only those.
+                const double tg = os_to_double(tf) * g;
+                np2 = app - tg;
+                nq2 = aqq + tg;
+                // a norm that dropped by 16x is recomputed (cancellation in the update); the
+                // decision is the same in both warps of the pair
+                const bool redo_p = os_hi(np2) < os_hi(app) - (4 << 20);
+                const bool redo_q = os_hi(nq2) < os_hi(aqq) - (4 << 20);
+                if (redo_p || redo_q) {
+                    double sp = warp_sum(na * na), sq = warp_sum(nb * nb);
+                    if (H == 2) {
+                        if (lane == 0) { red2[a][h][0] = sp; red2[a][h][1] = sq; }
+                        os_bar(1 + a, 64);
+                        sp = red2[a][0][0] + red2[a][1][0];
+                        sq = red2[a][0][1] + red2[a][1][1];
+                    }
+                    if (redo_p) np2 = sp;
+                    if (redo_q) nq2 = sq;
+                }
+                if (h == 0 && lane == 0) atomicAdd(&s_rot, 1);
+            }
+            // top[P-1] leaves to the right, bot[0] to the left (straight from registers, with
+            // the norm and the id); every other column is written back in place
+            const bool send_r = (a == P - 1) && (c < C - 1);
+            const bool send_l = (a == 0) && (c > 0);
+            if (send_r) {
+                const uint32_t dst = os_mapa(bufs + (size_t)(RL0 + ring) * OS_LD, c + 1);
+                os_st_remote(dst + 8u * (unsigned)e, na);
+                if (h == 0 && lane == 0) {
+                    os_st_remote(dst + 8u * 64u, np2);
+                    os_st_remote(dst + 8u * 65u, __longlong_as_double(idp));
+                }
+                os_arrive_remote(os_mapa(&rbar[0][ring], c + 1));
+            } else {
+                xp[e] = na;
+                if (h == 0 && lane == 0) xp[64] = np2;
+            }
+            if (send_l) {
+                const uint32_t dst = os_mapa(bufs + (size_t)(RR0 + ring) * OS_LD, c - 1);
+                os_st_remote(dst + 8u * (unsigned)e, nb);
+                if (h == 0 && lane == 0) {
+                    os_st_remote(dst + 8u * 64u, nq2);
+                    os_st_remote(dst + 8u * 65u, __longlong_as_double(idq));
+                }
+                os_arrive_remote(os_mapa(&rbar[1][ring], c - 1));
+            } else {
+                xq[e] = nb;
+                if (h == 0 && lane == 0) xq[64] = nq2;
+            }
+            // the columns arriving in this step (every thread acquires them itself); after one
+            // wait has run out the rest fail at once, so a lost neighbour costs one limit
+            const long long lim = timed_out ? 0 : prm.wait_limit;
+            if (c > 0 && !os_wait(&rbar[0][ring], phase, lim)) { timed_out = true; s_timeout = 1; }
+            if (c < C - 1 && !os_wait(&rbar[1][ring], phase, lim)) { timed_out = true; s_timeout = 1; }
             if (tid == 0) {
+                const int* top = map_top[par];
+                const int* bot = map_bot[par];
                 int* nt = map_top[par ^ 1];
-                int* nb = map_bot[par ^ 1];
-                nt[0] = (c == 0) ? top[0] : free_b;
+                int* nb_ = map_bot[par ^ 1];
+                nt[0] = (c == 0) ? top[0] : RL0 + ring;
                 nt[1] = (c == 0) ? bot[0] : top[0];
                 for (int u = 2; u < P; ++u) nt[u] = top[u - 1];
-                for (int u = 0; u < P - 1; ++u) nb[u] = bot[u + 1];
-                nb[P - 1] = (c == C - 1) ? top[P - 1] : free_a;
+                for (int u = 0; u < P - 1; ++u) nb_[u] = bot[u + 1];
+                nb_[P - 1] = (c == C - 1) ? top[P - 1] : RR0 + ring;
             }
             __syncthreads();
         }
         // cluster-wide rotation count and largest scaled |g| of this sweep
         const int sp = sweep & 1;
-        if (lane == 0 && warp < P) atomicMax(&s_lmax, __float_as_int(sweep_mx));
+        if (lane == 0 && h == 0) atomicMax(&s_lmax, __float_as_int(sweep_mx));
         __syncthreads();
         if (tid == 0) {
             atomicAdd(&cluster.map_shared_rank(s_cnt, 0)[sp], s_rot);
@@ -440,12 +472,13 @@ __global__ void __launch_bounds__(512) onesided_jacobi_kernel(OsParams prm) {
         // pair of the current columns is tested at once (the same scaled test, exact norms);
         // the sweep runs only if some pair fails.
         if (mx < 0x1p-20f && sweep < prm.max_sweeps) {
-            for (int u = warp; u < 2 * P; u += blockDim.x / 32) {
-                double* b = bufs + (size_t)u * LD;
+            const int par = (int)(K & 1u);
+            for (int u = warp; u < 2 * P; u += nwarps) {
+                double* b = bufs + (size_t)(u < P ? map_top[par][u] : map_bot[par][u - P]) * OS_LD;
                 double s2 = 0.0;
-                for (int r = lane; r < n; r += 32) s2 += b[r] * b[r];
+                for (int r = lane; r < R; r += 32) s2 = fma(b[r], b[r], s2);
                 s2 = warp_sum(s2);
-                if (lane == 0) b[n + 1] = s2;
+                if (lane == 0) b[64] = s2;
             }
             cluster.sync();
             int fails = 0;
@@ -453,21 +486,21 @@ __global__ void __launch_bounds__(512) onesided_jacobi_kernel(OsParams prm) {
             const int items = slots * slots * C;
             for (int it = tid; it < items; it += blockDim.x) {
                 const int u = it % slots, w = (it / slots) % slots, rk = it / (slots * slots);
-                const double* bu = bufs + (size_t)u * LD;
-                const double* bv = cluster.map_shared_rank(bufs, rk) + (size_t)w * LD;
-                const long long iu = __double_as_longlong(bu[n]), iv = __double_as_longlong(bv[n]);
+                const double* bu = bufs + (size_t)(u < P ? map_top[par][u] : map_bot[par][u - P]) * OS_LD;
+                const int* rt = cluster.map_shared_rank(&map_top[par][0], rk);
+                const int* rb = cluster.map_shared_rank(&map_bot[par][0], rk);
+                const double* bv = cluster.map_shared_rank(bufs, rk) + (size_t)(w < P ? rt[w] : rb[w - P]) * OS_LD;
+                const long long iu = __double_as_longlong(bu[65]), iv = __double_as_longlong(bv[65]);
                 if (!(iu < iv && iv < n)) continue;
-                const double au = bu[n + 1], av = bv[n + 1];
+                const double au = bu[64], av = bv[64];
                 if (!(au > 0.0 && av > 0.0)) continue;
                 double g0 = 0.0, g1 = 0.0, g2 = 0.0, g3 = 0.0;
-                int r = 0;
-                for (; r + 3 < n; r += 4) {
+                for (int r = 0; r < R; r += 4) {
                     g0 = fma(bu[r], bv[r], g0);
                     g1 = fma(bu[r + 1], bv[r + 1], g1);
                     g2 = fma(bu[r + 2], bv[r + 2], g2);
                     g3 = fma(bu[r + 3], bv[r + 3], g3);
                 }
-                for (; r < n; ++r) g0 = fma(bu[r], bv[r], g0);
                 const double g = (g0 + g1) + (g2 + g3);
                 if (g * g > tol2 * (au * av)) ++fails;
             }
@@ -483,24 +516,27 @@ __global__ void __launch_bounds__(512) onesided_jacobi_kernel(OsParams prm) {
         }
     }
     // outputs: lambda_j = ||x_j||^2, v_j = P^T x_j / ||x_j||
-    for (int u = warp; u < 2 * P; u += blockDim.x / 32) {
-        const double* b = bufs + (size_t)u * LD;
-        const int j = (int)__double_as_longlong(b[n]);
-        if (j >= n) continue;
-        double s2 = 0.0;
-        for (int r = lane; r < n; r += 32) s2 += b[r] * b[r];
-        s2 = warp_sum(s2);
-        const double nrm = sqrt(s2);
-        const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
-        for (int r = lane; r < n; r += 32) prm.V[prm.perm[r] + (size_t)j * n] = b[r] * inv;
-        if (lane == 0) prm.lam[j] = s2;
+    {
+        const int par = (int)(K & 1u);
+        for (int u = warp; u < 2 * P; u += nwarps) {
+            const double* b = bufs + (size_t)(u < P ? map_top[par][u] : map_bot[par][u - P]) * OS_LD;
+            const int j = (int)__double_as_longlong(b[65]);
+            if (j >= n) continue;
+            double s2 = 0.0;
+            for (int r = lane; r < R; r += 32) s2 = fma(b[r], b[r], s2);
+            s2 = warp_sum(s2);
+            const double nrm = sqrt(s2);
+            const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+            for (int r = lane; r < n; r += 32) prm.V[prm.perm[r] + (size_t)j * n] = b[r] * inv;
+            if (lane == 0) prm.lam[j] = s2;
+        }
     }
     // info: sweeps and the largest scaled |g| seen in the last sweep
-    if (lane == 0 && warp < 32) s_off[warp] = best_off;
+    if (lane == 0 && warp < 16) s_off[warp] = best_off;
     __syncthreads();
     if (tid == 0) {
         float off = 0.0f;
-        for (int w = 0; w < P && w < 32; ++w) off = fmaxf(off, s_off[w]);
+        for (int w = 0; w < nwarps && w < 16; ++w) off = fmaxf(off, s_off[w]);
         s_off_cta = off;
     }
     cluster.sync();
@@ -512,7 +548,112 @@ __global__ void __launch_bounds__(512) onesided_jacobi_kernel(OsParams prm) {
         if (!converged) atomicOr(&prm.info->flags, FLAG_NO_CONVERGENCE);
     }
     if (s_timeout && tid == 0) atomicOr(&prm.info->flags, FLAG_TIMEOUT);
-    cluster.sync();  // no CTA leaves while a neighbour may still read its shared memory
+    cluster.sync();  // no CTA leaves while a neighbour may still read or write its shared memory
+}
+
+// ---------------------------------------------------------------- kappa(B) estimate
+// L = rows of X scaled by 1/d_pos (d_pos = sqrt of M's diagonal at the pivot's original
+// index) is lower triangular with L L^T = P C P^T, C = D^-1 M D^-1 with unit diagonal, so
+// kappa(B) = (lambda_max / lambda_min)^(1/2) of L L^T.  One warp, FP32 (an estimate):
+// power iteration for lambda_max, inverse iteration (two triangular solves) for lambda_min.
+// Lane l holds rows l and l + 32.
+constexpr int KAPPA_ITERS = 16;
+constexpr int KLD = 65;  // padded column stride: row-wise reads hit distinct banks
+
+__global__ void __launch_bounds__(32)
+    kappa_kernel(const double* __restrict__ X, const int* __restrict__ perm, const double* __restrict__ M,
+                 int64_t ldm, int n, DevInfo* info) {
+    __shared__ float Lc[64 * KLD];  // column-major: Lc[i + KLD j] = L[i][j]
+    __shared__ float v[64], w[64];
+    const int lane = threadIdx.x;
+    bool bad = false;
+    for (int idx = lane; idx < 64 * 64; idx += 32) {
+        const int i = idx & 63, j = idx >> 6;
+        float val = 0.0f;
+        if (i < n && j < n && i >= j) {
+            const int o = perm[i];
+            const double dd = M[o + (size_t)o * ldm];
+            val = dd > 0.0 ? (float)(X[i + (size_t)j * n] / sqrt(dd)) : 0.0f;
+        }
+        Lc[i + KLD * j] = val;
+    }
+    __syncwarp();
+    for (int j = lane; j < n; j += 32)
+        if (!(Lc[j + KLD * j] != 0.0f)) bad = true;
+    bad = __any_sync(0xffffffffu, bad);
+    float lmax = 0.0f, lmin = 0.0f;
+    if (!bad) {
+        // lambda_max of L^T L (= that of L L^T): v <- L^T (L v), normalised
+        for (int i = lane; i < 64; i += 32) v[i] = i < n ? 1.0f + 0.01f * (float)i : 0.0f;
+        __syncwarp();
+        for (int it = 0; it < KAPPA_ITERS; ++it) {
+            // w = L v
+            for (int i = lane; i < 64; i += 32) {
+                float s = 0.0f;
+                for (int j = 0; j <= i && j < n; ++j) s = fmaf(Lc[i + KLD * j], v[j], s);
+                w[i] = s;
+            }
+            __syncwarp();
+            // v = L^T w
+            float nn = 0.0f;
+            float nv[2] = {0.0f, 0.0f};
+            for (int q = 0; q < 2; ++q) {
+                const int j = lane + 32 * q;
+                float s = 0.0f;
+                for (int i = j; i < n; ++i) s = fmaf(Lc[i + KLD * j], w[i], s);
+                nv[q] = s;
+                nn = fmaf(s, s, nn);
+            }
+            for (int o = 16; o > 0; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
+            // ||L^T L v|| / ||v|| with ||v|| = 1 after the first iteration
+            const float scale = rsqrtf(nn);
+            float vv = 0.0f;
+            for (int q = 0; q < 2; ++q) vv = fmaf(v[lane + 32 * q], v[lane + 32 * q], vv);
+            for (int o = 16; o > 0; o >>= 1) vv += __shfl_xor_sync(0xffffffffu, vv, o);
+            lmax = sqrtf(nn) * rsqrtf(vv);
+            __syncwarp();
+            for (int q = 0; q < 2; ++q) v[lane + 32 * q] = nv[q] * scale;
+            __syncwarp();
+        }
+        // lambda_min: w = (L^T L)^-1 v by L^T y = v (backward), then L w = y (forward)
+        for (int i = lane; i < 64; i += 32) v[i] = i < n ? 1.0f - 0.01f * (float)i : 0.0f;
+        __syncwarp();
+        for (int it = 0; it < KAPPA_ITERS; ++it) {
+            float r0 = v[lane], r1 = v[lane + 32];
+            // L^T y = v: for j = n-1 .. 0, y_j = r_j / L[j][j]; r_i -= L[j][i] y_j for i < j
+            for (int j = n - 1; j >= 0; --j) {
+                const float rj = __shfl_sync(0xffffffffu, j < 32 ? r0 : r1, j & 31);
+                const float yj = rj / Lc[j + KLD * j];
+                if (lane == (j & 31)) { if (j < 32) r0 = yj; else r1 = yj; }
+                if (lane < j) r0 = fmaf(-Lc[j + KLD * lane], yj, r0);
+                if (lane + 32 < j) r1 = fmaf(-Lc[j + KLD * (lane + 32)], yj, r1);
+            }
+            // L w = y: for j = 0 .. n-1, w_j = r_j / L[j][j]; r_i -= L[i][j] w_j for i > j
+            for (int j = 0; j < n; ++j) {
+                const float rj = __shfl_sync(0xffffffffu, j < 32 ? r0 : r1, j & 31);
+                const float wj = rj / Lc[j + KLD * j];
+                if (lane == (j & 31)) { if (j < 32) r0 = wj; else r1 = wj; }
+                if (lane > j) r0 = fmaf(-Lc[lane + KLD * j], wj, r0);
+                if (lane + 32 > j && lane + 32 < n) r1 = fmaf(-Lc[lane + 32 + KLD * j], wj, r1);
+            }
+            if (lane >= n) r0 = 0.0f;
+            if (lane + 32 >= n) r1 = 0.0f;
+            float nn = r0 * r0 + r1 * r1, vv = v[lane] * v[lane] + v[lane + 32] * v[lane + 32];
+            for (int o = 16; o > 0; o >>= 1) {
+                nn += __shfl_xor_sync(0xffffffffu, nn, o);
+                vv += __shfl_xor_sync(0xffffffffu, vv, o);
+            }
+            lmin = sqrtf(vv) * rsqrtf(nn);  // ||v|| / ||(L^T L)^-1 v|| -> lambda_min
+            const float scale = rsqrtf(nn);
+            __syncwarp();
+            v[lane] = r0 * scale;
+            v[lane + 32] = r1 * scale;
+            __syncwarp();
+        }
+    }
+    if (lane == 0)
+        info->kappa = (bad || !(lmin > 0.0f)) ? __longlong_as_double(0x7ff0000000000000ll)
+                                               : sqrt((double)lmax / (double)lmin);
 }
 
 // The FP64 pipe of one SM sets the pace, so the pairs are spread over as many
@@ -524,13 +665,34 @@ int cluster_size_for(int n, bool allow16) {
     return allow16 ? 16 : 8;
 }
 
-}  // namespace
+cudaError_t launch_cluster_jacobi(OsParams prm, int C, cudaStream_t s) {
+    prm.np = ((prm.n < 4 ? 4 : prm.n) + 4 * C - 1) / (4 * C) * (4 * C);
+    prm.P = prm.np / (2 * C);
+    prm.H = prm.n > 32 ? 2 : 1;
+    const size_t smem = sizeof(double) * (size_t)(2 * prm.P + 2 * (2 * prm.P + 2)) * OS_LD;
+    cudaError_t e =
+        cudaFuncSetAttribute(onesided_jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C, 1, 1);
+    cfg.blockDim = dim3(32 * prm.P * prm.H, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, onesided_jacobi_kernel, prm);
+}
 
-size_t eig_onesided_scratch_bytes(int n) { return sizeof(double) * (size_t)n * n + sizeof(int) * 256 + 256; }
+}  // namespace
 
 cudaError_t launch_eig_onesided(const double* M, int n, int64_t ldm, double tol, int max_sweeps,
                                 void* scratch, double* lam_ws, double* V_ws, DevInfo* info,
-                                cudaStream_t s) {
+                                cudaStream_t s, const EigSide* side, long long wait_cycles) {
     if (n > 64) return cudaErrorNotSupported;
     double* X = reinterpret_cast<double*>(scratch);
     int* perm = reinterpret_cast<int*>(reinterpret_cast<char*>(scratch) + sizeof(double) * (size_t)n * n);
@@ -541,50 +703,35 @@ cudaError_t launch_eig_onesided(const double* M, int n, int64_t ldm, double tol,
     chol_piv_kernel<<<1, 256, chol_smem, s>>>(M, n, ldm, X, perm, info);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    // kappa(B) on the side stream, beside the Jacobi (joined before the caller's next launch)
+    const bool fork = side != nullptr && side->stream != nullptr;
+    if (fork) {
+        e = cudaEventRecord(side->fork, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(side->stream, side->fork, 0);
+        if (e != cudaSuccess) return e;
+    }
+    kappa_kernel<<<1, 32, 0, fork ? side->stream : s>>>(X, perm, M, ldm, n, info);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (fork) {
+        e = cudaEventRecord(side->join, side->stream);
+        if (e != cudaSuccess) return e;
+    }
 
     const bool allow16 =
         cudaFuncSetAttribute(onesided_jacobi_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess;
     if (!allow16) (void)cudaGetLastError();
+    OsParams prm{X, perm, n, 0, 0, 0, tol, max_sweeps, wait_limit_of(wait_cycles), lam_ws, V_ws, info};
     int C = cluster_size_for(n, allow16);
-    int np = ((n < 4 ? 4 : n) + 4 * C - 1) / (4 * C) * (4 * C);
-    const int P = np / (2 * C);
-    const int LD = ((n + 2) + 1) & ~1;
-    const size_t smem = sizeof(double) * ((size_t)2 * P * LD + (size_t)4 * LD);
-    OsParams prm{X, perm, n, np, P, tol, max_sweeps, lam_ws, V_ws, info};
-    e = cudaFuncSetAttribute(onesided_jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-    if (e != cudaSuccess) return e;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(C, 1, 1);
-    cfg.blockDim = dim3(32 * (P < 2 ? 2 : P), 1, 1);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = C;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, onesided_jacobi_kernel, prm);
+    e = launch_cluster_jacobi(prm, C, s);
     if (e != cudaSuccess && C == 16) {
         // the device may not schedule a 16-CTA cluster: the portable size instead
         (void)cudaGetLastError();
-        C = 8;
-        np = ((n < 4 ? 4 : n) + 4 * C - 1) / (4 * C) * (4 * C);
-        prm.np = np;
-        prm.P = np / (2 * C);
-        const size_t smem8 = sizeof(double) * ((size_t)2 * prm.P * LD + (size_t)4 * LD);
-        e = cudaFuncSetAttribute(onesided_jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem8);
-        if (e != cudaSuccess) return e;
-        cfg.gridDim = dim3(C, 1, 1);
-        cfg.blockDim = dim3(32 * (prm.P < 2 ? 2 : prm.P), 1, 1);
-        cfg.dynamicSmemBytes = smem8;
-        attr[0].val.clusterDim.x = C;
-        e = cudaLaunchKernelEx(&cfg, onesided_jacobi_kernel, prm);
+        e = launch_cluster_jacobi(prm, 8, s);
     }
-    if (e != cudaSuccess) return e;
-    return cudaGetLastError();
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess && fork) e = cudaStreamWaitEvent(s, side->join, 0);
+    return e;
 }
 
 }  // namespace tsvd

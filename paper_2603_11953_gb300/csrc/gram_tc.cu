@@ -326,7 +326,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     gram_tc_kernel(const __grid_constant__ CUtensorMap tmapA, const __grid_constant__ CUtensorMap tmapB, int64_t m,
                    int n, int split, int64_t rows_per_cta,
                    long long* __restrict__ part_hi, long long* __restrict__ part_lo, int* __restrict__ part_E,
-                   DevInfo* info, const TcBatchItem* __restrict__ items) {
+                   DevInfo* info, const TcBatchItem* __restrict__ items, long long wait_limit) {
     extern __shared__ unsigned char tc_dyn[];
     // 1024-byte alignment for the swizzled operand atoms
     unsigned char* base = tc_dyn + ((1024 - (smem_addr(tc_dyn) & 1023)) & 1023);
@@ -405,7 +405,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             int issued = 0;
             for (int g = 0; g < G; ++g) {
                 const int f = g % TC_SF;
-                if (g >= TC_SF && !mbar_wait(&S.fp_empty[f], ((g / TC_SF) - 1) & 1)) {
+                if (g >= TC_SF && !mbar_wait(&S.fp_empty[f], ((g / TC_SF) - 1) & 1, wait_limit)) {
                     atomicExch(&S.abort, 1);
                     break;
                 }
@@ -423,13 +423,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             int period = 0;
             for (int g = 0; g < G; ++g) {
                 const int d = g % TC_SD;
-                if (!mbar_wait(&S.dig_full[d], (g / TC_SD) & 1) || S.abort) { atomicExch(&S.abort, 1); break; }
+                if (!mbar_wait(&S.dig_full[d], (g / TC_SD) & 1, wait_limit) || S.abort) {
+                    atomicExch(&S.abort, 1);
+                    break;
+                }
                 mbar_arrive(&S.fp_empty[g % TC_SF]);  // every worker has read this FP32 stage
                 const int newp = S.dig_newp[d];
                 if (newp && g > 0) {
                     // close the running period: the workers drain it before it is overwritten
                     mma_commit(&S.acc_full);
-                    if (!mbar_wait(&S.acc_empty, period & 1)) { atomicExch(&S.abort, 1); break; }
+                    if (!mbar_wait(&S.acc_empty, period & 1, wait_limit)) { atomicExch(&S.abort, 1); break; }
                     tc_fence_after();
                     ++period;
                 }
@@ -463,7 +466,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 int fl = 0;
                 if (g < G) {
                     const int f = g % TC_SF;
-                    if (!mbar_wait(&S.fp_full[f], (g / TC_SF) & 1)) fl |= 4;
+                    if (!mbar_wait(&S.fp_full[f], (g / TC_SF) & 1, wait_limit)) fl |= 4;
                     // max |a| of column j on the bit patterns (Inf / NaN have the largest); the
                     // lanes start at staggered row quads so each 16-byte load is conflict-free
                     unsigned mine = 0;
@@ -488,7 +491,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     }
                     Epend = max(Epend, e);
                 }
-                if (g >= TC_RD && !mbar_wait(&S.dec_empty[r], ((g / TC_RD) - 1) & 1)) fl |= 4;
+                if (g >= TC_RD && !mbar_wait(&S.dec_empty[r], ((g / TC_RD) - 1) & 1, wait_limit)) fl |= 4;
                 if (S.abort) fl |= 4;
                 fl = __reduce_or_sync(0xffffffffu, fl);
                 if (lane == 0) S.dflags[g & 1][dw] = fl;
@@ -543,7 +546,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         bool failed = false;
         for (int g = 0; g <= G; ++g) {
             const int r = g % TC_RD;
-            bool ok = mbar_wait(&S.dec_full[r], (g / TC_RD) & 1) && !S.abort;
+            bool ok = mbar_wait(&S.dec_full[r], (g / TC_RD) & 1, wait_limit) && !S.abort;
             if (!__all_sync(0xffffffffu, ok)) { failed = true; break; }
             const TcRecord& R = S.rec[r];
             const int newp = R.newp;
@@ -551,7 +554,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const int d = g % TC_SD, f = g % TC_SF;
                 // the FP32 stage has landed: the deciders waited for it before publishing the record
                 // (their release on dec_full orders it before this warp's acquire)
-                ok = g < TC_SD || mbar_wait(&S.dig_empty[d], ((g / TC_SD) - 1) & 1);
+                ok = g < TC_SD || mbar_wait(&S.dig_empty[d], ((g / TC_SD) - 1) & 1, wait_limit);
                 if (!__all_sync(0xffffffffu, ok)) { failed = true; break; }
                 // digits of sub-chunk g: y = 128 a 2^-E (|y| < 128, < 256 after a soft growth);
                 // digit s is y's remainder rounded to the grid 2^-8s (|digit| <= 128 grid units,
@@ -603,7 +606,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             if (((newp && g > 0) || g == G) && G > 0) {
                 // the MMA issuer closes a period on seeing the first stage of the next one
                 // (or after the last sub-chunk); drain it
-                ok = mbar_wait(&S.acc_full, drained & 1);
+                ok = mbar_wait(&S.acc_full, drained & 1, wait_limit);
                 if (!__all_sync(0xffffffffu, ok)) { failed = true; break; }
                 tc_fence_after();
                 tc_drain(R, tmem, quad, lane, J0, hi, lo);
@@ -704,7 +707,8 @@ cudaError_t launch_gram_tc2(const void* A, int64_t m, int n, int64_t lda, int c1
     e = cudaFuncSetAttribute(gram_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
     if (e != cudaSuccess) return e;
     gram_tc_kernel<false><<<plan.P, TC_THREADS, TC_SMEM, s>>>(tmapA, tmapB, m, split ? 64 : n, split ? 1 : 0,
-                                                       plan.rows_per_cta, ph, pl, pE, info, nullptr);
+                                                              plan.rows_per_cta, ph, pl, pE, info, nullptr,
+                                                              wait_limit_of(plan.wait_cycles));
     return cudaGetLastError();
 }
 
@@ -719,7 +723,7 @@ cudaError_t make_tc_batch_tmap(void* map, const float* A, int64_t m, int n, int6
 }
 
 cudaError_t launch_gram_tc_batch(const TcBatchItem* items, int nitems, void* part, int total_slots, DevInfo* infos,
-                                 cudaStream_t s) {
+                                 cudaStream_t s, long long wait_cycles) {
     if (nitems == 0) return cudaSuccess;
     long long* ph = reinterpret_cast<long long*>(part);
     long long* pl = ph + (size_t)total_slots * 64 * 64;
@@ -728,7 +732,8 @@ cudaError_t launch_gram_tc_batch(const TcBatchItem* items, int nitems, void* par
     if (e != cudaSuccess) return e;
     CUtensorMap unused;
     std::memset(&unused, 0, sizeof(unused));
-    gram_tc_kernel<true><<<nitems, TC_THREADS, TC_SMEM, s>>>(unused, unused, 0, 64, 0, 0, ph, pl, pE, infos, items);
+    gram_tc_kernel<true><<<nitems, TC_THREADS, TC_SMEM, s>>>(unused, unused, 0, 64, 0, 0, ph, pl, pE, infos, items,
+                                                             wait_limit_of(wait_cycles));
     return cudaGetLastError();
 }
 

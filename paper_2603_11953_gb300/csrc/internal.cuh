@@ -24,6 +24,20 @@ enum : int {
     FLAG_TIMEOUT = 8,
 };
 
+// Limit, in GPU clock cycles, of the steady-state bounded waits of the
+// pipelined kernels for a tsvd_opts.timeout_cycles value (0 = the default,
+// about a second of GPU clock).  Waits that drain copies and MMAs already in
+// flight before a kernel exits keep the default whatever the option.
+constexpr long long WAIT_CYCLES_DEFAULT = 1ll << 31;
+inline long long wait_limit_of(long long opt) { return opt > 0 ? opt : WAIT_CYCLES_DEFAULT; }
+
+// A second stream and two events of a handle: small independent kernels fork
+// off the main stream and join it again (capturable in a CUDA graph).
+struct EigSide {
+    cudaStream_t stream;
+    cudaEvent_t fork, join;
+};
+
 // Sentinel exponent of an all-zero column (no digits, nothing accumulated).
 constexpr int EXP_EMPTY = -(1 << 20);
 
@@ -40,6 +54,7 @@ struct GramPlan {
     int NP;            // padded n (16, 32, 48 or 64)
     int P;             // CTAs over m (split-K)
     int64_t rows_per_cta;
+    long long wait_cycles = 0;  // limit of the tensor-core Gram's steady-state waits (0 = default)
 };
 GramPlan gram_plan(int64_t m, int n, int sm_count, int split_k_opt);
 size_t gram_partials_bytes(const GramPlan& p);
@@ -98,10 +113,12 @@ cudaError_t launch_jacobi(const double* M, int n, int64_t ldm, double tol, int m
 
 // Preconditioned one-sided Jacobi in FP64 (pivoted Cholesky, then one-sided
 // Jacobi on R^T over a thread-block cluster), n <= 64.  scratch: at least
-// n*n doubles + 256 ints.  Writes unsorted lambda and V like launch_jacobi.
+// n*n doubles + 256 ints.  Writes unsorted lambda and V like launch_jacobi,
+// and the kappa(B) estimate into info->kappa (on side->stream when given,
+// joined back into s before returning).  wait_cycles: tsvd_opts.timeout_cycles.
 cudaError_t launch_eig_onesided(const double* M, int n, int64_t ldm, double tol, int max_sweeps,
                                 void* scratch, double* lam_ws, double* V_ws, DevInfo* info,
-                                cudaStream_t s);
+                                cudaStream_t s, const EigSide* side = nullptr, long long wait_cycles = 0);
 
 // Double-double eigen stage for FP64 working (n <= 64, one CTA): pivoted
 // Cholesky of M = G + G_lo in double-double, then a one-sided Jacobi SVD of
@@ -179,7 +196,7 @@ bool gram_tc_batch_ok(const void* A, int64_t lda);
 size_t tc_tmap_bytes();
 cudaError_t make_tc_batch_tmap(void* map, const float* A, int64_t m, int n, int64_t lda, int box_cols);
 cudaError_t launch_gram_tc_batch(const TcBatchItem* items, int nitems, void* part, int total_slots, DevInfo* infos,
-                                 cudaStream_t s);
+                                 cudaStream_t s, long long wait_cycles = 0);
 size_t gram_batch_partials_bytes(int total_slots);
 // One launch for the items of one padded width NP (16, 32, 48 or 64).
 cudaError_t launch_gram_batch(const BatchInst* inst, const BatchGramItem* items, int nitems, int NP, bool vec,

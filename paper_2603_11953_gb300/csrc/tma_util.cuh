@@ -36,9 +36,9 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
-// Wait for the phase with parity `parity` to complete; false when about a
-// second of GPU clock has passed without it.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+// Wait for the phase with parity `parity` to complete; false when `limit`
+// cycles (default about a second of GPU clock) have passed without it.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, long long limit = TMA_WAIT_CYCLES) {
     const long long t0 = clock64();
     for (;;) {
         uint32_t ok;
@@ -49,7 +49,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
             : "r"(smem_addr(bar)), "r"(parity)
             : "memory");
         if (ok) return true;
-        if (clock64() - t0 > TMA_WAIT_CYCLES) return false;
+        if (clock64() - t0 > limit) return false;
     }
 }
 // 2-D tiled TMA load of the box at (x = row, y = column) into dst.

@@ -28,6 +28,8 @@ struct tsvd_ctx {
     void* stage = nullptr;
     size_t stage_bytes = 0;
     cudaEvent_t stage_ev = nullptr;
+    // second stream for small kernels that run beside the main sequence (the kappa(B) estimate)
+    EigSide side{nullptr, nullptr, nullptr};
 };
 
 namespace {
@@ -112,7 +114,8 @@ bool use_fp64_pieces(tsvd_ctx* h, int working, int64_t n) {
 
 tsvd_status run_gram_fp64(tsvd_ctx* h, const void* A, int64_t m, int n, int64_t lda, double* G, double* G_lo,
                           int64_t ldg, size_t part_off) {
-    const GramPlan plan = gram_tc_plan(m, 64, h->sm_count, h->opts.split_k);
+    GramPlan plan = gram_tc_plan(m, 64, h->sm_count, h->opts.split_k);
+    plan.wait_cycles = h->opts.timeout_cycles;
     char* part = base(h) + part_off;
     void* extra = part + align_up(gram_partials_bytes(plan));
     cudaError_t e = launch_fp64_split(static_cast<const double*>(A), m, n, lda, extra, h->dinfo, h->stream);
@@ -153,7 +156,8 @@ tsvd_status run_gram(tsvd_ctx* h, const void* A, int64_t m, int n, int64_t lda, 
     if (tc && n > 64) {
         // 32-column blocks b1 < b2, one launch per pair: the cross tile always, block b1's
         // diagonal tile from the pair (b1, b1 + 1), the last block's from (nb - 2, nb - 1)
-        const GramPlan plan = gram_tc_plan(m, 64, h->sm_count, h->opts.split_k);
+        GramPlan plan = gram_tc_plan(m, 64, h->sm_count, h->opts.split_k);
+        plan.wait_cycles = h->opts.timeout_cycles;
         const int nb = (n + 31) / 32;
         for (int b1 = 0; b1 < nb - 1; ++b1)
             for (int b2 = b1 + 1; b2 < nb; ++b2) {
@@ -166,8 +170,9 @@ tsvd_status run_gram(tsvd_ctx* h, const void* A, int64_t m, int n, int64_t lda, 
             }
         return TSVD_OK;
     }
-    const GramPlan plan = tc ? gram_tc_plan(m, n, h->sm_count, h->opts.split_k)
-                             : gram_plan(m, n, h->sm_count, h->opts.split_k);
+    GramPlan plan = tc ? gram_tc_plan(m, n, h->sm_count, h->opts.split_k)
+                       : gram_plan(m, n, h->sm_count, h->opts.split_k);
+    plan.wait_cycles = h->opts.timeout_cycles;
     e = tc ? launch_gram_tc(A, m, n, lda, plan, base(h) + part_off, h->dinfo, h->stream)
            : launch_gram_ozaki(A, working, m, n, lda, plan, base(h) + part_off, h->dinfo, h->stream);
     if (e != cudaSuccess) return from_cuda(e);
@@ -206,7 +211,7 @@ cudaError_t run_eig(tsvd_ctx* h, const double* M, int n, int64_t ldm, double* sc
                            (h->opts.eig_variant == EIG_DEFAULT && n <= 64);
     if (one_sided)
         return launch_eig_onesided(M, n, ldm, jacobi_tol(h, n), max_sweeps(h), scratch, lam, Vh, h->dinfo,
-                                   h->stream);
+                                   h->stream, &h->side, h->opts.timeout_cycles);
     return launch_jacobi(M, n, ldm, jacobi_tol(h, n), max_sweeps(h), scratch, lam, Vh, h->dinfo, h->stream);
 }
 
@@ -296,7 +301,7 @@ tsvd_status tsvd_create(tsvd_handle* out, int device, void* stream, const tsvd_o
         if (opts->eig_variant < 0 || opts->eig_variant > 2) return TSVD_ERR_UNSUPPORTED;
         if (opts->gram_variant < 0 || opts->gram_variant > 2) return TSVD_ERR_ARG;
         if (opts->u_variant < 0 || opts->u_variant > 1) return TSVD_ERR_ARG;
-        if (opts->timing < 0) return TSVD_ERR_ARG;
+        if (opts->timing < 0 || opts->timeout_cycles < 0) return TSVD_ERR_ARG;
     }
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
@@ -312,6 +317,16 @@ tsvd_status tsvd_create(tsvd_handle* out, int device, void* stream, const tsvd_o
     if (cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
         cudaMalloc(&h->dinfo, sizeof(DevInfo)) != cudaSuccess) {
         cudaGetLastError();
+        delete h;
+        return TSVD_ERR_CUDA;
+    }
+    if (cudaStreamCreateWithFlags(&h->side.stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->side.fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->side.join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        if (h->side.stream) cudaStreamDestroy(h->side.stream);
+        if (h->side.fork) cudaEventDestroy(h->side.fork);
+        cudaFree(h->dinfo);
         delete h;
         return TSVD_ERR_CUDA;
     }
@@ -333,6 +348,9 @@ tsvd_status tsvd_destroy(tsvd_handle h) {
         if (ev) cudaEventDestroy(ev);
     if (h->stage) cudaFreeHost(h->stage);
     if (h->stage_ev) cudaEventDestroy(h->stage_ev);
+    if (h->side.stream) cudaStreamSynchronize(h->side.stream), cudaStreamDestroy(h->side.stream);
+    if (h->side.fork) cudaEventDestroy(h->side.fork);
+    if (h->side.join) cudaEventDestroy(h->side.join);
     delete h;
     return TSVD_OK;
 }
@@ -540,7 +558,7 @@ tsvd_status batch_run(tsvd_ctx* h, int32_t count, const void* const* A, const in
     if (e != cudaSuccess) return from_cuda(e);
     record(h, 0);
     e = launch_gram_tc_batch(reinterpret_cast<const TcBatchItem*>(base(h) + o_tci), (int)tci.size(), part, slots,
-                             dinfos, h->stream);
+                             dinfos, h->stream, h->opts.timeout_cycles);
     if (e != cudaSuccess) return from_cuda(e);
     for (int c = 0; c < 4; ++c) {
         e = launch_gram_batch(dinst, ditems + coff[c], (int)cls[c].size(), 16 * (c + 1), vec[c], part, slots, dinfos,

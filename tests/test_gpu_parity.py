@@ -473,6 +473,68 @@ def test_solve_fp64_with_fp64_stage_and_statuses():
     T.tsvd_destroy(h)
 
 
+# ------------------------------------------------------------------ kappa(B) in tsvd_info
+@pytest.mark.parametrize("m,n,kappa,logd", [(20000, 16, 1e3, 3.0), (9000, 33, 1e2, 2.0), (40000, 64, 1e4, 4.0),
+                                            (5000, 8, 10.0, 1.0)])
+def test_info_kappa_b_estimate(m, n, kappa, logd):
+    """tsvd_info.kappa_B estimates kappa(B) = kappa(C)^(1/2), C = D^-1 M D^-1 the column-scaled exact
+    Gram (A = B D): power and inverse iteration can only under-estimate the extreme eigenvalue
+    ratio, and after their fixed iteration count they are within 20 %."""
+    A, _ = workloads.small_case(m, n, kappa_sigma=kappa, logd=logd, seed=7 * m + n, device="cuda")
+    h = handle()
+    sigma = torch.zeros(n, device="cuda")
+    V = colmajor(n, n, torch.float32)
+    info = torch.zeros(6, dtype=torch.int32, device="cuda")
+    T.tsvd_solve(h, A, m, n, m, T.TSVD_FP32, T.TSVD_FP64, sigma, V, n, None, 0, info)
+    torch.cuda.synchronize()
+    T.tsvd_destroy(h)
+    assert int(info[0].item()) == T.TSVD_OK
+    k_hat = float(info.view(torch.float64)[2].item())
+    S = oracle.gram(workloads.to_numpy_colmajor(A, m))[0]
+    d = np.sqrt(np.diag(S))
+    k_true = math.sqrt(np.linalg.cond(S / np.outer(d, d)))
+    assert 0.8 * k_true <= k_hat <= 1.02 * k_true, (k_hat, k_true)
+
+
+def test_info_kappa_b_rank_deficient_is_infinite():
+    m, n = 3000, 12
+    A, _ = workloads.small_case(m, n, seed=8, device="cuda")
+    A[:, 5] = 0.0
+    h = handle()
+    sigma = torch.zeros(n, device="cuda")
+    V = colmajor(n, n, torch.float32)
+    info = torch.zeros(6, dtype=torch.int32, device="cuda")
+    T.tsvd_solve(h, A, m, n, m, T.TSVD_FP32, T.TSVD_FP64, sigma, V, n, None, 0, info)
+    torch.cuda.synchronize()
+    T.tsvd_destroy(h)
+    assert int(info[0].item()) == T.TSVD_ERR_NOT_FULL_RANK
+    assert math.isinf(float(info.view(torch.float64)[2].item()))
+
+
+# ------------------------------------------------------------------ bounded waits (tsvd_opts.timeout_cycles)
+def test_timeout_option_reports_timeout_and_handle_recovers():
+    """A wait limit far below the time a TMA load or a period drain takes makes the tcgen05 Gram's
+    steady-state waits run out: the kernel records TSVD_ERR_TIMEOUT, drains what it started (those
+    waits keep the default limit), frees its TMEM and returns; the status reaches the host, and the
+    context stays usable (a default handle then gives the exact Gram)."""
+    m, n = 1 << 21, 64
+    A, _ = workloads.small_case(m, n, seed=12, device="cuda")
+    h = handle(timeout_cycles=1)
+    G = torch.zeros(n * n, dtype=torch.float64, device="cuda")
+    T.tsvd_gram(h, A, m, n, m, T.TSVD_FP32, T.TSVD_FP64, G, n)
+    assert T.tsvd_sync_status(h) == T.TSVD_ERR_TIMEOUT
+    T.tsvd_destroy(h)
+    torch.cuda.synchronize()
+    Gh, _, st = gpu_gram(A, 1 << 16, n, m)  # the first 65536 rows (lda = m)
+    assert st == T.TSVD_OK
+    A_np = workloads.to_numpy_colmajor(A, 1 << 16)
+    assert check_gram(A_np, Gh, 1 << 16, n) <= 2.0 ** -50
+    # a negative limit is an argument error
+    opts = T.tsvd_opts(timeout_cycles=-5)
+    _, st = T.tsvd_create(0, None, opts, check=False)
+    assert st == T.TSVD_ERR_ARG
+
+
 # ------------------------------------------------------------------ statuses and arguments
 def test_status_nonfinite_rank_convergence_and_args():
     m, n = 4096, 8
