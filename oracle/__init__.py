@@ -16,6 +16,7 @@ Functions (all matrices column-major, numpy ``order='F'``):
   rows_times(A, W, rows, p)      -> RN_p of exact A[rows] @ W        (Alg. 1 l.6)
   rows_explicit_u(A, V_hi, V_lo, sig_hi, sig_lo, rows) -> exact A V_h / sigma_h (DD)
   round_dd(hi, lo, p)            -> RN_p(hi + lo) by one exact rounding (Alg. 1 l.4-5)
+  alg2(M, working)               -> Algorithm 2: FP64 Cholesky, cast R, SVD of R (sigma, V)
 """
 from __future__ import annotations
 
@@ -67,9 +68,10 @@ def _load():
             lib.oracle_sort_sign.argtypes = [I, P, P, P, P, P, P]
             lib.oracle_svd.argtypes = [P, I64, I64, I64, I, I, D, I, P, P, P, P, P, P, P, P]
             lib.oracle_round_dd.argtypes = [P, P, I64, I, P]
+            lib.oracle_alg2.argtypes = [P, I, I, D, I, P, P, P]
             for f in (lib.oracle_gram, lib.oracle_rows_times, lib.oracle_rows_explicit_u,
                       lib.oracle_jacobi_fp64, lib.oracle_jacobi_dd, lib.oracle_sort_sign,
-                      lib.oracle_svd, lib.oracle_round_dd):
+                      lib.oracle_svd, lib.oracle_round_dd, lib.oracle_alg2):
                 f.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -148,6 +150,25 @@ def round_dd(hi, lo, p):
     if st != OK:
         raise ValueError(f"oracle_round_dd status {st}")
     return out
+
+
+def alg2(M, working=0, tol=None, max_sweeps=100):
+    """Algorithm 2 on M (n x n): FP64 Cholesky M = R^T R, R cast to the working precision
+    (working 0: FP32, 1: FP64), SVD of that R to FP64 accuracy.  Returns dict(sigma, V, status,
+    sweeps), sigma descending, V with the sign rule.  tol defaults to n 2^-53: a one-sided Jacobi
+    recomputes x_p^T x_q from the columns, whose rounding (~sqrt(n) 2^-53 of ||x_p|| ||x_q||)
+    a smaller skip threshold could never get below."""
+    lib = _load()
+    M = np.array(M, dtype=np.float64, order="F", copy=True)
+    n = M.shape[0]
+    if tol is None:
+        tol = n * U_H_FP64
+    sig = np.zeros(n)
+    V = np.zeros((n, n), order="F")
+    sw = ctypes.c_int(0)
+    st = lib.oracle_alg2(_ptr(M), n, int(working), float(tol), int(max_sweeps), _ptr(sig), _ptr(V),
+                         ctypes.byref(sw))
+    return dict(sigma=sig, V=V, status=st, sweeps=sw.value)
 
 
 def jacobi_fp64(M, tol=U_H_FP64, max_sweeps=100):

@@ -601,3 +601,90 @@ int oracle_svd(const void* A, int64_t m, int64_t n, int64_t lda, int working, in
     free(Gh); free(Gl); free(lh); free(ll); free(Vh); free(Vl);
     return st;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Algorithm 2 (the mixed precision eigensolver for the Gram matrix), in the  */
+/* paper's order, on a given M_h (n x n, column-major, ld n):                 */
+/*   line 1  Cholesky M_h = R_h^T R_h at the higher precision (FP64; R_h upper */
+/*           triangular, no pivoting: the algorithm names none);              */
+/*   line 2  R = RN_w(R_h), the working precision (FP32 for working = 0);     */
+/*   line 3  SVD of R: R = U_R Sigma V^T, so that M_h ~= V Sigma^2 V^T.  The   */
+/*           oracle takes this SVD of the working-precision R to FP64         */
+/*           accuracy: one-sided cyclic Jacobi (row-cyclic pairs, the scaled   */
+/*           skip test with tol >= n 2^-53, the rounding level of a recomputed  */
+/*           x_p^T x_q; Rutishauser's rotation) on the columns of R^T, whose   */
+/*           final normalised columns are the right singular vectors V of R   */
+/*           (R^T J = W Sigma gives R = J Sigma W^T).                         */
+/* Outputs sigma (descending) and V (sign rule) in FP64.  Returns ORC_OK,     */
+/* ORC_NOT_FULL_RANK (a non-positive Cholesky pivot) or ORC_NO_CONVERGENCE.   */
+/* ------------------------------------------------------------------------- */
+int oracle_alg2(const double* M, int n, int working, double tol, int max_sweeps, double* sigma, double* V,
+                int* sweeps_out) {
+    if (!M || !sigma || !V || n < 1 || max_sweeps < 1 || (working != 0 && working != 1)) return ORC_BAD_ARG;
+    double* Rm = (double*)calloc((size_t)n * n, sizeof(double)); /* R, column-major: R[i + j n], i <= j */
+    double* X = (double*)malloc(sizeof(double) * (size_t)n * n);  /* X = R^T, column c = row c of R */
+    double* lam = (double*)malloc(sizeof(double) * n);
+    if (!Rm || !X || !lam) { free(Rm); free(X); free(lam); return ORC_BAD_ARG; }
+    int status = ORC_OK;
+    /* line 1: r_jj = sqrt(m_jj - sum_k r_kj^2), r_ji = (m_ji - sum_k r_kj r_ki) / r_jj (i > j) */
+    for (int j = 0; j < n && status == ORC_OK; ++j) {
+        double d = M[j + (size_t)j * n];
+        for (int k = 0; k < j; ++k) d -= Rm[k + (size_t)j * n] * Rm[k + (size_t)j * n];
+        if (!(d > 0.0)) { status = ORC_NOT_FULL_RANK; break; }
+        const double rjj = sqrt(d);
+        Rm[j + (size_t)j * n] = rjj;
+        for (int i = j + 1; i < n; ++i) {
+            double s = M[j + (size_t)i * n];
+            for (int k = 0; k < j; ++k) s -= Rm[k + (size_t)j * n] * Rm[k + (size_t)i * n];
+            Rm[j + (size_t)i * n] = s / rjj;
+        }
+    }
+    int sweep = 0, converged = 0;
+    if (status == ORC_OK) {
+        /* line 2: the cast; X = R^T */
+        for (int c = 0; c < n; ++c)
+            for (int r = 0; r < n; ++r) {
+                const double v = Rm[c + (size_t)r * n];
+                X[r + (size_t)c * n] = working == 0 ? (double)(float)v : v;
+            }
+        /* line 3: one-sided Jacobi on the columns of X */
+        while (sweep < max_sweeps) {
+            ++sweep;
+            int rotations = 0;
+            for (int p = 0; p < n - 1; ++p)
+                for (int q = p + 1; q < n; ++q) {
+                    double* xp = X + (size_t)p * n;
+                    double* xq = X + (size_t)q * n;
+                    double g = 0.0, a = 0.0, b = 0.0;
+                    for (int r = 0; r < n; ++r) { g += xp[r] * xq[r]; a += xp[r] * xp[r]; b += xq[r] * xq[r]; }
+                    if (g == 0.0 || fabs(g) <= tol * sqrt(a * b)) continue;
+                    const double zeta = (b - a) / (2.0 * g);
+                    const double sg = zeta >= 0.0 ? 1.0 : -1.0;
+                    const double t = sg / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                    const double cs = 1.0 / sqrt(1.0 + t * t), sn = t * cs;
+                    for (int r = 0; r < n; ++r) {
+                        const double u = xp[r], v = xq[r];
+                        xp[r] = cs * u - sn * v;
+                        xq[r] = sn * u + cs * v;
+                    }
+                    ++rotations;
+                }
+            if (rotations == 0) { converged = 1; break; }
+        }
+        for (int j = 0; j < n; ++j) {
+            double s2 = 0.0;
+            for (int r = 0; r < n; ++r) s2 += X[r + (size_t)j * n] * X[r + (size_t)j * n];
+            lam[j] = s2;
+            const double inv = s2 > 0.0 ? 1.0 / sqrt(s2) : 0.0;
+            for (int r = 0; r < n; ++r) V[r + (size_t)j * n] = X[r + (size_t)j * n] * inv;
+        }
+        int st2 = oracle_sort_sign(n, lam, NULL, V, NULL, sigma, NULL);
+        if (st2 != ORC_OK) status = st2;
+        if (status == ORC_OK && !converged) status = ORC_NO_CONVERGENCE;
+    }
+    if (sweeps_out) *sweeps_out = sweep;
+    free(Rm);
+    free(X);
+    free(lam);
+    return status;
+}

@@ -364,3 +364,49 @@ def test_dd_jacobi_graded_relative_accuracy():
     # the FP64 n x n stage on the same exact Gram loses ~u kappa(B)^2 on the smallest sigma
     res1 = oracle.svd(A, higher=1)
     assert float(abs(sympy.Float(res1["sigma_h"][n - 1], 50) - exact[n - 1]) / exact[n - 1]) > 1e-15
+
+
+# ---------------------------------------------------------------- Algorithm 2 (Cholesky, cast, SVD of R)
+def test_alg2_exact_factor_matches_lapack_svd():
+    """M = R0^T R0 with a small-integer upper triangular R0: every step of the FP64 Cholesky is
+    exact, so R = R0 (FP32-exact, the cast changes nothing) and Algorithm 2's sigma and V are the
+    singular values and right singular vectors of R0, checked against LAPACK's SVD."""
+    rng = np.random.default_rng(1)
+    n = 7
+    R0 = np.triu(rng.integers(-5, 6, (n, n)).astype(float))
+    np.fill_diagonal(R0, np.arange(3, 3 + n))
+    M = R0.T @ R0
+    res = oracle.alg2(M, working=0)
+    assert res["status"] == 0
+    _, s, Vt = np.linalg.svd(R0)
+    np.testing.assert_allclose(res["sigma"], s, rtol=1e-14)
+    for j in range(n):  # same subspace, sign fixed by the sign rule
+        v = Vt[j] * np.sign(Vt[j][np.argmax(np.abs(Vt[j]))])
+        np.testing.assert_allclose(res["V"][:, j], v, atol=1e-13)
+    # M V = V diag(sigma^2): the eigen-decomposition of M the algorithm promises
+    np.testing.assert_allclose(M @ res["V"], res["V"] * res["sigma"] ** 2, atol=1e-11 * s[0] ** 2)
+
+
+def test_alg2_casts_r_to_working_precision():
+    """Line 2 of Algorithm 2 rounds R_h to the working precision: for FP32 working, sigma is the
+    SVD of fl32(R_h) (LAPACK on the rounded factor), not of R_h itself; for FP64 working the cast
+    is the identity and sigma^2 are the eigenvalues of M."""
+    rng = np.random.default_rng(5)
+    n = 9
+    B = rng.standard_normal((40, n)) * np.exp2(rng.integers(-6, 6, n))
+    M = B.T @ B
+    Rh = np.linalg.cholesky(M).T
+    s32 = np.linalg.svd(Rh.astype(np.float32).astype(np.float64), compute_uv=False)
+    s64 = np.linalg.svd(Rh, compute_uv=False)
+    res = oracle.alg2(M, working=0)
+    assert res["status"] == 0
+    np.testing.assert_allclose(res["sigma"], s32, rtol=1e-12)
+    assert np.max(np.abs(res["sigma"] - s64) / s64) > 1e-10  # the cast is really applied
+    res64 = oracle.alg2(M, working=1)
+    lam = np.sort(np.linalg.eigvalsh(M))[::-1]  # LAPACK: absolute accuracy ~ n u lambda_max
+    np.testing.assert_allclose(res64["sigma"] ** 2, lam, rtol=1e-12, atol=64 * 2.0 ** -53 * lam[0])
+
+
+def test_alg2_not_positive_definite():
+    M = np.array([[4.0, 2.0, 0.0], [2.0, 1.0, 0.0], [0.0, 0.0, 3.0]])  # rank 2 block
+    assert oracle.alg2(M)["status"] == oracle.NOT_FULL_RANK
