@@ -14,6 +14,8 @@
 //   4  BF16 mma.sync m16n8k16 -> f32      4096 flops per warp-op
 //   5  dependent FP64 fma latency (one thread): cycles per operation in *ops
 //   6  dependent FP32 fma latency (one thread): cycles per operation in *ops
+//   7, 8, 9  FP64 fma stream with only 1, 8 or 16 lanes of each warp active
+//            (does the narrow FP64 pipe charge for idle lanes?)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -40,6 +42,23 @@ __global__ void __launch_bounds__(kThreads) fp64_fma_kernel(double* out, int ite
 #pragma unroll
     for (int k = 0; k < 8; ++k) s += x[k];
     if (s == 123.456) out[blockIdx.x] = s;  // never true: keeps the chains alive
+}
+
+// kind 0 with only the first `active` lanes of every warp doing the work
+__global__ void __launch_bounds__(kThreads) fp64_fma_partial_kernel(double* out, int iters, double a, double b,
+                                                                    int active) {
+    if ((threadIdx.x & 31) >= active) return;
+    double x[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = threadIdx.x * 1e-3 + k;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = fma(x[k], a, b);
+    }
+    double s = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += x[k];
+    if (s == 123.456) out[blockIdx.x] = s;
 }
 
 __global__ void __launch_bounds__(kThreads) fp32_fma_kernel(float* out, int iters, float a, float b) {
@@ -186,6 +205,12 @@ extern "C" PROBE_API int tsvd_probe(int kind, int iters, double* ops, float* ms)
             case 4: bf16_mma_kernel<<<grid, kThreads>>>((float*)buf, iters); count = lanes / 32 * iters * 4 * 4096.0; break;
             case 5: fp64_latency_kernel<<<1, 1>>>((double*)buf, cyc, iters, 0.999999, 1e-6); break;
             case 6: fp32_latency_kernel<<<1, 1>>>((float*)buf, cyc, iters, 0.9999f, 1e-4f); break;
+            case 7: case 8: case 9: {
+                const int act = kind == 7 ? 1 : kind == 8 ? 8 : 16;
+                fp64_fma_partial_kernel<<<grid, kThreads>>>((double*)buf, iters, 0.999999, 1e-6, act);
+                count = lanes / 32 * act * iters * 8 * 2;
+                break;
+            }
             default: rep = 2; e = cudaErrorInvalidValue; break;
         }
         cudaEventRecord(e1);

@@ -17,7 +17,8 @@ import os
 from . import build as _build
 
 KINDS = {"fp64_fma": 0, "fp32_fma": 1, "fp32x2_fma": 2, "int8_mma_sync": 3, "bf16_mma_sync": 4,
-         "fp64_latency": 5, "fp32_latency": 6}
+         "fp64_latency": 5, "fp32_latency": 6, "fp64_fma_1lane": 7, "fp64_fma_8lanes": 8,
+         "fp64_fma_16lanes": 9}
 
 
 def _lib():
@@ -73,7 +74,10 @@ def measure(library_gemms: bool = True) -> dict:
     for name, iters, unit, scale in (("fp64_fma", 2000, "fp64_gflops", 1e9), ("fp32_fma", 20000, "fp32_tflops", 1e12),
                                      ("fp32x2_fma", 20000, "fp32x2_tflops", 1e12),
                                      ("int8_mma_sync", 4000, "int8_mma_sync_tops", 1e12),
-                                     ("bf16_mma_sync", 4000, "bf16_mma_sync_tflops", 1e12)):
+                                     ("bf16_mma_sync", 4000, "bf16_mma_sync_tflops", 1e12),
+                                     ("fp64_fma_1lane", 2000, "fp64_1lane_gflops", 1e9),
+                                     ("fp64_fma_8lanes", 2000, "fp64_8lanes_gflops", 1e9),
+                                     ("fp64_fma_16lanes", 2000, "fp64_16lanes_gflops", 1e9)):
         ops, ms = probe(name, iters)
         res[unit] = ops / (ms * 1e-3) / scale
     res["fp64_fma_latency_cycles"] = probe("fp64_latency", 100000)[0]
