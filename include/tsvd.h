@@ -79,7 +79,12 @@ typedef struct {
     int max_sweeps;        /* Jacobi sweep limit (default 40) */
     int eig_variant;       /* 0 = default (2 for n <= 64, else 1); 1 = two-sided
                               Jacobi on M_h (Sec. 2.1); 2 = pivoted Cholesky of M_h
-                              + one-sided Jacobi on R^T, both in FP64 (n <= 64) */
+                              + one-sided Jacobi on R^T, both in FP64 (n <= 64);
+                              3 = Algorithm 2 as the paper writes it: plain FP64
+                              Cholesky M_h = R_h^T R_h, R = RN_32(R_h), SVD of R in
+                              FP32 by one-sided Jacobi (skip threshold n 2^-24 unless
+                              jacobi_tol is set); FP32 working, n <= 64; accuracy
+                              O(u) kappa(B) + O(u_h) kappa(B)^2 (Remark 2) */
     int autotune;          /* reserved (0) */
     long long timeout_cycles; /* limit, in GPU clock cycles, of each steady-state mbarrier
                                  wait of the tcgen05 Gram kernel and of the cluster Jacobi

@@ -612,9 +612,11 @@ int oracle_svd(const void* A, int64_t m, int64_t n, int64_t lda, int working, in
 /*           oracle takes this SVD of the working-precision R to FP64         */
 /*           accuracy: one-sided cyclic Jacobi (row-cyclic pairs, the scaled   */
 /*           skip test with tol >= n 2^-53, the rounding level of a recomputed  */
-/*           x_p^T x_q; Rutishauser's rotation) on the columns of R^T, whose   */
-/*           final normalised columns are the right singular vectors V of R   */
-/*           (R^T J = W Sigma gives R = J Sigma W^T).                         */
+/*           x_p^T x_q; Rutishauser's rotation) on the columns of R, with the  */
+/*           rotations accumulated: R J = U_R Sigma, V = J.  The columns of R  */
+/*           carry the column scaling D of A = B D (R = R_C D with R_C^T R_C  */
+/*           = C), which one-sided Jacobi on columns resolves to relative       */
+/*           accuracy.                                                        */
 /* Outputs sigma (descending) and V (sign rule) in FP64.  Returns ORC_OK,     */
 /* ORC_NOT_FULL_RANK (a non-positive Cholesky pivot) or ORC_NO_CONVERGENCE.   */
 /* ------------------------------------------------------------------------- */
@@ -622,7 +624,7 @@ int oracle_alg2(const double* M, int n, int working, double tol, int max_sweeps,
                 int* sweeps_out) {
     if (!M || !sigma || !V || n < 1 || max_sweeps < 1 || (working != 0 && working != 1)) return ORC_BAD_ARG;
     double* Rm = (double*)calloc((size_t)n * n, sizeof(double)); /* R, column-major: R[i + j n], i <= j */
-    double* X = (double*)malloc(sizeof(double) * (size_t)n * n);  /* X = R^T, column c = row c of R */
+    double* X = (double*)malloc(sizeof(double) * (size_t)n * n);  /* X = R (cast), then R J */
     double* lam = (double*)malloc(sizeof(double) * n);
     if (!Rm || !X || !lam) { free(Rm); free(X); free(lam); return ORC_BAD_ARG; }
     int status = ORC_OK;
@@ -641,13 +643,14 @@ int oracle_alg2(const double* M, int n, int working, double tol, int max_sweeps,
     }
     int sweep = 0, converged = 0;
     if (status == ORC_OK) {
-        /* line 2: the cast; X = R^T */
+        /* line 2: the cast; X = R, V = I */
         for (int c = 0; c < n; ++c)
             for (int r = 0; r < n; ++r) {
-                const double v = Rm[c + (size_t)r * n];
+                const double v = Rm[r + (size_t)c * n];
                 X[r + (size_t)c * n] = working == 0 ? (double)(float)v : v;
+                V[r + (size_t)c * n] = r == c ? 1.0 : 0.0;
             }
-        /* line 3: one-sided Jacobi on the columns of X */
+        /* line 3: one-sided Jacobi on the columns of X, V <- V J */
         while (sweep < max_sweeps) {
             ++sweep;
             int rotations = 0;
@@ -662,10 +665,15 @@ int oracle_alg2(const double* M, int n, int working, double tol, int max_sweeps,
                     const double sg = zeta >= 0.0 ? 1.0 : -1.0;
                     const double t = sg / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
                     const double cs = 1.0 / sqrt(1.0 + t * t), sn = t * cs;
+                    double* vp = V + (size_t)p * n;
+                    double* vq = V + (size_t)q * n;
                     for (int r = 0; r < n; ++r) {
                         const double u = xp[r], v = xq[r];
                         xp[r] = cs * u - sn * v;
                         xq[r] = sn * u + cs * v;
+                        const double s_ = vp[r], t_ = vq[r];
+                        vp[r] = cs * s_ - sn * t_;
+                        vq[r] = sn * s_ + cs * t_;
                     }
                     ++rotations;
                 }
@@ -675,8 +683,6 @@ int oracle_alg2(const double* M, int n, int working, double tol, int max_sweeps,
             double s2 = 0.0;
             for (int r = 0; r < n; ++r) s2 += X[r + (size_t)j * n] * X[r + (size_t)j * n];
             lam[j] = s2;
-            const double inv = s2 > 0.0 ? 1.0 / sqrt(s2) : 0.0;
-            for (int r = 0; r < n; ++r) V[r + (size_t)j * n] = X[r + (size_t)j * n] * inv;
         }
         int st2 = oracle_sort_sign(n, lam, NULL, V, NULL, sigma, NULL);
         if (st2 != ORC_OK) status = st2;

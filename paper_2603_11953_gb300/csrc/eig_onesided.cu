@@ -22,20 +22,20 @@
 // instruction per ~64 cycles per SM sub-partition whatever the number of
 // active lanes, with a dependent latency of ~64 cycles; FP32 is ~60x faster.
 // So (i) the pairs are spread over the 16 SMs of a (non-portable) cluster,
-// two per SM, and each pair over two warps on different sub-partitions (32
-// rows each): a warp issues 1 FP64 multiply for its dot product, 5 + 1 adds
-// to reduce it, ~8 scalar operations for the rotation and the norms, and 4
-// for its half of the rotation; (ii) the angle, the scaled test and the
-// conversions run on the FP32 and integer pipes; (iii) a column that leaves
-// an SM is stored straight from registers into the neighbour's shared
-// memory (st.shared::cluster), into a ring of receive buffers that
-// the tournament maps in place, and signalled on the neighbour's mbarrier
-// (release / acquire at cluster scope): no copy, no cluster-wide barrier
-// within a sweep.
+// two per SM, one warp per pair, and a warp issues only the FP64
+// instructions that carry the result: 2 for its part of x_p^T x_q, 1 for the
+// norm difference, 8 for the rotation, 3 for the norm updates; (ii) the
+// reduction of the dot product (exact 64-bit fixed point), the angle (FP32),
+// the scaled test and the orthogonality correction (integer arithmetic) run
+// on the integer and FP32 pipes; (iii) a column that leaves an SM is written
+// straight from registers into the neighbour's shared memory by st.async,
+// into a ring of receive buffers that the tournament maps in place, each
+// store completing a transaction on the neighbour's mbarrier: no copy, no
+// fence, no cluster-wide barrier within a sweep.
 //
 // The rotation angle and (c0, s0) are computed in FP32 while the applied
-// rotation is made orthogonal to FP64 precision by one FP64 correction
-// factor: an inexact angle only leaves a residual g * O(2^-24) on a pair,
+// rotation is made orthogonal to FP64 precision by one correction factor:
+// an inexact angle only leaves a residual g * O(2^-24) on a pair,
 // which later sweeps remove, whereas a non-orthogonal rotation would change
 // the singular values.  Squared norms are updated within a sweep by the exact
 // quadratic form of the rotation, recomputed at the start of every sweep and
@@ -64,14 +64,16 @@ namespace {
 // is kept by original index and only its lower triangle (row index >= column index,
 // original order) is stored and updated: half the FP64 work of a full update, and no
 // rows or columns are swapped.  The remaining indices are a bit mask; their ascending
-// list turns the triangle into contiguous work for the warps.
+// list turns the triangle into contiguous work for the warps.  pivot = 0 takes the
+// lowest remaining index instead (the plain Cholesky factorization M_h = R_h^T R_h that
+// Algorithm 2 names); it fails, like the pivoted one, at a non-positive diagonal.
 __device__ __forceinline__ double chol_S(const double* sa, int n, int x, int y) {
     return x >= y ? sa[x + (size_t)y * n] : sa[y + (size_t)x * n];
 }
 
 __global__ void __launch_bounds__(256)
     chol_piv_kernel(const double* __restrict__ M, int n, int64_t ldm, double* __restrict__ X,
-                    int* __restrict__ perm_out, DevInfo* info) {
+                    int* __restrict__ perm_out, DevInfo* info, int pivot) {
     extern __shared__ double sa[];    // [n][n] Schur complement, lower triangle by original index
     double* Rr = sa + (size_t)n * n;  // [n][n]: row k of R by original column index
     __shared__ int s_list[64];        // remaining original indices, ascending
@@ -103,7 +105,7 @@ __global__ void __launch_bounds__(256)
             const int oo = __shfl_xor_sync(0xffffffffu, bo, off);
             if (ob > best || (ob == best && oo < bo)) { best = ob; bo = oo; }
         }
-        const int ok = bo;
+        const int ok = pivot ? bo : __ffsll((long long)rem) - 1;
         const double d = sa[ok + (size_t)ok * n];
         if (!(d > 0.0)) { deficient = true; kend = k; break; }
         const unsigned long long rn = rem & ~(1ull << ok);
@@ -160,7 +162,6 @@ struct OsParams {
     int n;            // true size
     int np;           // padded column count (multiple of 4 * clusterSize)
     int P;            // pairs per CTA (2 <= P <= 8)
-    int H;            // warps per pair: 2 (rows 0..31 and 32..63) for n > 32, else 1
     double tol;
     int max_sweeps;
     long long wait_limit;
@@ -201,14 +202,6 @@ __device__ __forceinline__ uint32_t os_mapa(const void* local, int rank) {
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(raddr) : "r"(os_smem(local)), "r"(rank));
     return raddr;
 }
-// store into another CTA's shared memory (address from os_mapa)
-__device__ __forceinline__ void os_st_remote(uint32_t raddr, double v) {
-    asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(raddr), "d"(v) : "memory");
-}
-// arrive on another CTA's mbarrier; release at cluster scope orders this thread's stores before it
-__device__ __forceinline__ void os_arrive_remote(uint32_t rbar) {
-    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(rbar) : "memory");
-}
 // bounded wait with cluster-scope acquire
 __device__ __forceinline__ bool os_wait(const uint64_t* bar, unsigned parity, long long limit) {
     const long long t0 = clock64();
@@ -224,32 +217,92 @@ __device__ __forceinline__ bool os_wait(const uint64_t* bar, unsigned parity, lo
         if (clock64() - t0 > limit) return false;
     }
 }
-__device__ __forceinline__ void os_bar(int id, int count) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory"); }
+// st.async into another CTA's shared memory: the write completes an 8-byte transaction on that
+// CTA's mbarrier (no release fence on the sender; the receiver's acquire sees the data)
+__device__ __forceinline__ void os_st_async(uint32_t raddr, double v, uint32_t rbar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b64 [%0], %1, [%2];" ::"r"(raddr),
+                 "l"(__double_as_longlong(v)), "r"(rbar)
+                 : "memory");
+}
+// one arrival on this CTA's mbarrier that expects `bytes` more for the phase
+__device__ __forceinline__ void os_arm(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(os_smem(bar)), "r"(bytes) : "memory");
+}
+// X 2^k (X unsigned), rounded to nearest even, as a double (normal range assumed)
+__device__ __forceinline__ double os_u64_to_double(unsigned long long X, int k, bool neg) {
+    if (X == 0ull) return 0.0;
+    const int lz = __clzll((long long)X);
+    const unsigned long long a = X << lz;
+    unsigned long long m = a >> 11;
+    const unsigned long long rest = a & 0x7ffull;
+    if (rest > 0x400ull || (rest == 0x400ull && (m & 1ull))) ++m;
+    int e = 63 - lz + k;  // exponent of the leading bit
+    if (m >> 53) { m >>= 1; ++e; }
+    return __longlong_as_double((long long)((neg ? (1ull << 63) : 0ull) | ((unsigned long long)(e + 1023) << 52) |
+                                            (m & 0xfffffffffffffull)));
+}
+// x as a signed fixed-point integer in units 2^(S - 62), truncated toward zero; requires |x| < 2^S
+// (then the magnitude stays below 2^62)
+__device__ __forceinline__ long long os_to_fixed(double x, int S) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int ex = (int)((b >> 52) & 0x7ff);
+    if (ex == 0) return 0;
+    const unsigned long long mant = (b & 0xfffffffffffffull) | (1ull << 52);  // x = mant 2^(ex - 1075)
+    const int sh = ex - 1075 - (S - 62);
+    const long long v = sh >= 0 ? (long long)(mant << sh) : (sh <= -64 ? 0ll : (long long)(mant >> (-sh)));
+    return (b >> 63) ? -v : v;
+}
+// (cs, sn) = (c0, s0) (c0^2 + s0^2)^(-1/2) to FP64 precision, from FP32 c0 in (1/2, 1] and
+// |s0| < 1, on the integer pipes: e = c0^2 + s0^2 - 1 exactly in units 2^-62 (the 24-bit
+// significands squared), f = 1 - e/2 + 3e^2/8 (error O(e^3), |e| ~ 2^-24), then the products
+// with f rounded once to FP64.
+__device__ __forceinline__ void os_orthogonal(float c0, float s0, double& cs, double& sn) {
+    const unsigned cb = __float_as_uint(c0), sb = __float_as_uint(s0);
+    const int ec = (int)((cb >> 23) & 0xff), es = (int)((sb >> 23) & 0xff);
+    const unsigned long long Cm = (cb & 0x7fffffu) | 0x800000u;
+    const unsigned long long Sm = es ? ((sb & 0x7fffffu) | 0x800000u) : 0ull;
+    const int shc = 2 * ec - 238, shs = 2 * es - 238;  // c0^2 = Cm^2 2^(shc - 62)
+    const long long C2 = (long long)(shc >= 0 ? (Cm * Cm) << shc : (Cm * Cm) >> (-shc));
+    const long long S2 = (long long)(shs >= 0 ? (Sm * Sm) << shs : (shs <= -64 ? 0ull : (Sm * Sm) >> (-shs)));
+    const long long E = C2 + S2 - (1ll << 62);
+    const unsigned long long aE = (unsigned long long)(E < 0 ? -E : E);
+    const unsigned long long F = (1ull << 62) - (unsigned long long)(E >> 1) + ((3ull * __umul64hi(aE, aE)) >> 1);
+    cs = os_u64_to_double(__umul64hi(Cm << 40, F), ec - 188, false);
+    sn = os_u64_to_double(__umul64hi(Sm << 40, F), es - 188, (sb >> 31) != 0);
+}
 
 // Column slots of a CTA: top[u] and bot[u] (u < P) hold the two columns of pair u.  A
 // slot maps to one of the CTA's buffers: 2P local ones (the initial columns), then a ring
-// of D buffers for columns arriving from the left neighbour and one for columns
-// from the right.  In the circle tournament, per step, the top row moves right and the
-// bottom row left: top[P-1] leaves to the right neighbour's top[0], bot[0] to the left
-// neighbour's bot[P-1]; the first CTA keeps top[0] and moves bot[0] to top[1], the last
-// moves top[P-1] to bot[P-1].  A received column stays at most 2P steps in a CTA (the
-// last CTA passes it through its top and its bottom row).  A neighbour stores into ring
-// slot K mod D at step K only after it has received this CTA's column of step K - 1,
-// which was sent after this CTA's barrier of step K - 2: so a ring of D = 2P + 2 buffers
-// per side keeps every store causally after the last read of the column it overwrites.
+// of D buffers for columns arriving from the left neighbour and one for columns from the
+// right.  In the circle tournament, per step, the top row moves right and the bottom row
+// left: top[P-1] leaves to the right neighbour's top[0], bot[0] to the left neighbour's
+// bot[P-1]; the first CTA keeps top[0] and moves bot[0] to top[1], the last moves top[P-1]
+// to bot[P-1].  A received column stays at most 2P steps in a CTA (the last CTA passes it
+// through its top and its bottom row).  A neighbour stores into ring slot K mod D at step K
+// only after it has received this CTA's column of step K - 1, which was sent after this
+// CTA's barrier of step K - 2: so a ring of D = 2P + 2 buffers per side keeps every store
+// causally after the last read of the column it overwrites.
+//
+// One warp per pair, lane l holding rows l and l + 32.  Per step a warp issues 14 FP64
+// instructions: 2 for its part of g = x_p^T x_q, 1 for a_qq - a_pp, 8 for the rotation, 3
+// for the norm updates.  The reduction of g is an exact sum of 64-bit fixed-point integers
+// (units 2^(S - 62), 2^S above ||x_p|| ||x_q|| from the exponents of the norms) on the
+// integer pipes, the angle is FP32, and the orthogonality correction of (c0, s0) is integer
+// arithmetic (os_orthogonal).  A leaving column is written from registers with st.async
+// into the neighbour's ring buffer, each 8-byte store completing a transaction on the
+// neighbour's mbarrier, which its owner arms (one arrival expecting a column's bytes) for
+// every use.
 __global__ void __launch_bounds__(512) onesided_jacobi_kernel(OsParams prm) {
     cg::cluster_group cluster = cg::this_cluster();
     const int C = (int)cluster.num_blocks();
     const int c = (int)cluster.block_rank();
-    const int n = prm.n, np = prm.np, P = prm.P, H = prm.H;
-    extern __shared__ __align__(16) double sm[];
+    const int n = prm.n, np = prm.np, P = prm.P;
     const int D = 2 * P + 2;  // receive ring depth per side
+    extern __shared__ __align__(16) double sm[];
     double* bufs = sm;  // [2P + 2D][OS_LD]
     const int RL0 = 2 * P, RR0 = 2 * P + D;
     __shared__ uint64_t rbar[2][OS_MAXRING];  // [0]: from the left, [1]: from the right
     __shared__ int map_top[2][OS_MAXP], map_bot[2][OS_MAXP];  // slot -> buffer, by step parity
-    __shared__ double red[2][OS_MAXP][2];   // per step parity, pair, half: dot products
-    __shared__ double red2[OS_MAXP][2][2];  // norm recomputation: pair, half, column
     __shared__ int s_rot;
     __shared__ int s_cnt[2];                // used in CTA 0: per-sweep cluster totals
     __shared__ int s_total;
@@ -263,18 +316,20 @@ __global__ void __launch_bounds__(512) onesided_jacobi_kernel(OsParams prm) {
     __shared__ float s_off_cta;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nwarps = (int)(blockDim.x >> 5);
-    const int a = warp % P, h = warp / P;  // pair and row half of this warp
-    const int e = 32 * h + lane;           // this lane's row
-    const int R = 32 * H;                  // rows held per column
     const int N = np - 1;
     const double tol2 = prm.tol * prm.tol;
     const float tol_f = (float)prm.tol;
+    const unsigned colbytes = (unsigned)(sizeof(double) * OS_LD);
 
     if (tid == 0) {
         for (int s = 0; s < 2; ++s)
-            for (int r = 0; r < D; ++r)
-                asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(os_smem(&rbar[s][r])), "r"(32 * H));
+            for (int r = 0; r < D; ++r) {
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(os_smem(&rbar[s][r])));
+            }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        // the first use of every ring slot expects one column
+        for (int s = 0; s < 2; ++s)
+            for (int r = 0; r < D; ++r) os_arm(&rbar[s][r], colbytes);
         s_cnt[0] = s_cnt[1] = 0;
         s_mx[0] = s_mx[1] = 0;
         s_fail[0] = s_fail[1] = 0;
@@ -300,7 +355,7 @@ __global__ void __launch_bounds__(512) onesided_jacobi_kernel(OsParams prm) {
     bool converged = false;
     unsigned K = 0;  // global step counter: map parity, ring slot, mbarrier phase
     float best_off = 0.0f;
-    float sweep_mx = 0.0f;  // lane 0 of a pair warp: the largest scaled |g| met in the sweep
+    float sweep_mx = 0.0f;  // the largest scaled |g| met in the sweep
     int checks = 0;
     bool timed_out = false;
     while (sweep < prm.max_sweeps) {
@@ -312,9 +367,7 @@ __global__ void __launch_bounds__(512) onesided_jacobi_kernel(OsParams prm) {
             const int par = (int)(K & 1u);
             for (int u = warp; u < 2 * P; u += nwarps) {
                 double* b = bufs + (size_t)(u < P ? map_top[par][u] : map_bot[par][u - P]) * OS_LD;
-                double s2 = 0.0;
-                for (int r = lane; r < R; r += 32) s2 = fma(b[r], b[r], s2);
-                s2 = warp_sum(s2);
+                double s2 = warp_sum(fma(b[lane], b[lane], b[lane + 32] * b[lane + 32]));
                 if (lane == 0) b[64] = s2;
             }
         }
@@ -323,120 +376,117 @@ __global__ void __launch_bounds__(512) onesided_jacobi_kernel(OsParams prm) {
             const int par = (int)(K & 1u);
             const int ring = (int)(K % (unsigned)D);
             const unsigned phase = (K / (unsigned)D) & 1u;
-            double* xp = bufs + (size_t)map_top[par][a] * OS_LD;
-            double* xq = bufs + (size_t)map_bot[par][a] * OS_LD;
-            const double va = xp[e], vb = xq[e];
-            const double app = xp[64], aqq = xq[64];
-            const long long idp = __double_as_longlong(xp[65]), idq = __double_as_longlong(xq[65]);
-            // g = x_p^T x_q over both halves (the same sum in the same order in both warps)
-            double g = warp_sum(va * vb);
-            if (H == 2) {
-                if (lane == 0) red[par][a][h] = g;
-                os_bar(1 + a, 64);
-                g = red[par][a][0] + red[par][a][1];
-            }
-            // column ids are integer bit patterns; positive doubles have positive patterns
-            // (integer compares keep these tests off the FP64 pipe)
-            const bool live = idp < n && idq < n && __double_as_longlong(app) > 0 && __double_as_longlong(aqq) > 0;
-            // the scaled test |g| > tol sqrt(a_pp a_qq): decided in FP32 when the FP32 ratio
-            // is clearly on one side (factor 2), exactly in FP64 otherwise
-            bool rot = false;
-            float rr = 0.0f;
-            bool in_range = false;
-            if (live && g != 0.0) {
-                const float gf = fabsf(os_to_float(g)), af = os_to_float(app), bf = os_to_float(aqq);
-                in_range = af > 1e-30f && af < 1e30f && bf > 1e-30f && bf < 1e30f && gf > 1e-30f && gf < 1e30f;
-                rr = in_range ? gf * rsqrtf(af) * rsqrtf(bf) : 0.0f;
-                if (in_range && rr > 2.0f * tol_f) rot = true;
-                else if (!in_range || rr > 0.5f * tol_f) rot = g * g > tol2 * (app * aqq);
-                if (!rot) best_off = fmaxf(best_off, rr);
-                sweep_mx = fmaxf(sweep_mx, in_range ? rr : (rot ? 1.0f : 0.0f));
-            }
-            double na = va, nb = vb, np2 = app, nq2 = aqq;
-            if (rot) {
-                // Rutishauser's t = sgn(zeta)/(|zeta| + sqrt(1 + zeta^2)), zeta = (a_qq - a_pp) / 2g,
-                // sgn(0) = +1, in FP32 from ratios <= 1 (its accuracy only sets how far g is
-                // reduced); c0 = 1/sqrt(1 + t^2), s0 = t c0.  The applied rotation (c0, s0) f is
-                // orthogonal to FP64 precision: with e = c0^2 + s0^2 - 1 (exact in FP64,
-                // |e| ~ 2^-24), f = 1 - e/2 + 3e^2/8 = (1 + e)^(-1/2) + O(e^3).  a_qq - a_pp is
-                // formed in FP64 first: for nearly equal norms (clustered sigma) the difference
-                // of two FP32 roundings would be noise and the angle would not shrink g.
-                const float df = os_to_float(aqq - app);
-                const float hf = 2.0f * os_to_float(g);
-                const float adf = fabsf(df), ahf = fabsf(hf);
-                const float sz = (df == 0.0f || (df > 0.0f) == (hf > 0.0f)) ? 1.0f : -1.0f;
-                float tf;
-                if (adf >= ahf) {
-                    const float z = ahf / adf;
-                    tf = sz * z / (1.0f + sqrtf(fmaf(z, z, 1.0f)));
-                } else {
-                    const float w = adf / ahf;
-                    tf = sz / (w + sqrtf(fmaf(w, w, 1.0f)));
+            if (warp < P) {
+                const int a = warp;
+                double* xp = bufs + (size_t)map_top[par][a] * OS_LD;
+                double* xq = bufs + (size_t)map_bot[par][a] * OS_LD;
+                const double p0 = xp[lane], p1 = xp[lane + 32], q0 = xq[lane], q1 = xq[lane + 32];
+                const double app = xp[64], aqq = xq[64];
+                const long long idp = __double_as_longlong(xp[65]), idq = __double_as_longlong(xq[65]);
+                const double dpq = aqq - app;
+                // g = x_p^T x_q: one FP64 partial per lane, summed exactly as 64-bit fixed-point
+                // integers in units 2^(S - 62), with 2^S >= 4 (a_pp a_qq)^(1/2) >= 4 sum |x_p x_q|
+                const int ea = (int)((__double_as_longlong(app) >> 52) & 0x7ff) - 1023;
+                const int eb = (int)((__double_as_longlong(aqq) >> 52) & 0x7ff) - 1023;
+                const int S = ((ea + eb + 3) >> 1) + 2;
+                long long G = os_to_fixed(fma(p0, q0, p1 * q1), S);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) G += __shfl_xor_sync(0xffffffffu, G, o);
+                const double g = os_u64_to_double((unsigned long long)(G < 0 ? -G : G), S - 62, G < 0);
+                // column ids are integer bit patterns; positive doubles have positive patterns
+                const bool live = idp < n && idq < n && __double_as_longlong(app) > 0 && __double_as_longlong(aqq) > 0;
+                // the scaled test |g| > tol sqrt(a_pp a_qq): decided in FP32 when the FP32 ratio
+                // is clearly on one side (factor 2), exactly in FP64 otherwise
+                bool rot = false;
+                if (live && G != 0) {
+                    const float gf = fabsf(os_to_float(g)), af = os_to_float(app), bf = os_to_float(aqq);
+                    const bool in_range =
+                        af > 1e-30f && af < 1e30f && bf > 1e-30f && bf < 1e30f && gf > 1e-30f && gf < 1e30f;
+                    const float rr = in_range ? gf * rsqrtf(af) * rsqrtf(bf) : 0.0f;
+                    if (in_range && rr > 2.0f * tol_f) rot = true;
+                    else if (!in_range || rr > 0.5f * tol_f) rot = g * g > tol2 * (app * aqq);
+                    if (!rot) best_off = fmaxf(best_off, rr);
+                    sweep_mx = fmaxf(sweep_mx, in_range ? rr : (rot ? 1.0f : 0.0f));
                 }
-                const float cf = rsqrtf(fmaf(tf, tf, 1.0f));
-                const double c0 = os_to_double(cf), s0 = os_to_double(tf * cf);
-                const double ee = fma(c0, c0, fma(s0, s0, -1.0));
-                const double f = fma(ee, fma(ee, 0.375, -0.5), 1.0);
-                const double cs = c0 * f, sn = s0 * f;
-                na = fma(cs, va, -sn * vb);
-                nb = fma(sn, va, cs * vb);
-                // Within a sweep the squared norms only steer later angles and tests; they
-                // follow the exact-angle update a_pp - t g, a_qq + t g.  Every sweep starts
-                // from exact norms, and the final sweep (no rotation) uses only those.
-                const double tg = os_to_double(tf) * g;
-                np2 = app - tg;
-                nq2 = aqq + tg;
-                // a norm that dropped by 16x is recomputed (cancellation in the update); the
-                // decision is the same in both warps of the pair
-                const bool redo_p = os_hi(np2) < os_hi(app) - (4 << 20);
-                const bool redo_q = os_hi(nq2) < os_hi(aqq) - (4 << 20);
-                if (redo_p || redo_q) {
-                    double sp = warp_sum(na * na), sq = warp_sum(nb * nb);
-                    if (H == 2) {
-                        if (lane == 0) { red2[a][h][0] = sp; red2[a][h][1] = sq; }
-                        os_bar(1 + a, 64);
-                        sp = red2[a][0][0] + red2[a][1][0];
-                        sq = red2[a][0][1] + red2[a][1][1];
+                double n0 = p0, n1 = p1, m0 = q0, m1 = q1, np2 = app, nq2 = aqq;
+                if (rot) {
+                    // Rutishauser's t = sgn(zeta)/(|zeta| + sqrt(1 + zeta^2)), zeta = (a_qq - a_pp)/2g,
+                    // sgn(0) = +1, in FP32 from ratios <= 1 (its accuracy only sets how far g is
+                    // reduced; a_qq - a_pp comes from FP64: for clustered sigma the difference of two
+                    // FP32 roundings would be noise); c0 = 1/sqrt(1 + t^2), s0 = t c0; the applied
+                    // rotation is (c0, s0) scaled to unit length in FP64 (os_orthogonal).
+                    const float df = os_to_float(dpq);
+                    const float hf = 2.0f * os_to_float(g);
+                    const float adf = fabsf(df), ahf = fabsf(hf);
+                    const float sz = (df == 0.0f || (df > 0.0f) == (hf > 0.0f)) ? 1.0f : -1.0f;
+                    float tf;
+                    if (adf >= ahf) {
+                        const float z = __fdividef(ahf, adf), w = fmaf(z, z, 1.0f);
+                        tf = sz * __fdividef(z, 1.0f + w * rsqrtf(w));
+                    } else {
+                        const float z = __fdividef(adf, ahf), w = fmaf(z, z, 1.0f);
+                        tf = sz * __fdividef(1.0f, z + w * rsqrtf(w));
                     }
-                    if (redo_p) np2 = sp;
-                    if (redo_q) nq2 = sq;
+                    const float cf = rsqrtf(fmaf(tf, tf, 1.0f));
+                    double cs, sn;
+                    os_orthogonal(cf, tf * cf, cs, sn);
+                    n0 = fma(cs, p0, -sn * q0);
+                    n1 = fma(cs, p1, -sn * q1);
+                    m0 = fma(sn, p0, cs * q0);
+                    m1 = fma(sn, p1, cs * q1);
+                    // Within a sweep the squared norms only steer later angles and tests; they
+                    // follow the exact-angle update a_pp - t g, a_qq + t g.  Every sweep starts
+                    // from exact norms, and the final sweep (no rotation) uses only those.
+                    const double tg = os_to_double(tf) * g;
+                    np2 = app - tg;
+                    nq2 = aqq + tg;
+                    // a norm that dropped by 16x is recomputed (cancellation in the update)
+                    if (os_hi(np2) < os_hi(app) - (4 << 20)) np2 = warp_sum(fma(n0, n0, n1 * n1));
+                    if (os_hi(nq2) < os_hi(aqq) - (4 << 20)) nq2 = warp_sum(fma(m0, m0, m1 * m1));
+                    if (lane == 0) atomicAdd(&s_rot, 1);
                 }
-                if (h == 0 && lane == 0) atomicAdd(&s_rot, 1);
-            }
-            // top[P-1] leaves to the right, bot[0] to the left (straight from registers, with
-            // the norm and the id); every other column is written back in place
-            const bool send_r = (a == P - 1) && (c < C - 1);
-            const bool send_l = (a == 0) && (c > 0);
-            if (send_r) {
-                const uint32_t dst = os_mapa(bufs + (size_t)(RL0 + ring) * OS_LD, c + 1);
-                os_st_remote(dst + 8u * (unsigned)e, na);
-                if (h == 0 && lane == 0) {
-                    os_st_remote(dst + 8u * 64u, np2);
-                    os_st_remote(dst + 8u * 65u, __longlong_as_double(idp));
+                // top[P-1] leaves to the right, bot[0] to the left, from registers with its norm
+                // and id; every other column is written back in place
+                if (a == P - 1 && c < C - 1) {
+                    const uint32_t dst = os_mapa(bufs + (size_t)(RL0 + ring) * OS_LD, c + 1);
+                    const uint32_t rb = os_mapa(&rbar[0][ring], c + 1);
+                    os_st_async(dst + 8u * (unsigned)lane, n0, rb);
+                    os_st_async(dst + 8u * (unsigned)(lane + 32), n1, rb);
+                    if (lane == 0) {
+                        os_st_async(dst + 8u * 64u, np2, rb);
+                        os_st_async(dst + 8u * 65u, __longlong_as_double(idp), rb);
+                    }
+                } else {
+                    xp[lane] = n0;
+                    xp[lane + 32] = n1;
+                    if (lane == 0) xp[64] = np2;
                 }
-                os_arrive_remote(os_mapa(&rbar[0][ring], c + 1));
-            } else {
-                xp[e] = na;
-                if (h == 0 && lane == 0) xp[64] = np2;
-            }
-            if (send_l) {
-                const uint32_t dst = os_mapa(bufs + (size_t)(RR0 + ring) * OS_LD, c - 1);
-                os_st_remote(dst + 8u * (unsigned)e, nb);
-                if (h == 0 && lane == 0) {
-                    os_st_remote(dst + 8u * 64u, nq2);
-                    os_st_remote(dst + 8u * 65u, __longlong_as_double(idq));
+                if (a == 0 && c > 0) {
+                    const uint32_t dst = os_mapa(bufs + (size_t)(RR0 + ring) * OS_LD, c - 1);
+                    const uint32_t rb = os_mapa(&rbar[1][ring], c - 1);
+                    os_st_async(dst + 8u * (unsigned)lane, m0, rb);
+                    os_st_async(dst + 8u * (unsigned)(lane + 32), m1, rb);
+                    if (lane == 0) {
+                        os_st_async(dst + 8u * 64u, nq2, rb);
+                        os_st_async(dst + 8u * 65u, __longlong_as_double(idq), rb);
+                    }
+                } else {
+                    xq[lane] = m0;
+                    xq[lane + 32] = m1;
+                    if (lane == 0) xq[64] = nq2;
                 }
-                os_arrive_remote(os_mapa(&rbar[1][ring], c - 1));
-            } else {
-                xq[e] = nb;
-                if (h == 0 && lane == 0) xq[64] = nq2;
             }
             // the columns arriving in this step (every thread acquires them itself); after one
             // wait has run out the rest fail at once, so a lost neighbour costs one limit
             const long long lim = timed_out ? 0 : prm.wait_limit;
-            if (c > 0 && !os_wait(&rbar[0][ring], phase, lim)) { timed_out = true; s_timeout = 1; }
-            if (c < C - 1 && !os_wait(&rbar[1][ring], phase, lim)) { timed_out = true; s_timeout = 1; }
+            const bool got_l = c > 0 && os_wait(&rbar[0][ring], phase, lim);
+            const bool got_r = c < C - 1 && os_wait(&rbar[1][ring], phase, lim);
+            if ((c > 0 && !got_l) || (c < C - 1 && !got_r)) { timed_out = true; s_timeout = 1; }
             if (tid == 0) {
+                // this slot's next use (step K + D) expects one column again (only once the
+                // phase has completed: an arrival on an incomplete phase would be one too many)
+                if (got_l) os_arm(&rbar[0][ring], colbytes);
+                if (got_r) os_arm(&rbar[1][ring], colbytes);
                 const int* top = map_top[par];
                 const int* bot = map_bot[par];
                 int* nt = map_top[par ^ 1];
@@ -451,7 +501,7 @@ __global__ void __launch_bounds__(512) onesided_jacobi_kernel(OsParams prm) {
         }
         // cluster-wide rotation count and largest scaled |g| of this sweep
         const int sp = sweep & 1;
-        if (lane == 0 && h == 0) atomicMax(&s_lmax, __float_as_int(sweep_mx));
+        if (lane == 0 && warp < P) atomicMax(&s_lmax, __float_as_int(sweep_mx));
         __syncthreads();
         if (tid == 0) {
             atomicAdd(&cluster.map_shared_rank(s_cnt, 0)[sp], s_rot);
@@ -476,7 +526,7 @@ __global__ void __launch_bounds__(512) onesided_jacobi_kernel(OsParams prm) {
             for (int u = warp; u < 2 * P; u += nwarps) {
                 double* b = bufs + (size_t)(u < P ? map_top[par][u] : map_bot[par][u - P]) * OS_LD;
                 double s2 = 0.0;
-                for (int r = lane; r < R; r += 32) s2 = fma(b[r], b[r], s2);
+                for (int r = lane; r < 64; r += 32) s2 = fma(b[r], b[r], s2);
                 s2 = warp_sum(s2);
                 if (lane == 0) b[64] = s2;
             }
@@ -495,7 +545,7 @@ __global__ void __launch_bounds__(512) onesided_jacobi_kernel(OsParams prm) {
                 const double au = bu[64], av = bv[64];
                 if (!(au > 0.0 && av > 0.0)) continue;
                 double g0 = 0.0, g1 = 0.0, g2 = 0.0, g3 = 0.0;
-                for (int r = 0; r < R; r += 4) {
+                for (int r = 0; r < 64; r += 4) {
                     g0 = fma(bu[r], bv[r], g0);
                     g1 = fma(bu[r + 1], bv[r + 1], g1);
                     g2 = fma(bu[r + 2], bv[r + 2], g2);
@@ -523,7 +573,7 @@ __global__ void __launch_bounds__(512) onesided_jacobi_kernel(OsParams prm) {
             const int j = (int)__double_as_longlong(b[65]);
             if (j >= n) continue;
             double s2 = 0.0;
-            for (int r = lane; r < R; r += 32) s2 = fma(b[r], b[r], s2);
+            for (int r = lane; r < 64; r += 32) s2 = fma(b[r], b[r], s2);
             s2 = warp_sum(s2);
             const double nrm = sqrt(s2);
             const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
@@ -668,14 +718,13 @@ int cluster_size_for(int n, bool allow16) {
 cudaError_t launch_cluster_jacobi(OsParams prm, int C, cudaStream_t s) {
     prm.np = ((prm.n < 4 ? 4 : prm.n) + 4 * C - 1) / (4 * C) * (4 * C);
     prm.P = prm.np / (2 * C);
-    prm.H = prm.n > 32 ? 2 : 1;
     const size_t smem = sizeof(double) * (size_t)(2 * prm.P + 2 * (2 * prm.P + 2)) * OS_LD;
     cudaError_t e =
         cudaFuncSetAttribute(onesided_jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(C, 1, 1);
-    cfg.blockDim = dim3(32 * prm.P * prm.H, 1, 1);
+    cfg.blockDim = dim3(32 * prm.P, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
@@ -690,6 +739,16 @@ cudaError_t launch_cluster_jacobi(OsParams prm, int C, cudaStream_t s) {
 
 }  // namespace
 
+cudaError_t launch_cholesky(const double* M, int n, int64_t ldm, double* X, int* perm, DevInfo* info, bool pivot,
+                            cudaStream_t s) {
+    if (n > 64) return cudaErrorNotSupported;
+    cudaError_t e = cudaFuncSetAttribute(chol_piv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(2 * sizeof(double) * 64 * 64));
+    if (e != cudaSuccess) return e;
+    chol_piv_kernel<<<1, 256, 2 * sizeof(double) * (size_t)n * n, s>>>(M, n, ldm, X, perm, info, pivot ? 1 : 0);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_eig_onesided(const double* M, int n, int64_t ldm, double tol, int max_sweeps,
                                 void* scratch, double* lam_ws, double* V_ws, DevInfo* info,
                                 cudaStream_t s, const EigSide* side, long long wait_cycles) {
@@ -700,7 +759,7 @@ cudaError_t launch_eig_onesided(const double* M, int n, int64_t ldm, double tol,
     cudaError_t e = cudaFuncSetAttribute(chol_piv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)(2 * sizeof(double) * 64 * 64));
     if (e != cudaSuccess) return e;
-    chol_piv_kernel<<<1, 256, chol_smem, s>>>(M, n, ldm, X, perm, info);
+    chol_piv_kernel<<<1, 256, chol_smem, s>>>(M, n, ldm, X, perm, info, 1);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // kappa(B) on the side stream, beside the Jacobi (joined before the caller's next launch)
@@ -721,7 +780,7 @@ cudaError_t launch_eig_onesided(const double* M, int n, int64_t ldm, double tol,
     const bool allow16 =
         cudaFuncSetAttribute(onesided_jacobi_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess;
     if (!allow16) (void)cudaGetLastError();
-    OsParams prm{X, perm, n, 0, 0, 0, tol, max_sweeps, wait_limit_of(wait_cycles), lam_ws, V_ws, info};
+    OsParams prm{X, perm, n, 0, 0, tol, max_sweeps, wait_limit_of(wait_cycles), lam_ws, V_ws, info};
     int C = cluster_size_for(n, allow16);
     e = launch_cluster_jacobi(prm, C, s);
     if (e != cudaSuccess && C == 16) {

@@ -120,6 +120,19 @@ cudaError_t launch_eig_onesided(const double* M, int n, int64_t ldm, double tol,
                                 void* scratch, double* lam_ws, double* V_ws, DevInfo* info,
                                 cudaStream_t s, const EigSide* side = nullptr, long long wait_cycles = 0);
 
+// Cholesky of M (n <= 64, FP64, one CTA) into X = R^T (n x n, ld n, rows in pivot
+// order) and perm (position -> original index); pivot = false is the plain
+// factorization (perm = identity).  A non-positive pivot flags rank deficiency.
+cudaError_t launch_cholesky(const double* M, int n, int64_t ldm, double* X, int* perm, DevInfo* info, bool pivot,
+                            cudaStream_t s);
+
+// Algorithm 2 (n <= 64): the plain FP64 Cholesky M = R^T R, R cast to FP32, and
+// the SVD of that R by a one-CTA one-sided Jacobi in FP32 (tol: the scaled skip
+// threshold, e.g. n 2^-24).  Writes unsorted lambda = sigma^2 and V (FP64 copies
+// of the FP32 results) like launch_jacobi.  scratch as launch_eig_onesided.
+cudaError_t launch_eig_alg2(const double* M, int n, int64_t ldm, float tol, int max_sweeps, void* scratch,
+                            double* lam_ws, double* V_ws, DevInfo* info, cudaStream_t s);
+
 // Double-double eigen stage for FP64 working (n <= 64, one CTA): pivoted
 // Cholesky of M = G + G_lo in double-double, then a one-sided Jacobi SVD of
 // R^T in double-double.  scratch: unused.  Writes unsorted lambda (rounded to
@@ -128,7 +141,7 @@ cudaError_t launch_eig_dd(const double* M, const double* M_lo, int n, int64_t ld
                           double* lam_ws, double* V_ws, DevInfo* info, cudaStream_t s);
 
 // Eigensolver variants (tsvd_opts.eig_variant).
-enum : int { EIG_DEFAULT = 0, EIG_TWO_SIDED = 1, EIG_ONE_SIDED = 2 };
+enum : int { EIG_DEFAULT = 0, EIG_TWO_SIDED = 1, EIG_ONE_SIDED = 2, EIG_ALG2 = 3 };
 
 // Sort descending, sign rule, sigma = sqrt(lambda), round to working.
 // working: 0 FP32, 1 FP64.  Outputs (any may be null):

@@ -207,6 +207,12 @@ int max_sweeps(tsvd_ctx* h) { return h->opts.max_sweeps > 0 ? h->opts.max_sweeps
 // The eigen stage on M (n x n, ldm): unsorted lambda and V into lam / Vh.
 cudaError_t run_eig(tsvd_ctx* h, const double* M, int n, int64_t ldm, double* scratch, double* lam,
                     double* Vh) {
+    if (h->opts.eig_variant == EIG_ALG2) {
+        // Algorithm 2: the SVD of R runs at the working precision; its skip threshold is
+        // n 2^-24 (the rounding level of an FP32 dot product) unless jacobi_tol is given
+        const float tol = h->opts.jacobi_tol > 0.0 ? (float)h->opts.jacobi_tol : (float)n * 5.9604644775390625e-8f;
+        return launch_eig_alg2(M, n, ldm, tol, max_sweeps(h), scratch, lam, Vh, h->dinfo, h->stream);
+    }
     const bool one_sided = h->opts.eig_variant == EIG_ONE_SIDED ||
                            (h->opts.eig_variant == EIG_DEFAULT && n <= 64);
     if (one_sided)
@@ -298,7 +304,7 @@ tsvd_status tsvd_create(tsvd_handle* out, int device, void* stream, const tsvd_o
         if (opts->slices != 0 && opts->slices != GRAM_DIGITS) return TSVD_ERR_UNSUPPORTED;
         if (opts->chunk_rows != 0 && opts->chunk_rows != GRAM_KC) return TSVD_ERR_UNSUPPORTED;
         if (opts->split_k < 0 || opts->max_sweeps < 0 || opts->jacobi_tol < 0.0) return TSVD_ERR_ARG;
-        if (opts->eig_variant < 0 || opts->eig_variant > 2) return TSVD_ERR_UNSUPPORTED;
+        if (opts->eig_variant < 0 || opts->eig_variant > 3) return TSVD_ERR_UNSUPPORTED;
         if (opts->gram_variant < 0 || opts->gram_variant > 2) return TSVD_ERR_ARG;
         if (opts->u_variant < 0 || opts->u_variant > 1) return TSVD_ERR_ARG;
         if (opts->timing < 0 || opts->timeout_cycles < 0) return TSVD_ERR_ARG;
@@ -376,7 +382,7 @@ tsvd_status tsvd_gram(tsvd_handle h, const void* A, int64_t m, int64_t n, int64_
 tsvd_status tsvd_eig(tsvd_handle h, const double* M, int64_t n, int64_t ldm, double* lambda,
                      double* V, int64_t ldv, tsvd_info* info) {
     if (!h || !M || !lambda || !V || n < 1 || ldm < n || ldv < n) return TSVD_ERR_ARG;
-    if (n > 256) return TSVD_ERR_UNSUPPORTED;
+    if (n > 256 || (h->opts.eig_variant == EIG_ALG2 && n > 64)) return TSVD_ERR_UNSUPPORTED;
     DeviceGuard g(h->device);
     const Layout L = layout_for(n, 0, 1);
     tsvd_status st = ensure_ws(h, L.total);
@@ -406,6 +412,8 @@ tsvd_status tsvd_solve(tsvd_handle h, const void* A, int64_t m, int64_t n, int64
     // double-double (higher = DD) or FP64 (higher = FP64) n x n stage; the plain
     // FP64 Gram (gram_variant 1) has no double-double form.
     if (working == TSVD_FP32 && higher != TSVD_FP64) return TSVD_ERR_UNSUPPORTED;
+    // Algorithm 2 (SVD of the cast Cholesky factor at the working precision): FP32 working, n <= 64
+    if (h->opts.eig_variant == EIG_ALG2 && (working != TSVD_FP32 || n > 64)) return TSVD_ERR_UNSUPPORTED;
     if (higher == TSVD_DD && h->opts.gram_variant == 1) return TSVD_ERR_UNSUPPORTED;
     if (!gram_supported(h, A, working, n, lda)) return TSVD_ERR_UNSUPPORTED;
     DeviceGuard g(h->device);
