@@ -29,18 +29,25 @@ sys.path.insert(0, ROOT)
 
 METRIC = "A GB/s per thin SVD, mixed vs all-FP64 on GB300, sigma rel err≤1e-5; %HBM peak"
 DEFAULT_WORKLOAD = "ozaki_4194304x64_fp32"
-# gram_tc, gram_combine, chol_piv, onesided_jacobi, finish, compute_u_tc, finalize_info
-KERNELS_PER_STEP = 7
-FP64_DFMA_PER_CLK_SM = 1.68  # measured on GB300: 16 warps x independent DFMA chains, one SM
+# gram_tc, gram_combine, chol_piv, kappa (beside the Jacobi), onesided_jacobi, finish, compute_u_tc,
+# finalize_info
+KERNELS_PER_STEP = 8
+# Arithmetic peaks measured on GB300 with the library's probe kernels (python -m
+# paper_2603_11953_gb300.peaks; profiles/peaks_gb300.md); bench.py measures them again at run
+# time and falls back to these only when the probe cannot run.
+RECORDED_FP64_GFLOPS = 1251.7
+RECORDED_FP32_TFLOPS = 78.1
+# TF32 dense tensor rate per BF16 rate (nominal 1.1 / 2.25 PFLOP/s)
+TF32_PER_BF16 = 1.1 / 2.25
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of each stage's kernels, from
 # the ncu --set full summaries in profiles/ (captured at m = 1,048,576 rows); stages whose traffic
 # grows with m are scaled by m / 1,048,576.  None where no capture covers the stage.
 NCU_TRAFFIC = {
     "ozaki_4194304x64_fp32": {"gram": (272.634624e6, True),          # gram_tc_kernel (+ combine 10 MB)
-                              "jacobi": (0.222208e6, False),         # chol_piv + onesided_jacobi + finish
+                              "eig": None,                           # kernels changed since the capture
                               "compute_u": (482.525952e6, True)},    # compute_u_tc_kernel
     "stress_16777216x32_fp64": {"gram": None,
-                                "jacobi": (0.119296e6, False),       # eig_dd_kernel
+                                "eig": (0.119296e6, False),          # eig_dd_kernel
                                 "compute_u": (491.981568e6, True)},  # compute_u_kernel<double>
 }
 NCU_ROWS = 1048576
@@ -56,6 +63,47 @@ def peaks():
                     sm_max_mhz=float(p.get("sm_max_mhz", 2070.0)), src="measured")
     except Exception:
         return dict(hbm=6800.0, bf16=1900.0, bf16_sus=1700.0, sm_max_mhz=2070.0, src="fallback")
+
+
+def arith_peaks(skip=False):
+    """FP64 and FP32 FMA peaks of this GPU, measured now with the library's probe kernels."""
+    if not skip:
+        try:
+            from paper_2603_11953_gb300 import peaks as P
+            f64, t64 = P.probe("fp64_fma", 2000)
+            f32, t32 = P.probe("fp32_fma", 20000)
+            return {"fp64_gflops": f64 / (t64 * 1e-3) / 1e9, "fp32_tflops": f32 / (t32 * 1e-3) / 1e12,
+                    "src": "measured now (probe kernels)"}
+        except Exception as exc:  # noqa: BLE001 - reported in the line
+            return {"fp64_gflops": RECORDED_FP64_GFLOPS, "fp32_tflops": RECORDED_FP32_TFLOPS,
+                    "src": f"recorded (probe failed: {exc.__class__.__name__})"}
+    return {"fp64_gflops": RECORDED_FP64_GFLOPS, "fp32_tflops": RECORDED_FP32_TFLOPS, "src": "recorded"}
+
+
+def sample_accuracy(T, A, A_cpu, rows, m, n, working, higher, local, stream):
+    """sigma of the mixed form and of the all-FP64 plain form on the first `rows` rows of A (the
+    same rows the CPU baseline uses), against the oracle's double-double Algorithm 1 on them."""
+    import numpy as np
+    import torch
+    import oracle
+    from paper_2603_11953_gb300 import workloads
+    ref = oracle.svd(workloads.to_numpy_colmajor(A_cpu, rows), higher=2)
+    s_ref = ref["sigma_h"] + ref["sigma_h_lo"]
+    out = {"sample": f"first {rows} rows", "reference": "oracle: exact Gram + double-double Jacobi",
+           "oracle_status": int(ref["status"])}
+    dev = A.device
+    for name, kw, hi in (("mixed", {}, higher), ("fp64_plain", {"gram_variant": 1}, T.TSVD_FP64)):
+        h, _ = T.tsvd_create(local, stream.cuda_stream, T.tsvd_opts(**kw))
+        sig = torch.zeros(n, dtype=A.dtype, device=dev)
+        V = torch.zeros(n, n, dtype=A.dtype, device=dev)
+        info = torch.zeros(6, dtype=torch.int32, device=dev)
+        T.tsvd_solve(h, A, rows, n, A.shape[0], working, hi, sig, V, n, None, 0, info)
+        torch.cuda.synchronize(dev)
+        T.tsvd_destroy(h)
+        s = sig.double().cpu().numpy()
+        out[f"sigma_max_rel_err_{name}"] = float(np.max(np.abs(s - s_ref) / s_ref))
+        out[f"status_{name}"] = T.tsvd_status_string(int(info[0].item()))
+    return out
 
 
 class ClockSampler:
@@ -285,13 +333,13 @@ def run_batch(args):
     inf = info.view(count, 6).cpu().numpy()
     sweeps = inf[:, 1]
     jac_flops = float(sum(n ** 3 / 3.0 + sw * (n * (n - 1) // 2) * 8 * n for n, sw in zip(ns, sweeps)))
-    sm_fp64 = 2 * FP64_DFMA_PER_CLK_SM * pk["sm_max_mhz"] * 1e6 / 1e9
+    arp = arith_peaks(args.no_probe)
     gram_ms, eig_ms, u_ms = stage_ms[0], stage_ms[1], stage_ms[2]
     cands = {
         "gram": (gram_ms, {"bound": "hbm", "achieved": bytes_A / (gram_ms * 1e-3) / 1e9, "peak": pk["hbm"],
                            "unit": "GB/s"}),
         "jacobi": (eig_ms, {"bound": "alu", "achieved": jac_flops / (eig_ms * 1e-3) / 1e9,
-                            "peak": 152 * sm_fp64, "unit": "GFLOP/s"}),
+                            "peak": arp["fp64_gflops"], "unit": "GFLOP/s"}),
         "compute_u": (u_ms, {"bound": "hbm", "achieved": 2.0 * bytes_A / (u_ms * 1e-3) / 1e9, "peak": pk["hbm"],
                              "unit": "GB/s"}),
     }
@@ -349,6 +397,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-probe", action="store_true")
     ap.add_argument("--cpu-rows", type=int, default=32768)
     ap.add_argument("--ref-rows", type=int, default=16384)
     ap.add_argument("--batch-count", type=int, default=4096)
@@ -484,83 +534,105 @@ def main():
             T.tsvd_destroy(L["h"])
         del A_host, lanes
 
-    # the all-FP64 plain form of the same method (FP64 DFMA Gram, same Jacobi / U)
+    info_main = info.cpu()  # status, sweeps, off-norm, kappa(B) of the last timed step
+    # the all-FP64 plain form of the same method (FP64 DFMA Gram, same n x n stage and U),
+    # timed on the same resident A
     plain = None
+    sig_mixed = sigma.double().cpu().numpy()
     if not args.no_plain and n <= 64:
-        # FP64 Gram and FP64 n x n stage (the plain form has no double-double Gram)
-        hp, _ = T.tsvd_create(local, stream.cuda_stream, T.tsvd_opts(timing=1, gram_variant=1))
-        T.tsvd_solve(hp, A, m, n, m, working, T.TSVD_FP64, sigma, V, n, U, m, info)
+        hp, _ = T.tsvd_create(local, stream.cuda_stream, T.tsvd_opts(timing=3, gram_variant=1))
+        sig_p = torch.zeros_like(sigma)
+        T.tsvd_solve(hp, A, m, n, m, working, T.TSVD_FP64, sig_p, V, n, U, m, info)
         torch.cuda.synchronize(dev)
         kp = 3
         p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         p0.record(stream)
         for _ in range(kp):
-            T.tsvd_solve(hp, A, m, n, m, working, T.TSVD_FP64, sigma, V, n, U, m, info)
+            T.tsvd_solve(hp, A, m, n, m, working, T.TSVD_FP64, sig_p, V, n, U, m, info)
         p1.record(stream)
         torch.cuda.synchronize(dev)
-        pst = T.tsvd_last_stage_ms(hp)
+        pst = T.tsvd_stage_ms_mean(hp, kp)
         ms_plain = p0.elapsed_time(p1) / kp
+        sp = sig_p.double().cpu().numpy()
         plain = {"value": bytes_A / (ms_plain * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": ms_plain,
-                 "gram_ms": pst[0], "speedup_mixed_vs_plain": ms_plain / ms_step}
+                 "gram_ms": pst[0], "eig_ms": pst[1], "u_ms": pst[2], "speedup_mixed_vs_plain": ms_plain / ms_step,
+                 "sigma_max_rel_diff_vs_mixed": float((abs(sp - sig_mixed) / sig_mixed).max()),
+                 "status": T.tsvd_status_string(int(info[0].item()))}
         T.tsvd_destroy(hp)
 
+    # the other eigen stage (two-sided Jacobi on M_h) and the other U (CUDA-core FP32 FMA),
+    # each with everything else at its default, on the same resident A
+    variants = {}
+    if not args.no_variants and n <= 64 and working == T.TSVD_FP32:
+        for name, kw in (("eig_two_sided", dict(eig_variant=1)), ("u_cuda_core_fp32", dict(u_variant=1))):
+            hv, _ = T.tsvd_create(local, stream.cuda_stream, T.tsvd_opts(timing=5, **kw))
+            for _ in range(7):
+                T.tsvd_solve(hv, A, m, n, m, working, higher, sigma, V, n, U, m, info)
+            torch.cuda.synchronize(dev)
+            vst = T.tsvd_stage_ms_mean(hv, 5)
+            variants[name] = {"gram_ms": vst[0], "eig_ms": vst[1], "u_ms": vst[2], "total_ms": vst[3],
+                              "status": T.tsvd_status_string(int(info[0].item()))}
+            T.tsvd_destroy(hv)
     pk = peaks()
-    # roofline of the dominant stage (events recorded by the library on its stream)
+    arp = arith_peaks(args.no_probe)
     gram_ms, eig_ms, u_ms = stage_ms[0], stage_ms[1], stage_ms[2]
-    NP = 16 if n <= 16 else 32 if n <= 32 else 48 if n <= 48 else 64
-    gram_flops = 16 * 2.0 * m * NP * NP          # 16 exact digit-pair products on the tensor cores
-    gram_bytes = bytes_A
-    u_bytes = 2.0 * bytes_A
-    # FP64 work of one Jacobi pass is data dependent; count it from the sweeps reported
-    sweeps = int(info[1].item())
-    # algorithmic FP64 flops of the n x n stage: pivoted Cholesky n^3/3, then per sweep every
-    # pair's dot product (2n) and rotation (6n), counted as if every pair rotated
-    jac_flops = n ** 3 / 3.0 + sweeps * (n * (n - 1) // 2) * 8 * n
-    # FP64 peak of the SMs the n x n stage uses: a 16-CTA cluster (8 for n <= 32), one CTA per
-    # SM, at the measured 1.68 DFMA lanes per clock per SM (2 flops each)
-    eig_sms = 1 if n > 64 else 16 if n > 32 else 8 if n > 16 else 2 if n > 8 else 1  # n > 64: one-CTA two-sided
-    if n > 64 and working == T.TSVD_FP32:
-        nb = (n + 31) // 32
-        gram_flops = nb * (nb - 1) // 2 * 16 * 2.0 * m * 64 * 64  # one 64-column pass per block pair
-    sm_fp64 = 2 * FP64_DFMA_PER_CLK_SM * pk["sm_max_mhz"] * 1e6 / 1e9
-    fp64_peak = eig_sms * sm_fp64
-    launches = KERNELS_PER_STEP
-    u_cand = {"bound": "hbm", "achieved": u_bytes / (u_ms * 1e-3) / 1e9, "peak": pk["hbm"], "unit": "GB/s"}
+    sweeps = int(info_main[1].item())
+    kappa_b = float(info_main.view(torch.float64)[2].item())
+    nb = (n + 31) // 32
     if working == T.TSVD_FP64:
-        # pieces Gram: one 64-column tensor-core pass per needed 32-column block pair of the
-        # m x 4NB piece matrix; double-double n x n stage on one SM (about 20 FP64 operations per
-        # double-double multiply-add); U = A W in FP64 on every SM
+        # pieces Gram: one 64-column tensor-core pass per needed 32-column block pair of the m x 4NB
+        # piece matrix; double-double n x n stage (about 20 FP64 operations per double-double
+        # multiply-add); U = A W in FP64
         nbp = ((n + 31) // 32 * 32) // 32
         npass = sum(1 for b1 in range(4 * nbp) for b2 in range(b1 + 1, 4 * nbp) if b1 // nbp + b2 // nbp <= 3)
         gram_flops = npass * 16 * 2.0 * m * 64 * 64
-        jac_flops = 20.0 * (n ** 3 / 3.0 + sweeps * (n * (n - 1) // 2) * 8 * n)
-        fp64_peak = sm_fp64
-        u_cand = {"bound": "alu", "achieved": 2.0 * m * n * n / (u_ms * 1e-3) / 1e9,
-                  "peak": 152 * sm_fp64, "unit": "GFLOP/s", "hbm_gbs": u_bytes / (u_ms * 1e-3) / 1e9}
-        # colmax, split, npass x (gram_tc + combine), fold, eig_dd, finish, compute_u, finalize
-        launches = 2 + 2 * npass + 5
-    cands = {
-        "gram": (gram_ms, {"bound": "tensor", "achieved": gram_flops / (gram_ms * 1e-3) / 1e12,
-                           "peak": pk["bf16_sus"], "unit": "TFLOP/s",
-                           "hbm_gbs": gram_bytes / (gram_ms * 1e-3) / 1e9}),
-        "jacobi": (eig_ms, {"bound": "alu", "achieved": jac_flops / (eig_ms * 1e-3) / 1e9,
-                            "peak": fp64_peak, "unit": "GFLOP/s"}),
-        "compute_u": (u_ms, u_cand),
-    }
-    dom = max(cands, key=lambda k: cands[k][0])
-    rl = dict(cands[dom][1])
-    rl["kernel"] = dom
-    rl["frac"] = rl["achieved"] / rl["peak"]
+        eig_flops = 20.0 * (n ** 3 / 3.0 + sweeps * (n * (n - 1) // 2) * 8 * n)
+        u_terms = {"fp64": (2.0 * m * n * n / 1e9, arp["fp64_gflops"], "GFLOP/s")}
+        launches = 2 + 2 * npass + 5  # colmax, split, npass x (gram_tc + combine), fold, eig_dd, finish, U, finalize
+    else:
+        passes = 1 if n <= 64 else nb * (nb - 1) // 2
+        gram_flops = passes * 16 * 2.0 * m * 64 * 64  # 16 exact digit-pair products per 64-column pass
+        if n <= 64:
+            # pivoted Cholesky n^3/3, then per sweep every pair's dot product (2n) and rotation (6n)
+            eig_flops = n ** 3 / 3.0 + sweeps * (n * (n - 1) // 2) * 8 * n
+            launches = KERNELS_PER_STEP
+        else:
+            # two-sided: per pair, rows and columns p, q of M (8n) and of V (6n)
+            eig_flops = sweeps * (n * (n - 1) // 2) * 14.0 * n
+            launches = 2 * passes + 4
+        # tensor-core U: three TF32 products per output (A_hi W_hi, A_hi W_lo, A_lo W_hi)
+        u_terms = {"tensor_tf32": (3 * 2.0 * m * n * n / 1e12, pk["bf16_sus"] * TF32_PER_BF16, "TFLOP/s")}
+    u_terms["hbm"] = (2.0 * bytes_A / 1e9, pk["hbm"], "GB/s")
+    gram_terms = {"hbm": (bytes_A / 1e9, pk["hbm"], "GB/s"), "tensor": (gram_flops / 1e12, pk["bf16_sus"], "TFLOP/s")}
+    eig_terms = {"fp64": (eig_flops / 1e9, arp["fp64_gflops"], "GFLOP/s")}
+
+    def stage_roofline(ms, terms):
+        """Every term as achieved / peak; the binding term is the one with the largest floor."""
+        out = {}
+        for k, (work, peak, unit) in terms.items():
+            ach = work / (ms * 1e-3)
+            out[k] = {"achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
+                      "floor_ms": 1e3 * work / peak}
+        bound = max(out, key=lambda k: out[k]["floor_ms"])
+        return {"bound": bound, "ms": ms, "terms": out}
+
+    stage_rl = {"gram": stage_roofline(gram_ms, gram_terms), "eig": stage_roofline(eig_ms, eig_terms),
+                "compute_u": stage_roofline(u_ms, u_terms)}
+    dom = max(stage_rl, key=lambda k: stage_rl[k]["ms"])
+    bt = stage_rl[dom]["bound"]
+    term = stage_rl[dom]["terms"][bt]
+    rl = {"bound": {"hbm": "hbm", "tensor": "tensor", "tensor_tf32": "tensor"}.get(bt, "alu"),
+          "achieved": term["achieved"], "peak": term["peak"], "unit": term["unit"], "frac": term["frac"],
+          "kernel": dom, "term": bt}
     tr = NCU_TRAFFIC.get(spec.name, {}).get(dom)
     rl["traffic"] = None if tr is None else tr[0] * (m / NCU_ROWS if tr[1] else 1.0)
-    rl["peak_source"] = pk["src"]
+    rl["peak_source"] = pk["src"] if bt in ("hbm", "tensor", "tensor_tf32") else arp["src"]
     stages = {"gram_ms": gram_ms, "eig_ms": eig_ms, "u_ms": u_ms, "total_ms": stage_ms[3],
-              "gram_hbm_frac": (gram_bytes / (gram_ms * 1e-3) / 1e9) / pk["hbm"],
-              "u_hbm_frac": (u_bytes / (u_ms * 1e-3) / 1e9) / pk["hbm"],
-              "gram_tensor_frac": (gram_flops / (gram_ms * 1e-3) / 1e12) / pk["bf16_sus"],
-              "jacobi_sweeps": sweeps}
+              "jacobi_sweeps": sweeps, "kappa_B_estimate": kappa_b, "rooflines": stage_rl,
+              "variants": variants or None}
 
     cpu = None
+    accuracy = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rows = min(args.cpu_rows, m)
         A_cpu = A[:rows].cpu()
@@ -569,16 +641,21 @@ def main():
                "sample": f"first {rows} rows of {spec.name}: exact Gram + "
                          f"{'FP64' if working == T.TSVD_FP32 else 'double-double'} Jacobi + exact U rows "
                          f"({dt:.1f} s)"}
+        if n <= 64:
+            accuracy = sample_accuracy(T, A, A_cpu, rows, m, n, working, higher, local, stream)
 
     line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "fp32" if working == T.TSVD_FP32 else "fp64", "data": "synthetic",
             "config": {"workload": spec.name, "m": m, "n": n, "working": "fp32" if working == 0 else "fp64",
                        "higher": "fp64" if higher == 1 else "dd", "parallelism": f"replicas{world}",
+                       "eig": "pivoted Cholesky + one-sided Jacobi (FP64, 16-CTA cluster)" if n <= 64 and
+                              working == T.TSVD_FP32 else "default for this shape",
+                       "u": "tcgen05 3-term TF32 split" if working == T.TSVD_FP32 and n <= 64 else "CUDA cores",
                        "l2": "inputs larger than L2 (A is %.2f GB > 129 MB)" % (bytes_A / 1e9),
-                       "status": T.tsvd_status_string(status)},
-            "roofline": rl, "stages": stages, "fp64_plain": plain, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": launches * args.steps, "clocks": clocks,
+                       "status": T.tsvd_status_string(int(info_main[0].item()))},
+            "roofline": rl, "stages": stages, "fp64_plain": plain, "accuracy": accuracy, "cpu_baseline": cpu,
+            "e2e": e2e, "gpu_launches": launches * args.steps, "clocks": clocks, "arith_peaks": arp,
             "hbm_frac_of_A_stream": (bytes_A / (ms_step * 1e-3) / 1e9) / pk["hbm"]}
     T.tsvd_destroy(h)
     if rank == 0:
