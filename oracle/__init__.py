@@ -17,6 +17,8 @@ Functions (all matrices column-major, numpy ``order='F'``):
   rows_explicit_u(A, V_hi, V_lo, sig_hi, sig_lo, rows) -> exact A V_h / sigma_h (DD)
   round_dd(hi, lo, p)            -> RN_p(hi + lo) by one exact rounding (Alg. 1 l.4-5)
   alg2(M, working)               -> Algorithm 2: FP64 Cholesky, cast R, SVD of R (sigma, V)
+  cholesky(M)                    -> R, plain FP64 Cholesky M = R^T R (Cholesky QR, step 2)
+  cholqr_rows(A, Rw, rows, p)    -> RN_p of the solutions q of q Rw = a for the given rows (step 3)
 """
 from __future__ import annotations
 
@@ -69,9 +71,12 @@ def _load():
             lib.oracle_svd.argtypes = [P, I64, I64, I64, I, I, D, I, P, P, P, P, P, P, P, P]
             lib.oracle_round_dd.argtypes = [P, P, I64, I, P]
             lib.oracle_alg2.argtypes = [P, I, I, D, I, P, P, P]
+            lib.oracle_cholesky.argtypes = [P, I, P]
+            lib.oracle_cholqr_rows.argtypes = [P, I64, I64, I64, I, P, P, I64, I, P]
             for f in (lib.oracle_gram, lib.oracle_rows_times, lib.oracle_rows_explicit_u,
                       lib.oracle_jacobi_fp64, lib.oracle_jacobi_dd, lib.oracle_sort_sign,
-                      lib.oracle_svd, lib.oracle_round_dd, lib.oracle_alg2):
+                      lib.oracle_svd, lib.oracle_round_dd, lib.oracle_alg2, lib.oracle_cholesky,
+                      lib.oracle_cholqr_rows):
                 f.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -169,6 +174,29 @@ def alg2(M, working=0, tol=None, max_sweeps=100):
     st = lib.oracle_alg2(_ptr(M), n, int(working), float(tol), int(max_sweeps), _ptr(sig), _ptr(V),
                          ctypes.byref(sw))
     return dict(sigma=sig, V=V, status=st, sweeps=sw.value)
+
+
+def cholesky(M):
+    """Plain FP64 Cholesky M = R^T R: (R upper triangular, status)."""
+    lib = _load()
+    M = np.array(M, dtype=np.float64, order="F", copy=True)
+    n = M.shape[0]
+    R = np.zeros((n, n), order="F")
+    st = lib.oracle_cholesky(_ptr(M), n, _ptr(R))
+    return R, st
+
+
+def cholqr_rows(A, Rw, rows, p):
+    """RN_p of q = a Rw^-1 for the given rows a of A (double-double forward substitution)."""
+    lib = _load()
+    A, m, n, lda, working = _as_input(A)
+    Rw = np.asfortranarray(np.asarray(Rw, dtype=np.float64))
+    rows = np.ascontiguousarray(np.asarray(rows, dtype=np.int64))
+    out = np.zeros((len(rows), n), order="F")
+    st = lib.oracle_cholqr_rows(_ptr(A), m, n, lda, working, _ptr(Rw), _ptr(rows), len(rows), int(p), _ptr(out))
+    if st != OK:
+        raise ValueError(f"oracle_cholqr_rows status {st}")
+    return out
 
 
 def jacobi_fp64(M, tol=U_H_FP64, max_sweeps=100):

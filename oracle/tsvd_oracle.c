@@ -694,3 +694,53 @@ int oracle_alg2(const double* M, int n, int working, double tol, int max_sweeps,
     free(lam);
     return status;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Mixed precision Cholesky QR (Sec. 3.1: the Gram matrix at the higher        */
+/* precision, its Cholesky factorization at the higher precision, then Q from  */
+/* the linear systems Q R = A at the working precision).                      */
+/*   oracle_cholesky: R upper triangular with M = R^T R, plain FP64 (no        */
+/*     pivoting), column-major n x n, zeros below the diagonal.               */
+/*   oracle_cholqr_rows: for the given rows, q = a R_w^-1 (R_w the factor     */
+/*     given, normally RN_w(R)) by forward substitution in double-double      */
+/*     (q_j = (a_j - sum_{k<j} q_k r_kj) / r_jj), each entry then rounded once */
+/*     to p bits: the exact solution to ~2^-100, rounded.                     */
+/* ------------------------------------------------------------------------- */
+int oracle_cholesky(const double* M, int n, double* R) {
+    if (!M || !R || n < 1) return ORC_BAD_ARG;
+    for (int k = 0; k < n * n; ++k) R[k] = 0.0;
+    for (int j = 0; j < n; ++j) {
+        double d = M[j + (size_t)j * n];
+        for (int k = 0; k < j; ++k) d -= R[k + (size_t)j * n] * R[k + (size_t)j * n];
+        if (!(d > 0.0)) return ORC_NOT_FULL_RANK;
+        const double rjj = sqrt(d);
+        R[j + (size_t)j * n] = rjj;
+        for (int i = j + 1; i < n; ++i) {
+            double s = M[j + (size_t)i * n];
+            for (int k = 0; k < j; ++k) s -= R[k + (size_t)j * n] * R[k + (size_t)i * n];
+            R[j + (size_t)i * n] = s / rjj;
+        }
+    }
+    return ORC_OK;
+}
+
+int oracle_cholqr_rows(const void* A, int64_t m, int64_t n, int64_t lda, int working, const double* Rw,
+                       const int64_t* rows, int64_t nrows, int p, double* out) {
+    if (!A || !Rw || !rows || !out || n < 1 || p < 2 || p > 53) return ORC_BAD_ARG;
+    dd* q = (dd*)malloc(sizeof(dd) * (size_t)n);
+    superacc* s = (superacc*)malloc(sizeof(superacc));
+    if (!q || !s) { free(q); free(s); return ORC_BAD_ARG; }
+    for (int64_t k = 0; k < nrows; ++k) {
+        const int64_t r = rows[k];
+        if (r < 0 || r >= m) { free(q); free(s); return ORC_BAD_ARG; }
+        for (int64_t j = 0; j < n; ++j) {
+            dd acc = dd_make(elem(A, working, lda, r, j));
+            for (int64_t i = 0; i < j; ++i) acc = dd_sub(acc, dd_mul(q[i], dd_make(Rw[i + j * n])));
+            q[j] = dd_div(acc, dd_make(Rw[j + j * n]));
+            out[k + j * nrows] = round_dd_exact(s, q[j].hi, q[j].lo, p);
+        }
+    }
+    free(q);
+    free(s);
+    return ORC_OK;
+}

@@ -410,3 +410,57 @@ def test_alg2_casts_r_to_working_precision():
 def test_alg2_not_positive_definite():
     M = np.array([[4.0, 2.0, 0.0], [2.0, 1.0, 0.0], [0.0, 0.0, 3.0]])  # rank 2 block
     assert oracle.alg2(M)["status"] == oracle.NOT_FULL_RANK
+
+
+# ---------------------------------------------------------------- mixed precision Cholesky QR (Sec. 3.1)
+def test_cholesky_exact_factor_and_lapack():
+    rng = np.random.default_rng(2)
+    n = 8
+    R0 = np.triu(rng.integers(-4, 5, (n, n)).astype(float))
+    np.fill_diagonal(R0, np.arange(2, 2 + n))
+    R, st = oracle.cholesky(R0.T @ R0)
+    assert st == 0 and np.array_equal(R, R0)  # every step exact on small integers
+    B = rng.standard_normal((30, n))
+    M = B.T @ B
+    R, st = oracle.cholesky(M)
+    np.testing.assert_allclose(R, np.linalg.cholesky(M).T, rtol=1e-12, atol=1e-12)
+    assert oracle.cholesky(np.array([[1.0, 2.0], [2.0, 1.0]]))[1] == oracle.NOT_FULL_RANK
+
+
+def test_cholqr_rows_exact_rational_solution():
+    """q R = a solved exactly (Fractions, forward substitution) and rounded once: the oracle's
+    double-double substitution rounded to 24 and to 53 bits gives the same values."""
+    rng = np.random.default_rng(8)
+    m, n = 7, 5
+    A = np.asfortranarray(rng.standard_normal((m, n)).astype(np.float32))
+    Rw = np.triu(rng.standard_normal((n, n))) + np.diag(np.full(n, 2.0))
+    Rw = Rw.astype(np.float32).astype(np.float64)
+    rows = np.array([0, 3, 6])
+    for p in (24, 53):
+        out = oracle.cholqr_rows(A, Rw, rows, p)
+        for k, r in enumerate(rows):
+            q = []
+            for j in range(n):
+                acc = Fraction(float(A[r, j])) - sum(q[i] * Fraction(Rw[i, j]) for i in range(j))
+                q.append(acc / Fraction(Rw[j, j]))
+                assert out[k, j] == round_frac(q[j], p), (p, r, j)
+
+
+def test_cholqr_orthogonality_theorem3():
+    """Theorem 3: with the Gram and the Cholesky factorization at u_h = 2^-53 <= u^2 and Q from
+    Q R = A at u = 2^-24, ||Q^T Q - I|| is O(u) kappa(B), not O(u) kappa(B)^2 as with u_h = u: a
+    graded A with kappa(B) ~ 1e3 and kappa(A) ~ 1e7 keeps Q orthogonal to ~1e-4 (c = 2n)."""
+    import torch
+    from paper_2603_11953_gb300 import workloads
+    m, n = 3000, 10
+    A, _ = workloads.small_case(m, n, kappa_sigma=1e3, logd=2.0, seed=19)
+    A_np = workloads.to_numpy_colmajor(A, m)
+    M = oracle.gram(A_np)[0]
+    R, st = oracle.cholesky(M)
+    assert st == 0
+    Rw = R.astype(np.float32).astype(np.float64)
+    Q = oracle.cholqr_rows(A_np, Rw, np.arange(m), 24)
+    d = np.sqrt(np.diag(M))
+    kB = math.sqrt(np.linalg.cond(M / np.outer(d, d)))
+    orth = np.linalg.norm(Q.T @ Q - np.eye(n), 2)
+    assert orth <= 2 * n * 2.0 ** -24 * kB, (orth, kB)
