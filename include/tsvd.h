@@ -58,8 +58,9 @@ typedef enum { TSVD_FP32 = 0, TSVD_FP64 = 1, TSVD_DD = 2 } tsvd_prec;
 typedef enum {
     TSVD_OK = 0,
     TSVD_ERR_ARG = 1,            /* bad size, null pointer, bad tag */
-    TSVD_ERR_ALIGN = 2,          /* reserved: not returned (every path accepts any alignment;
-                                    unaligned input takes the CUDA-core kernels) */
+    TSVD_ERR_ALIGN = 2,          /* the input must be TMA-loadable (16-byte aligned A, lda a
+                                    multiple of 4): the fixed-scale and row-sharded Grams only;
+                                    every other path accepts any alignment */
     TSVD_ERR_NONFINITE = 3,      /* A contains Inf or NaN */
     TSVD_ERR_NOT_FULL_RANK = 4,  /* some eigenvalue of M_h is <= 0 */
     TSVD_ERR_NO_CONVERGENCE = 5, /* Jacobi hit max_sweeps */
@@ -102,6 +103,14 @@ typedef struct {
     int u_variant;         /* 0 = U = A W on tcgen05 in a 3-term TF32 split when the input
                               can be TMA-loaded (FP32, n <= 64), else CUDA cores;
                               1 = CUDA-core FP32 kernel */
+    int fixed_scale;       /* 1: the FP32 Gram first finds every column's exponent over the
+                              whole of A (one extra read of A) and digits every entry against
+                              it: the Gram is then bitwise the same for any split over CTAs
+                              and any order of the rows, and equals the row-sharded Gram of
+                              tsvd_gram_partial / tsvd_gram_finish.  FP32 working, n <= 64,
+                              A 16-byte aligned and lda a multiple of 4 (else
+                              TSVD_ERR_ALIGN).  0 (default): running per-CTA scales (one
+                              read of A; bitwise reproducible run to run for a given split) */
 } tsvd_opts;
 
 /* Per-call numeric report (written asynchronously by the device). */
@@ -213,6 +222,68 @@ TSVD_API tsvd_status tsvd_last_stage_ms(tsvd_handle h, float ms[4]);
  * Synchronises on the recorded events only.  TSVD_ERR_ARG otherwise. */
 #define TSVD_MAX_TIMED 1024
 TSVD_API tsvd_status tsvd_stage_ms_mean(tsvd_handle h, int last, float ms[4]);
+
+/* ---- Row-sharded Gram (Sec. 4.2.1: the rows of A are distributed over the
+ * processes, each computes its part of A^T A, and one global sum combines them).
+ * Per rank, with A_r its block of rows (FP32, n <= 64, device pointers):
+ *   1. tsvd_gram_colexp(A_r) -> E (n int32): E_j = the least e with max |a_rj| < 2^e
+ *      over the rank's rows (INT32 -1048576 for an all-zero column).
+ *   2. all-reduce E with MAX over the ranks (E must bound the whole column).
+ *   3. tsvd_gram_partial(A_r, E) -> limbs (4 x n x n int64): the rank's part of
+ *      A^T A as an exact integer in units 2^(E_i + E_j - 63), split into four
+ *      32-bit limbs (value = sum_k limbs[k][i][j] 2^(32k)).
+ *   4. all-reduce the limbs with SUM over the ranks (integer sums: exact in any
+ *      order, no overflow for up to 2^31 ranks).
+ *   5. tsvd_gram_finish(limbs, E) -> G (and its double-double low part): one
+ *      rounding of the exact sum.
+ *   6. tsvd_solve_gram(G, A_r) on every rank: the n x n stage (the same on every
+ *      rank) and the rank's rows of U.
+ * The Gram is bitwise the same for every partition of the rows over ranks and
+ * CTAs and every order of the rows, and equals tsvd_gram with fixed_scale = 1 on
+ * the whole A.  The accuracy is that of tsvd_gram (2^-50 (|A|^T|A|) per entry). */
+
+/* Step 1.  A: m x n FP32 (m >= 0), lda >= max(m, 1).  E: device int32[n].
+ * Errors: TSVD_ERR_ARG, TSVD_ERR_UNSUPPORTED (FP64 working or n > 64).  Inf or
+ * NaN in A: TSVD_ERR_NONFINITE via tsvd_sync_status. */
+TSVD_API tsvd_status tsvd_gram_colexp(tsvd_handle h, const void* A, int64_t m, int64_t n, int64_t lda,
+                                      tsvd_prec working, int32_t* E);
+
+/* Step 3.  A as for step 1, 16-byte aligned with lda a multiple of 4 (else
+ * TSVD_ERR_ALIGN); E: device, the column exponents over ALL ranks (an entry at
+ * or above 2^E_j gives TSVD_ERR_ARG via tsvd_sync_status); limbs: device int64
+ * [4][n][n] (limb k of entry (i, j) at limbs[k n^2 + i + j n]). */
+TSVD_API tsvd_status tsvd_gram_partial(tsvd_handle h, const void* A, int64_t m, int64_t n, int64_t lda,
+                                       tsvd_prec working, const int32_t* E, int64_t* limbs);
+
+/* Step 5.  limbs, E: device, as above (summed over the ranks).  G: device FP64
+ * n x n (ldg >= n), both triangles; higher == TSVD_DD also writes the low parts
+ * at G + ldg * n.  Errors: TSVD_ERR_ARG, TSVD_ERR_UNSUPPORTED (n > 64). */
+TSVD_API tsvd_status tsvd_gram_finish(tsvd_handle h, const int64_t* limbs, const int32_t* E, int64_t n,
+                                      tsvd_prec higher, double* G, int64_t ldg);
+
+/* Alg. 1 lines 3-6 on a given M_h = G (device FP64 n x n, ldg >= n): the n x n
+ * stage (as tsvd_solve: eig_variant, tolerances, kappa_B), sigma and V in
+ * working precision, and U = A W for the given rows of A (m >= 0 rows, lda >=
+ * max(m, 1); U NULL to skip).  FP32 working, FP64 higher, n <= 256.
+ * Arguments and errors otherwise as tsvd_solve. */
+TSVD_API tsvd_status tsvd_solve_gram(tsvd_handle h, const double* G, int64_t ldg, const void* A, int64_t m,
+                                     int64_t n, int64_t lda, tsvd_prec working, tsvd_prec higher, void* sigma,
+                                     void* V, int64_t ldv, void* U, int64_t ldu, tsvd_info* info);
+
+/* The mixed precision Cholesky QR algorithm (Sec. 3.1; Theorem 3): A = Q R with
+ *   1. M_h = A^T A at the higher precision (tsvd_gram's kernels),
+ *   2. M_h = R^T R, the plain Cholesky factorization in FP64,
+ *   3. Q from the linear systems Q R = A at the working precision: each row of Q
+ *      by forward substitution in FP32 against RN_32(R).
+ * With u_h = 2^-53 <= u^2, ||Q^T Q - I|| = O(u) kappa(B) (Theorem 3).
+ *   A: device m x n FP32 (m >= n), lda >= m.  Q: device m x n FP32, ldq >= m,
+ *   or NULL (R only).  R: device FP64 n x n upper triangular (zeros below the
+ *   diagonal), ldr >= n, or NULL.  info: NULL or device / pinned-host tsvd_info.
+ * FP32 working, FP64 higher, n <= 64.  Errors: TSVD_ERR_ARG, TSVD_ERR_UNSUPPORTED;
+ * numeric (via info / tsvd_sync_status): TSVD_ERR_NOT_FULL_RANK at a non-positive
+ * Cholesky pivot, TSVD_ERR_NONFINITE. */
+TSVD_API tsvd_status tsvd_cholqr(tsvd_handle h, const void* A, int64_t m, int64_t n, int64_t lda, tsvd_prec working,
+                                 tsvd_prec higher, void* Q, int64_t ldq, double* R, int64_t ldr, tsvd_info* info);
 
 /* Size of the one device array that tsvd_gram_static works in (16 MiB). */
 #define TSVD_GRAM_STATIC_SCRATCH_BYTES ((size_t)16 << 20)

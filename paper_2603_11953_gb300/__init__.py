@@ -25,7 +25,8 @@ TSVD_FP32, TSVD_FP64, TSVD_DD = 0, 1, 2
 
 EXPORTED = ["tsvd_create", "tsvd_destroy", "tsvd_status_string", "tsvd_gram", "tsvd_eig",
             "tsvd_solve", "tsvd_batch_solve", "tsvd_sync_status", "tsvd_last_stage_ms",
-            "tsvd_stage_ms_mean", "tsvd_gram_static"]
+            "tsvd_stage_ms_mean", "tsvd_gram_static", "tsvd_gram_colexp", "tsvd_gram_partial",
+            "tsvd_gram_finish", "tsvd_solve_gram", "tsvd_cholqr"]
 
 
 class tsvd_opts(ctypes.Structure):
@@ -33,7 +34,7 @@ class tsvd_opts(ctypes.Structure):
                 ("jacobi_tol", ctypes.c_double), ("max_sweeps", ctypes.c_int),
                 ("eig_variant", ctypes.c_int), ("autotune", ctypes.c_int),
                 ("timeout_cycles", ctypes.c_longlong), ("gram_variant", ctypes.c_int),
-                ("timing", ctypes.c_int), ("u_variant", ctypes.c_int)]
+                ("timing", ctypes.c_int), ("u_variant", ctypes.c_int), ("fixed_scale", ctypes.c_int)]
 
 
 class tsvd_info(ctypes.Structure):
@@ -72,6 +73,11 @@ def load_library(path: str = LIB_PATH):
         lib.tsvd_sync_status.argtypes = [P]
         lib.tsvd_last_stage_ms.argtypes = [P, ctypes.POINTER(ctypes.c_float)]
         lib.tsvd_gram_static.argtypes = [P, I64, I64, I64, I, I, P, I64, P, P]
+        lib.tsvd_gram_colexp.argtypes = [P, P, I64, I64, I64, I, P]
+        lib.tsvd_gram_partial.argtypes = [P, P, I64, I64, I64, I, P, P]
+        lib.tsvd_gram_finish.argtypes = [P, P, P, I64, I, P, I64]
+        lib.tsvd_solve_gram.argtypes = [P, P, I64, P, I64, I64, I64, I, I, P, P, I64, P, I64, P]
+        lib.tsvd_cholqr.argtypes = [P, P, I64, I64, I64, I, I, P, I64, P, I64, P]
         for name in EXPORTED:
             if name != "tsvd_status_string":
                 getattr(lib, name).restype = ctypes.c_int
@@ -173,3 +179,35 @@ def tsvd_stage_ms_mean(h, last):
     out = (ctypes.c_float * 4)()
     _check("tsvd_stage_ms_mean", load_library().tsvd_stage_ms_mean(h, int(last), out))
     return list(out)
+
+
+def tsvd_gram_colexp(h, A, m, n, lda, working, E, check=True):
+    """Row-sharded Gram, step 1: E[j] = least e with max |a_rj| < 2^e over these rows."""
+    st = load_library().tsvd_gram_colexp(h, _p(A), int(m), int(n), int(lda), int(working), _p(E))
+    return _check("tsvd_gram_colexp", st) if check else st
+
+
+def tsvd_gram_partial(h, A, m, n, lda, working, E, limbs, check=True):
+    """Row-sharded Gram, step 3: these rows' exact part of A^T A as 4 x n x n int64 limbs."""
+    st = load_library().tsvd_gram_partial(h, _p(A), int(m), int(n), int(lda), int(working), _p(E), _p(limbs))
+    return _check("tsvd_gram_partial", st) if check else st
+
+
+def tsvd_gram_finish(h, limbs, E, n, higher, G, ldg, check=True):
+    """Row-sharded Gram, step 5: the (rank-summed) limbs rounded once to G."""
+    st = load_library().tsvd_gram_finish(h, _p(limbs), _p(E), int(n), int(higher), _p(G), int(ldg))
+    return _check("tsvd_gram_finish", st) if check else st
+
+
+def tsvd_solve_gram(h, G, ldg, A, m, n, lda, working, higher, sigma, V, ldv, U=None, ldu=0, info=None, check=True):
+    """Alg. 1 lines 3-6 on a given Gram matrix G, with U for the given rows of A."""
+    st = load_library().tsvd_solve_gram(h, _p(G), int(ldg), _p(A), int(m), int(n), int(lda), int(working),
+                                        int(higher), _p(sigma), _p(V), int(ldv), _p(U), int(ldu), _p(info))
+    return _check("tsvd_solve_gram", st) if check else st
+
+
+def tsvd_cholqr(h, A, m, n, lda, working, higher, Q, ldq, R=None, ldr=0, info=None, check=True):
+    """Mixed precision Cholesky QR: A = Q R (Gram and Cholesky in FP64, Q R = A solved in FP32)."""
+    st = load_library().tsvd_cholqr(h, _p(A), int(m), int(n), int(lda), int(working), int(higher), _p(Q), int(ldq),
+                                    _p(R), int(ldr), _p(info))
+    return _check("tsvd_cholqr", st) if check else st

@@ -18,7 +18,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libtsvd.so")
 PROBE_LIB = os.path.join(OUT, "libtsvd_probe.so")
 PROBE_SOURCE = "peak_probe.cu"
-SOURCES = ["tsvd_api.cu", "gram_ozaki.cu", "jacobi.cu", "compute_u.cu", "compute_u_tc.cu", "gram_static.cu", "eig_onesided.cu", "tma_util.cu", "gram_tc.cu", "gram_fp64.cu", "eig_dd.cu", "batch.cu", "eig_alg2.cu"]
+SOURCES = ["tsvd_api.cu", "gram_ozaki.cu", "jacobi.cu", "compute_u.cu", "compute_u_tc.cu", "gram_static.cu", "eig_onesided.cu", "tma_util.cu", "gram_tc.cu", "gram_fp64.cu", "eig_dd.cu", "batch.cu", "eig_alg2.cu", "gram_sharded.cu", "cholqr.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ARCH + ["-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",

@@ -24,10 +24,10 @@
 // So (i) the pairs are spread over the 16 SMs of a (non-portable) cluster,
 // two per SM, one warp per pair, and a warp issues only the FP64
 // instructions that carry the result: 2 for its part of x_p^T x_q, 1 for the
-// norm difference, 8 for the rotation, 3 for the norm updates; (ii) the
-// reduction of the dot product (exact 64-bit fixed point), the angle (FP32),
-// the scaled test and the orthogonality correction (integer arithmetic) run
-// on the integer and FP32 pipes; (iii) a column that leaves an SM is written
+// norm difference, 5 for the orthogonality correction, 8 for the rotation, 3
+// for the norm updates; (ii) the reduction of the dot product (exact 64-bit
+// fixed point), the angle and the scaled test (FP32) run on the integer and
+// FP32 pipes; (iii) a column that leaves an SM is written
 // straight from registers into the neighbour's shared memory by st.async,
 // into a ring of receive buffers that the tournament maps in place, each
 // store completing a transaction on the neighbour's mbarrier: no copy, no
@@ -70,6 +70,18 @@ namespace {
 __device__ __forceinline__ double chol_S(const double* sa, int n, int x, int y) {
     return x >= y ? sa[x + (size_t)y * n] : sa[y + (size_t)x * n];
 }
+// 1 / sqrt(d) for a positive normal d: d = dm 4^k with dm in [1, 4) by an exponent shift,
+// y0 = rsqrtf(dm) (FP32), one Newton step with its second-order term in FP64,
+// y = y0 (1 + e/2 + 3e^2/8) with e = 1 - dm y0^2 (|e| ~ 2^-23, error O(e^3)), then 2^-k.
+__device__ __forceinline__ double chol_rsqrt(double d) {
+    const long long b = __double_as_longlong(d);
+    const int k = (int)(((b >> 52) & 0x7ff) - 1023) >> 1;  // floor(exponent / 2)
+    const double dm = __longlong_as_double(b - ((long long)(2 * k) << 52));
+    const double y0 = (double)rsqrtf((float)dm);
+    const double e = fma(-dm * y0, y0, 1.0);
+    const double y = y0 * fma(e, fma(e, 0.375, 0.5), 1.0);
+    return __longlong_as_double(__double_as_longlong(y) - ((long long)k << 52));
+}
 
 __global__ void __launch_bounds__(256)
     chol_piv_kernel(const double* __restrict__ M, int n, int64_t ldm, double* __restrict__ X,
@@ -109,7 +121,7 @@ __global__ void __launch_bounds__(256)
         const double d = sa[ok + (size_t)ok * n];
         if (!(d > 0.0)) { deficient = true; kend = k; break; }
         const unsigned long long rn = rem & ~(1ull << ok);
-        const double rinv = rsqrt(d);  // 1 / r_kk
+        const double rinv = chol_rsqrt(d);  // 1 / r_kk
         // row k of R over the remaining indices, and their ascending list
         for (int o = tid; o < n; o += nt) {
             if (o == ok) Rr[(size_t)k * n + o] = d * rinv;
@@ -118,19 +130,17 @@ __global__ void __launch_bounds__(256)
         }
         if (tid == 0) s_perm[k] = ok;
         __syncthreads();
-        // trailing update S(a, b) -= R[k][a] R[k][b] over the remaining lower triangle:
-        // t enumerates pairs (i', j'), j' <= i', row by row; i = rc - 1 - j' and j = rc - 1 - i'
-        // give consecutive i (rows) for consecutive t, so a warp's accesses are contiguous
+        // trailing update S(a, b) -= R[k][a] R[k][b] over the remaining lower triangle: the
+        // warps take its columns b (round robin), the lanes its rows a >= b, contiguous
         const int rc = __popcll(rn);
-        const int T = rc * (rc + 1) / 2;
         const double* rk = Rr + (size_t)k * n;
-        for (int t = tid; t < T; t += nt) {
-            int ip = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
-            while (ip * (ip + 1) / 2 > t) --ip;
-            while ((ip + 1) * (ip + 2) / 2 <= t) ++ip;
-            const int jp = t - ip * (ip + 1) / 2;
-            const int a = s_list[rc - 1 - jp], b = s_list[rc - 1 - ip];  // a >= b
-            sa[a + (size_t)b * n] -= rk[a] * rk[b];
+        for (int jb = tid >> 5; jb < rc; jb += nt >> 5) {
+            const int b = s_list[jb];
+            const double rb = rk[b];
+            for (int ia = jb + lane; ia < rc; ia += 32) {
+                const int a = s_list[ia];
+                sa[a + (size_t)b * n] -= rk[a] * rb;
+            }
         }
         rem = rn;
         __syncthreads();
@@ -252,25 +262,6 @@ __device__ __forceinline__ long long os_to_fixed(double x, int S) {
     const long long v = sh >= 0 ? (long long)(mant << sh) : (sh <= -64 ? 0ll : (long long)(mant >> (-sh)));
     return (b >> 63) ? -v : v;
 }
-// (cs, sn) = (c0, s0) (c0^2 + s0^2)^(-1/2) to FP64 precision, from FP32 c0 in (1/2, 1] and
-// |s0| < 1, on the integer pipes: e = c0^2 + s0^2 - 1 exactly in units 2^-62 (the 24-bit
-// significands squared), f = 1 - e/2 + 3e^2/8 (error O(e^3), |e| ~ 2^-24), then the products
-// with f rounded once to FP64.
-__device__ __forceinline__ void os_orthogonal(float c0, float s0, double& cs, double& sn) {
-    const unsigned cb = __float_as_uint(c0), sb = __float_as_uint(s0);
-    const int ec = (int)((cb >> 23) & 0xff), es = (int)((sb >> 23) & 0xff);
-    const unsigned long long Cm = (cb & 0x7fffffu) | 0x800000u;
-    const unsigned long long Sm = es ? ((sb & 0x7fffffu) | 0x800000u) : 0ull;
-    const int shc = 2 * ec - 238, shs = 2 * es - 238;  // c0^2 = Cm^2 2^(shc - 62)
-    const long long C2 = (long long)(shc >= 0 ? (Cm * Cm) << shc : (Cm * Cm) >> (-shc));
-    const long long S2 = (long long)(shs >= 0 ? (Sm * Sm) << shs : (shs <= -64 ? 0ull : (Sm * Sm) >> (-shs)));
-    const long long E = C2 + S2 - (1ll << 62);
-    const unsigned long long aE = (unsigned long long)(E < 0 ? -E : E);
-    const unsigned long long F = (1ull << 62) - (unsigned long long)(E >> 1) + ((3ull * __umul64hi(aE, aE)) >> 1);
-    cs = os_u64_to_double(__umul64hi(Cm << 40, F), ec - 188, false);
-    sn = os_u64_to_double(__umul64hi(Sm << 40, F), es - 188, (sb >> 31) != 0);
-}
-
 // Column slots of a CTA: top[u] and bot[u] (u < P) hold the two columns of pair u.  A
 // slot maps to one of the CTA's buffers: 2P local ones (the initial columns), then a ring
 // of D buffers for columns arriving from the left neighbour and one for columns from the
@@ -283,12 +274,13 @@ __device__ __forceinline__ void os_orthogonal(float c0, float s0, double& cs, do
 // CTA's barrier of step K - 2: so a ring of D = 2P + 2 buffers per side keeps every store
 // causally after the last read of the column it overwrites.
 //
-// One warp per pair, lane l holding rows l and l + 32.  Per step a warp issues 14 FP64
-// instructions: 2 for its part of g = x_p^T x_q, 1 for a_qq - a_pp, 8 for the rotation, 3
-// for the norm updates.  The reduction of g is an exact sum of 64-bit fixed-point integers
-// (units 2^(S - 62), 2^S above ||x_p|| ||x_q|| from the exponents of the norms) on the
-// integer pipes, the angle is FP32, and the orthogonality correction of (c0, s0) is integer
-// arithmetic (os_orthogonal).  A leaving column is written from registers with st.async
+// One warp per pair, lane l holding rows l and l + 32.  Per step a warp issues 19 FP64
+// instructions: 2 for its part of g = x_p^T x_q, 1 for a_qq - a_pp, 5 for the orthogonality
+// correction, 8 for the rotation, 3 for the norm updates.  The reduction of g is an exact
+// sum of 64-bit fixed-point integers (units 2^(S - 62), 2^S above ||x_p|| ||x_q|| from the
+// exponents of the norms) on the integer pipes and the angle is FP32.  (Measured per step:
+// the FP64 correction's dependent chain is shorter than the same correction in integer
+// arithmetic, whose 64-bit multiplies run one warp deep per SM sub-partition.)  A leaving column is written from registers with st.async
 // into the neighbour's ring buffer, each 8-byte store completing a transaction on the
 // neighbour's mbarrier, which its owner arms (one arrival expecting a column's bytes) for
 // every use.
@@ -358,6 +350,8 @@ __global__ void __launch_bounds__(512) onesided_jacobi_kernel(OsParams prm) {
     float sweep_mx = 0.0f;  // the largest scaled |g| met in the sweep
     int checks = 0;
     bool timed_out = false;
+    int ring = 0;            // K mod D
+    unsigned phase = 0u;     // (K / D) mod 2
     while (sweep < prm.max_sweeps) {
         ++sweep;
         if (tid == 0) { s_rot = 0; s_lmax = 0; }
@@ -374,8 +368,6 @@ __global__ void __launch_bounds__(512) onesided_jacobi_kernel(OsParams prm) {
         __syncthreads();
         for (int k = 0; k < N; ++k, ++K) {
             const int par = (int)(K & 1u);
-            const int ring = (int)(K % (unsigned)D);
-            const unsigned phase = (K / (unsigned)D) & 1u;
             if (warp < P) {
                 const int a = warp;
                 double* xp = bufs + (size_t)map_top[par][a] * OS_LD;
@@ -414,7 +406,7 @@ __global__ void __launch_bounds__(512) onesided_jacobi_kernel(OsParams prm) {
                     // sgn(0) = +1, in FP32 from ratios <= 1 (its accuracy only sets how far g is
                     // reduced; a_qq - a_pp comes from FP64: for clustered sigma the difference of two
                     // FP32 roundings would be noise); c0 = 1/sqrt(1 + t^2), s0 = t c0; the applied
-                    // rotation is (c0, s0) scaled to unit length in FP64 (os_orthogonal).
+                    // rotation is (c0, s0) scaled to unit length in FP64.
                     const float df = os_to_float(dpq);
                     const float hf = 2.0f * os_to_float(g);
                     const float adf = fabsf(df), ahf = fabsf(hf);
@@ -428,8 +420,12 @@ __global__ void __launch_bounds__(512) onesided_jacobi_kernel(OsParams prm) {
                         tf = sz * __fdividef(1.0f, z + w * rsqrtf(w));
                     }
                     const float cf = rsqrtf(fmaf(tf, tf, 1.0f));
-                    double cs, sn;
-                    os_orthogonal(cf, tf * cf, cs, sn);
+                    // (c0, s0) scaled to unit length to FP64 precision: e = c0^2 + s0^2 - 1 (exact in
+                    // FP64, |e| ~ 2^-24), f = 1 - e/2 + 3e^2/8 = (1 + e)^(-1/2) + O(e^3)
+                    const double c0 = os_to_double(cf), s0 = os_to_double(tf * cf);
+                    const double ee = fma(c0, c0, fma(s0, s0, -1.0));
+                    const double f = fma(ee, fma(ee, 0.375, -0.5), 1.0);
+                    const double cs = c0 * f, sn = s0 * f;
                     n0 = fma(cs, p0, -sn * q0);
                     n1 = fma(cs, p1, -sn * q1);
                     m0 = fma(sn, p0, cs * q0);
@@ -497,6 +493,7 @@ __global__ void __launch_bounds__(512) onesided_jacobi_kernel(OsParams prm) {
                 for (int u = 0; u < P - 1; ++u) nb_[u] = bot[u + 1];
                 nb_[P - 1] = (c == C - 1) ? top[P - 1] : RR0 + ring;
             }
+            if (++ring == D) { ring = 0; phase ^= 1u; }
             __syncthreads();
         }
         // cluster-wide rotation count and largest scaled |g| of this sweep

@@ -297,45 +297,9 @@ __global__ void __launch_bounds__(256, 1)
 }
 
 // ---------------------------------------------------------------- exact combine
-__device__ __forceinline__ int msb_u128(unsigned __int128 v) {
-    const unsigned long long hi = (unsigned long long)(v >> 64);
-    if (hi) return 127 - __clzll((long long)hi);
-    return 63 - __clzll((long long)(unsigned long long)v);
-}
-
-// Round v * 2^scale to the nearest double (ties to even); rounded_int gets
-// the exact integer value of the result in units of 2^scale.
-__device__ double round_i128(__int128 v, int scale, __int128& rounded_int) {
-    if (v == 0) { rounded_int = 0; return 0.0; }
-    const bool neg = v < 0;
-    unsigned __int128 mag = neg ? (unsigned __int128)(-v) : (unsigned __int128)v;
-    const int msb = msb_u128(mag);
-    unsigned long long mant;
-    int sh = 0;
-    if (msb <= 52) {
-        mant = (unsigned long long)mag;
-    } else {
-        sh = msb - 52;
-        mant = (unsigned long long)(mag >> sh);
-        const unsigned __int128 rem = mag - ((unsigned __int128)mant << sh);
-        const unsigned __int128 half = (unsigned __int128)1 << (sh - 1);
-        if (rem > half || (rem == half && (mant & 1ull))) ++mant;  // mant may become 2^53: still exact
-    }
-    const __int128 r = (__int128)((unsigned __int128)mant << sh);
-    rounded_int = neg ? -r : r;
-    const double d = ldexp((double)mant, sh + scale);
-    return neg ? -d : d;
-}
-
 // One warp per Gram entry (i, j), i <= j: the lanes take every 32nd partial, and the
 // exact int128 sums are added across the warp (integer addition: the result does not
 // depend on the order, so the Gram is bitwise reproducible).
-__device__ __forceinline__ __int128 shfl_xor_i128(__int128 v, int o) {
-    const unsigned long long lo = (unsigned long long)v, hi = (unsigned long long)(v >> 64);
-    const unsigned long long l2 = __shfl_xor_sync(0xffffffffu, lo, o), h2 = __shfl_xor_sync(0xffffffffu, hi, o);
-    return (__int128)(((unsigned __int128)h2 << 64) | (unsigned __int128)l2);
-}
-
 // The exact sum over P partials (slot c at c * slot (hi, lo) and c * estride
 // (exponents), NP x NP row-major) of entry (i, j), rounded to a double-double;
 // all 32 lanes of the warp take part.

@@ -66,7 +66,9 @@ constexpr int TC_DIG_BYTES = 7 * 64 * 128;         // 7 slices x 64 rows x 128 B
 constexpr int TC_SMEM = TC_SD * TC_DIG_BYTES + TC_SF * TC_FP_BYTES + 1024;  // + alignment slack
 
 // slot position of each digit (0-based digit index -> position)
-__constant__ int c_pos_of_digit[7] = {1, 2, 4, 5, 3, 6, 0};
+__host__ __device__ constexpr int tc_pos_of_digit(int s) {
+    return s == 0 ? 1 : s == 1 ? 2 : s == 2 ? 4 : s == 3 ? 5 : s == 4 ? 3 : s == 5 ? 6 : 0;
+}
 
 __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
     uint64_t d = 0;
@@ -138,7 +140,7 @@ struct TcRecord {
     int regrid[2]; // per decider warp: some dsh of its columns is non-zero
     int pad;
     int E[64];     // scale of each column for this sub-chunk's digits
-    int dsh[64];   // when newp: E_old - E_acc of the period that ends (64: nothing accumulated yet)
+    int dsh[64];   // when newp: E_old - E_acc of the period that ends (0 while nothing was accumulated)
 };
 
 struct TcShared {
@@ -222,8 +224,24 @@ __device__ __forceinline__ void tc_pin(unsigned long long (&hi)[16], uint32_t (&
                       "+r"(lo[14]), "+r"(lo[15]));
 }
 
+// Residuals of the s + t = 6 blocks: kind 2 adds RN(P / 2^RS) to lo and keeps the exact
+// remainder P - RN(P / 2^RS) 2^RS (|.| <= 2^(RS - 1)) in units of 2^-9 of lo's unit (an
+// off-diagonal block's remainder counts twice, the diagonal (3,3) block's once): two 16-bit
+// sums per 32-bit register, columns k and k + 8 (|sum| < 2^15 for R <= 2^15 rows: two blocks
+// of at most 2^9 per 1024-row period).  With them every digit-pair product is accumulated
+// exactly.
+__device__ __forceinline__ void tc_res_add(uint32_t (&res)[8], int kk, int r) {
+    res[kk & 7] += (kk < 8) ? (uint32_t)r : ((uint32_t)r << 16);
+}
+__device__ __forceinline__ int tc_res_get(const uint32_t (&res)[8], int kk) {
+    const int v = (int)res[kk & 7];
+    const int low = (int)(short)(v & 0xffff);
+    return kk < 8 ? low : ((v - low) >> 16);
+}
+
 template <int H, int CB>
-__device__ __forceinline__ void tc_fold_block(uint32_t trow, unsigned long long (&hi)[16], uint32_t (&lo)[16]) {
+__device__ __forceinline__ void tc_fold_block(uint32_t trow, unsigned long long (&hi)[16], uint32_t (&lo)[16],
+                                              uint32_t (&res)[8]) {
     constexpr TcFold F = tc_fold(H, CB);
     // two halves of 8 columns keep the temporaries few (the accumulators use 48 registers)
 #pragma unroll
@@ -232,13 +250,21 @@ __device__ __forceinline__ void tc_fold_block(uint32_t trow, unsigned long long 
         tc_pin(hi, lo);
         tmem_ld8(trow + CB * 64 + 8 * hf, r);
         if constexpr (F.kind == 2) {
-            constexpr unsigned long long C = tc_magic2(23 + F.sh - F.w);
+            constexpr unsigned long long C = tc_magic2(23 + F.sh - F.w), CR = tc_magic2(23 - F.w);
+            constexpr uint32_t PR = tc_magic(23 - F.w);
+            constexpr int RW = F.sh == 8 ? 2 : 1;  // remainder weight in units 2^-9 of lo's unit
 #pragma unroll
             for (int k = 0; k < 8; k += 2) {
-                float t0, t1;
-                f2_unpack(f2_add(f2_pack(__uint_as_float(r[k]), __uint_as_float(r[k + 1])), C), t0, t1);
+                const unsigned long long v = f2_pack(__uint_as_float(r[k]), __uint_as_float(r[k + 1]));
+                const unsigned long long t = f2_add(v, C);                  // RN(P / 2^RS) in the low bits
+                const unsigned long long u = f2_add(f2_sub(v, f2_sub(t, C)), CR);  // the exact remainder
+                float t0, t1, u0, u1;
+                f2_unpack(t, t0, t1);
+                f2_unpack(u, u0, u1);
                 lo[8 * hf + k] += __float_as_uint(t0);
                 lo[8 * hf + k + 1] += __float_as_uint(t1);
+                tc_res_add(res, 8 * hf + k, RW * (int)(__float_as_uint(u0) - PR));
+                tc_res_add(res, 8 * hf + k + 1, RW * (int)(__float_as_uint(u1) - PR));
             }
         } else {
             constexpr unsigned long long C1 = tc_magic2(23 + F.g - F.w), C2 = tc_magic2(23 - F.w);
@@ -269,15 +295,16 @@ __device__ __forceinline__ void tc_fold_block(uint32_t trow, unsigned long long 
     }
 }
 template <int H>
-__device__ __forceinline__ void tc_fold_all(uint32_t trow, unsigned long long (&hi)[16], uint32_t (&lo)[16]) {
-    tc_fold_block<H, 0>(trow, hi, lo);
-    tc_fold_block<H, 1>(trow, hi, lo);
-    tc_fold_block<H, 2>(trow, hi, lo);
-    tc_fold_block<H, 3>(trow, hi, lo);
-    tc_fold_block<H, 4>(trow, hi, lo);
-    tc_fold_block<H, 5>(trow, hi, lo);
-    tc_fold_block<H, 6>(trow, hi, lo);
-    tc_fold_block<H, 7>(trow, hi, lo);
+__device__ __forceinline__ void tc_fold_all(uint32_t trow, unsigned long long (&hi)[16], uint32_t (&lo)[16],
+                                            uint32_t (&res)[8]) {
+    tc_fold_block<H, 0>(trow, hi, lo, res);
+    tc_fold_block<H, 1>(trow, hi, lo, res);
+    tc_fold_block<H, 2>(trow, hi, lo, res);
+    tc_fold_block<H, 3>(trow, hi, lo, res);
+    tc_fold_block<H, 4>(trow, hi, lo, res);
+    tc_fold_block<H, 5>(trow, hi, lo, res);
+    tc_fold_block<H, 6>(trow, hi, lo, res);
+    tc_fold_block<H, 7>(trow, hi, lo, res);
     constexpr unsigned long long OH = tc_hi_offset(H);
     constexpr uint32_t OL = tc_lo_offset(H);
 #pragma unroll
@@ -293,10 +320,15 @@ __device__ __forceinline__ void tc_fold_all(uint32_t trow, unsigned long long (&
 // `quad` is fixed by the warp (a warp may only read its own 32 TMEM lanes),
 // columns J0..J0+15.
 __device__ __forceinline__ void tc_drain(const TcRecord& R, uint32_t tmem, int quad, int lane, int J0,
-                                         unsigned long long (&hi)[16], uint32_t (&lo)[16]) {
+                                         unsigned long long (&hi)[16], uint32_t (&lo)[16], uint32_t (&res)[8]) {
     if (R.regrid[0] | R.regrid[1]) {
-        // truncating shift onto the grid of the grown scales
+        // truncating shift onto the grid of the grown scales (the residuals are first rounded
+        // into lo: a re-grid truncates anyway)
         const int di = R.dsh[(quad * 32 + lane) & 63];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) lo[k] += (uint32_t)((tc_res_get(res, k) + 256) >> 9);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) res[k] = 0u;
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
             const int sh = di + R.dsh[J0 + k];
@@ -307,8 +339,8 @@ __device__ __forceinline__ void tc_drain(const TcRecord& R, uint32_t tmem, int q
         }
     }
     const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16) + J0;
-    if (quad < 2) tc_fold_all<0>(trow, hi, lo);   // TMEM lanes 0..63: first digit of A
-    else tc_fold_all<1>(trow, hi, lo);            // lanes 64..127: second digit
+    if (quad < 2) tc_fold_all<0>(trow, hi, lo, res);   // TMEM lanes 0..63: first digit of A
+    else tc_fold_all<1>(trow, hi, lo, res);            // lanes 64..127: second digit
 }
 
 // partial slot and status block of this CTA (batched use: those of its item)
@@ -326,7 +358,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     gram_tc_kernel(const __grid_constant__ CUtensorMap tmapA, const __grid_constant__ CUtensorMap tmapB, int64_t m,
                    int n, int split, int64_t rows_per_cta,
                    long long* __restrict__ part_hi, long long* __restrict__ part_lo, int* __restrict__ part_E,
-                   DevInfo* info, const TcBatchItem* __restrict__ items, long long wait_limit) {
+                   DevInfo* info, const TcBatchItem* __restrict__ items, long long wait_limit,
+                   const int* __restrict__ E_fixed) {
     extern __shared__ unsigned char tc_dyn[];
     // 1024-byte alignment for the swizzled operand atoms
     unsigned char* base = tc_dyn + ((1024 - (smem_addr(tc_dyn) & 1023)) & 1023);
@@ -460,17 +493,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             // above the running scale, or the exactness budget is spent) and publish a record.
             const int dw = warp - 2, j = 32 * dw + lane;
             int Ecur = EXP_EMPTY, Epend = EXP_EMPTY, Eacc = EXP_EMPTY, period_len = 0;
-            bool bad = false;
+            bool bad = false, over = false;
+            // fixed scales (E_fixed): every sub-chunk's digits are relative to the given column
+            // exponent, so nothing grows and no period is re-gridded; an entry at or above 2^E
+            // is an argument error (the exponents must bound the whole column)
+            const int Efix = (E_fixed != nullptr && j < n) ? E_fixed[j] : EXP_EMPTY;
             for (int g = 0; g <= G; ++g) {
                 const int r = g % TC_RD;
                 int fl = 0;
                 if (g < G) {
                     const int f = g % TC_SF;
-                    if (!mbar_wait(&S.fp_full[f], (g / TC_SF) & 1, wait_limit)) fl |= 4;
+                    const bool landed = mbar_wait(&S.fp_full[f], (g / TC_SF) & 1, wait_limit);
+                    if (!landed) fl |= 4;
                     // max |a| of column j on the bit patterns (Inf / NaN have the largest); the
-                    // lanes start at staggered row quads so each 16-byte load is conflict-free
+                    // lanes start at staggered row quads so each 16-byte load is conflict-free.
+                    // A stage whose wait gave up is not read (its contents are not the input).
                     unsigned mine = 0;
-                    if (j < n) {
+                    if (landed && j < n) {
                         const float* col = fpb + (size_t)f * 64 * TC_SUB + (size_t)j * TC_SUB;
 #pragma unroll 4
                         for (int k = 0; k < 16; ++k) {
@@ -485,11 +524,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     const int e = (mine == 0u || mine >= 0x7f800000u) ? EXP_EMPTY : tc_exp_above(__uint_as_float(mine));
                     // one binade above the running scale is "soft" (top digit in [-256, 256], still
                     // exact in bf16); more, or a first non-zero entry, is "hard"
-                    if (e != EXP_EMPTY) {
-                        if (Ecur == EXP_EMPTY || e > Ecur + 1) fl |= 2;
-                        else if (e == Ecur + 1) fl |= 1;
+                    if (E_fixed != nullptr) {
+                        if (e != EXP_EMPTY && e > Efix) over = true;
+                        Epend = Efix;
+                    } else {
+                        if (e != EXP_EMPTY) {
+                            if (Ecur == EXP_EMPTY || e > Ecur + 1) fl |= 2;
+                            else if (e == Ecur + 1) fl |= 1;
+                        }
+                        Epend = max(Epend, e);
                     }
-                    Epend = max(Epend, e);
                 }
                 if (g >= TC_RD && !mbar_wait(&S.dec_empty[r], ((g / TC_RD) - 1) & 1, wait_limit)) fl |= 4;
                 if (S.abort) fl |= 4;
@@ -509,7 +553,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 int dsh = 0;
                 if (newp) {
                     if (g > 0) {
-                        dsh = Eacc == EXP_EMPTY ? 64 : Ecur - Eacc;  // re-grid of the accumulators
+                        // re-grid of the accumulators.  A column whose grid is still EXP_EMPTY has
+                        // accumulated only zeros (its scale never shrinks): nothing to move, and no
+                        // re-grid is flagged for it (a flagged re-grid rounds the residuals away)
+                        dsh = Eacc == EXP_EMPTY ? 0 : Ecur - Eacc;
                         Eacc = Ecur;
                     }
                     Ecur = Epend;  // the new period starts on every grown scale
@@ -527,11 +574,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 if (lane == 0) mbar_arrive(&S.dec_full[r]);
             }
             if (bad) atomicOr(&tc_info<BATCH>(info, items)->flags, FLAG_NONFINITE);
+            if (over) atomicOr(&tc_info<BATCH>(info, items)->flags, FLAG_BAD_SCALE);
             part_E[(size_t)tc_slot<BATCH>(items) * 64 + j] = Eacc;
         }
     } else {
         // ---------------- 16 worker warps.  Per sub-chunk: take the record, write the 7 digit
-        // slices of columns w, w+16, w+32, w+48 (lane l: rows 2l, 2l+1), hand the stage to
+        // slices of columns 4w .. 4w+3 (lane l: 8 rows of one column), hand the stage to
         // the MMA; when a period closes, drain TMEM lanes 32 (w % 4).. x columns 16 (w / 4)...
         // Warps only meet on mbarriers: no CTA-wide barrier until the partials are written.
         asm volatile("setmaxnreg.inc.sync.aligned.u32 112;");
@@ -540,9 +588,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int J0 = 16 * (wq >> 2);             // drain columns J0..J0+15
         unsigned long long hi[16];
         uint32_t lo[16];
+        uint32_t res[8];
 #pragma unroll
         for (int k = 0; k < 16; ++k) { hi[k] = 0; lo[k] = 0; }
-        int drained = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) res[k] = 0u;
+        int drained = 0, res_periods = 0;
         bool failed = false;
         for (int g = 0; g <= G; ++g) {
             const int r = g % TC_RD;
@@ -558,22 +609,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 if (!__all_sync(0xffffffffu, ok)) { failed = true; break; }
                 // digits of sub-chunk g: y = 128 a 2^-E (|y| < 128, < 256 after a soft growth);
                 // digit s is y's remainder rounded to the grid 2^-8s (|digit| <= 128 grid units,
-                // exact in bf16: 8 significant bits); the MMA sees digit s scaled by 2^-8s
-                const float* fp = fpb + (size_t)f * 64 * TC_SUB + 2 * lane;
-                unsigned char* ds = dig + (size_t)d * TC_DIG_BYTES;
-                unsigned long long y[4];
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    const int j = wq + 16 * c;
-                    const int E = R.E[j];
-                    y[c] = 0ull;
-                    if (E != EXP_EMPTY) {
-                        const float2 a2 = *reinterpret_cast<const float2*>(fp + j * TC_SUB);
-                        const int k = 7 - E, k1 = k / 2, k2 = k - k1;
-                        const float s1 = __int_as_float((k1 + 127) << 23), s2 = __int_as_float((k2 + 127) << 23);
-                        y[c] = f2_mul(f2_mul(f2_pack(a2.x, a2.y), f2_pack(s1, s1)), f2_pack(s2, s2));
-                    }
+                // exact in bf16: 8 significant bits); the MMA sees digit s scaled by 2^-8s.
+                // Lane l takes rows 8 (l % 8) .. + 7 of column j = 4 w + l / 8: one 16-byte chunk
+                // of a digit slice per digit (a quarter-warp writes one slice row, 128 bytes).
+                const int jj = 4 * wq + (lane >> 3), rb = lane & 7;
+                const int E = R.E[jj];
+                unsigned long long y[4] = {0ull, 0ull, 0ull, 0ull};
+                if (E != EXP_EMPTY) {
+                    const float4* src =
+                        reinterpret_cast<const float4*>(fpb + (size_t)f * 64 * TC_SUB + (size_t)jj * TC_SUB + 8 * rb);
+                    const float4 a = src[0], b = src[1];
+                    const int k = 7 - E, k1 = k / 2, k2 = k - k1;
+                    const float s1 = __int_as_float((k1 + 127) << 23), s2 = __int_as_float((k2 + 127) << 23);
+                    const unsigned long long S1 = f2_pack(s1, s1), S2 = f2_pack(s2, s2);
+                    y[0] = f2_mul(f2_mul(f2_pack(a.x, a.y), S1), S2);
+                    y[1] = f2_mul(f2_mul(f2_pack(a.z, a.w), S1), S2);
+                    y[2] = f2_mul(f2_mul(f2_pack(b.x, b.y), S1), S2);
+                    y[3] = f2_mul(f2_mul(f2_pack(b.z, b.w), S1), S2);
                 }
+                unsigned char* drow = dig + (size_t)d * TC_DIG_BYTES + jj * 128 + ((rb ^ (jj & 7)) << 4);
 #pragma unroll
                 for (int sdig = 0; sdig < 7; ++sdig) {
                     const unsigned long long M2 = tc_magic2(23 - 8 * sdig);
@@ -587,14 +641,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         // the digit has at most 8 significant bits: its bf16 is the top half
                         bq[c] = __byte_perm(__float_as_uint(a0), __float_as_uint(a1), 0x7632);
                     }
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        const int j = wq + 16 * c;
-                        // slice position of digit s: 64 rows (columns j) of 128 bytes, 16-byte
-                        // chunks swizzled by row
-                        *reinterpret_cast<uint32_t*>(ds + c_pos_of_digit[sdig] * 8192 + j * 128 +
-                                                     ((((lane >> 2) ^ (j & 7)) << 4) | ((lane & 3) << 2))) = bq[c];
-                    }
+                    // slice position of digit s: 64 rows (columns j) of 128 bytes, 16-byte chunks
+                    // swizzled by row
+                    *reinterpret_cast<uint4*>(drow + tc_pos_of_digit(sdig) * 8192) =
+                        make_uint4(bq[0], bq[1], bq[2], bq[3]);
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncwarp();
@@ -609,7 +659,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 ok = mbar_wait(&S.acc_full, drained & 1, wait_limit);
                 if (!__all_sync(0xffffffffu, ok)) { failed = true; break; }
                 tc_fence_after();
-                tc_drain(R, tmem, quad, lane, J0, hi, lo);
+                if (res_periods == 32) {
+                    // the 16-bit residual sums hold 32 periods; more (scale growths shorten
+                    // periods) are first rounded into lo.  A CTA of fixed scales (at most 2^15
+                    // rows, 1024-row periods) never gets here.
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) lo[k] += (uint32_t)((tc_res_get(res, k) + 256) >> 9);
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) res[k] = 0u;
+                    res_periods = 0;
+                }
+                tc_drain(R, tmem, quad, lane, J0, hi, lo, res);
+                ++res_periods;
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0 && g < G) mbar_arrive(&S.acc_empty);
@@ -628,7 +689,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             if (h == hh) {
 #pragma unroll
                 for (int k = 0; k < 16; ++k) {
-                    const long long l63 = (long long)((unsigned long long)(long long)(int)lo[k] << 9);
+                    const long long l63 =
+                        (long long)((unsigned long long)(long long)(int)lo[k] << 9) + (long long)tc_res_get(res, k);
                     if (hh == 0) { ph[i * 64 + J0 + k] = (long long)hi[k]; pl[i * 64 + J0 + k] = l63; }
                     else { ph[i * 64 + J0 + k] += (long long)hi[k]; pl[i * 64 + J0 + k] += l63; }
                 }
@@ -708,7 +770,7 @@ cudaError_t launch_gram_tc2(const void* A, int64_t m, int n, int64_t lda, int c1
     if (e != cudaSuccess) return e;
     gram_tc_kernel<false><<<plan.P, TC_THREADS, TC_SMEM, s>>>(tmapA, tmapB, m, split ? 64 : n, split ? 1 : 0,
                                                               plan.rows_per_cta, ph, pl, pE, info, nullptr,
-                                                              wait_limit_of(plan.wait_cycles));
+                                                              wait_limit_of(plan.wait_cycles), plan.E_fixed);
     return cudaGetLastError();
 }
 
@@ -733,7 +795,7 @@ cudaError_t launch_gram_tc_batch(const TcBatchItem* items, int nitems, void* par
     CUtensorMap unused;
     std::memset(&unused, 0, sizeof(unused));
     gram_tc_kernel<true><<<nitems, TC_THREADS, TC_SMEM, s>>>(unused, unused, 0, 64, 0, 0, ph, pl, pE, infos, items,
-                                                             wait_limit_of(wait_cycles));
+                                                             wait_limit_of(wait_cycles), nullptr);
     return cudaGetLastError();
 }
 

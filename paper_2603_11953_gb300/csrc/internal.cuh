@@ -22,6 +22,7 @@ enum : int {
     FLAG_NOT_FULL_RANK = 2,
     FLAG_NO_CONVERGENCE = 4,
     FLAG_TIMEOUT = 8,
+    FLAG_BAD_SCALE = 16,  // a given column exponent does not bound its column
 };
 
 // Limit, in GPU clock cycles, of the steady-state bounded waits of the
@@ -37,6 +38,44 @@ struct EigSide {
     cudaStream_t stream;
     cudaEvent_t fork, join;
 };
+
+// Exact 128-bit integer helpers of the Gram combines (device only).
+__device__ __forceinline__ int msb_u128(unsigned __int128 v) {
+    const unsigned long long hi = (unsigned long long)(v >> 64);
+    if (hi) return 127 - __clzll((long long)hi);
+    return 63 - __clzll((long long)(unsigned long long)v);
+}
+
+// Round v * 2^scale to the nearest double (ties to even); rounded_int gets
+// the exact integer value of the result in units of 2^scale.
+__device__ __forceinline__ double round_i128(__int128 v, int scale, __int128& rounded_int) {
+    if (v == 0) { rounded_int = 0; return 0.0; }
+    const bool neg = v < 0;
+    unsigned __int128 mag = neg ? (unsigned __int128)(-v) : (unsigned __int128)v;
+    const int msb = msb_u128(mag);
+    unsigned long long mant;
+    int sh = 0;
+    if (msb <= 52) {
+        mant = (unsigned long long)mag;
+    } else {
+        sh = msb - 52;
+        mant = (unsigned long long)(mag >> sh);
+        const unsigned __int128 rem = mag - ((unsigned __int128)mant << sh);
+        const unsigned __int128 half = (unsigned __int128)1 << (sh - 1);
+        if (rem > half || (rem == half && (mant & 1ull))) ++mant;  // mant may become 2^53: still exact
+    }
+    const __int128 r = (__int128)((unsigned __int128)mant << sh);
+    rounded_int = neg ? -r : r;
+    const double d = ldexp((double)mant, sh + scale);
+    return neg ? -d : d;
+}
+
+__device__ __forceinline__ __int128 shfl_xor_i128(__int128 v, int o) {
+    const unsigned long long lo = (unsigned long long)v, hi = (unsigned long long)(v >> 64);
+    const unsigned long long l2 = __shfl_xor_sync(0xffffffffu, lo, o), h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+    return (__int128)(((unsigned __int128)h2 << 64) | (unsigned __int128)l2);
+}
+
 
 // Sentinel exponent of an all-zero column (no digits, nothing accumulated).
 constexpr int EXP_EMPTY = -(1 << 20);
@@ -55,6 +94,7 @@ struct GramPlan {
     int P;             // CTAs over m (split-K)
     int64_t rows_per_cta;
     long long wait_cycles = 0;  // limit of the tensor-core Gram's steady-state waits (0 = default)
+    const int* E_fixed = nullptr;  // tensor-core Gram: fixed column exponents (device, 64 ints) or null
 };
 GramPlan gram_plan(int64_t m, int n, int sm_count, int split_k_opt);
 size_t gram_partials_bytes(const GramPlan& p);
@@ -72,6 +112,19 @@ cudaError_t launch_gram_tc2(const void* A, int64_t m, int n, int64_t lda, int c1
                             void* part, DevInfo* info, cudaStream_t s);
 cudaError_t launch_gram_tc(const void* A, int64_t m, int n, int64_t lda, const GramPlan& plan, void* part,
                            DevInfo* info, cudaStream_t s);
+// Row-partitioned Gram (gram_sharded.cu).  launch_colexp: E[j] = the least e with
+// max_r |a_rj| < 2^e (EXP_EMPTY for a zero column; FP32, n <= 64; colmax_ws: n
+// unsigned).  With plan.E_fixed = E the tensor-core Gram's partials are exact
+// integers in units 2^(E_i + E_j - 63); launch_gram_limbs sums them exactly into
+// four 32-bit limbs per entry (limbs: 4 n x n int64), launch_gram_finish rounds a
+// (possibly rank-summed) limb array to G (and G_lo).
+cudaError_t launch_colexp(const float* A, int64_t m, int n, int64_t lda, unsigned* colmax_ws, int* E, DevInfo* info,
+                          int sm_count, cudaStream_t s);
+cudaError_t launch_gram_limbs(const GramPlan& plan, const void* part, int n, const int* E, long long* limbs,
+                              cudaStream_t s);
+cudaError_t launch_gram_finish(const long long* limbs, int n, const int* E, double* G, double* G_lo, int64_t ldg,
+                               cudaStream_t s);
+
 // Combine the partials into G (n x n FP64, both triangles) and optionally the
 // double-double low parts G_lo (may be null).
 cudaError_t launch_gram_combine(const GramPlan& plan, const void* part, int n, double* G,
@@ -132,6 +185,12 @@ cudaError_t launch_cholesky(const double* M, int n, int64_t ldm, double* X, int*
 // of the FP32 results) like launch_jacobi.  scratch as launch_eig_onesided.
 cudaError_t launch_eig_alg2(const double* M, int n, int64_t ldm, float tol, int max_sweeps, void* scratch,
                             double* lam_ws, double* V_ws, DevInfo* info, cudaStream_t s);
+
+// Cholesky QR, step 3 (cholqr.cu): Q from Q R = A by FP32 forward substitution per row
+// against RN_32(R), X = R^T (FP64, ld n, plain Cholesky); also R into the caller's
+// R (FP64, ldr; skipped when null).  FP32, n <= 64.
+cudaError_t launch_cholqr_q(const float* A, int64_t m, int n, int64_t lda, const double* X, float* Q, int64_t ldq,
+                            double* R, int64_t ldr, int sm_count, cudaStream_t s);
 
 // Double-double eigen stage for FP64 working (n <= 64, one CTA): pivoted
 // Cholesky of M = G + G_lo in double-double, then a one-sided Jacobi SVD of

@@ -203,6 +203,7 @@ __global__ void finalize_info_kernel(DevInfo* info) {
     const int f = info->flags;
     int st = TSVD_OK;
     if (f & FLAG_NONFINITE) st = TSVD_ERR_NONFINITE;
+    else if (f & FLAG_BAD_SCALE) st = TSVD_ERR_ARG;
     else if (f & FLAG_TIMEOUT) st = TSVD_ERR_TIMEOUT;
     else if (f & FLAG_NOT_FULL_RANK) st = TSVD_ERR_NOT_FULL_RANK;
     else if (f & FLAG_NO_CONVERGENCE) st = TSVD_ERR_NO_CONVERGENCE;

@@ -112,6 +112,15 @@ bool use_fp64_pieces(tsvd_ctx* h, int working, int64_t n) {
     return working == TSVD_FP64 && h->opts.gram_variant == 0 && n <= 64;
 }
 
+// Fixed column scales (tsvd_opts.fixed_scale, and the row-sharded entry points): FP32,
+// n <= 64, TMA-loadable input.
+tsvd_status fixed_scale_check(const void* A, int working, int64_t n, int64_t lda) {
+    if (working != TSVD_FP32 || n > 64) return TSVD_ERR_UNSUPPORTED;
+    if (!gram_tc_ok(A, working, (int)n, lda)) return TSVD_ERR_ALIGN;
+    return TSVD_OK;
+}
+constexpr size_t FIXED_EXTRA = 512;  // column maxima (n unsigned) and exponents (n int) after the partials
+
 tsvd_status run_gram_fp64(tsvd_ctx* h, const void* A, int64_t m, int n, int64_t lda, double* G, double* G_lo,
                           int64_t ldg, size_t part_off) {
     GramPlan plan = gram_tc_plan(m, 64, h->sm_count, h->opts.split_k);
@@ -152,6 +161,20 @@ tsvd_status run_gram(tsvd_ctx* h, const void* A, int64_t m, int n, int64_t lda, 
         return from_cuda(e);
     }
     if (use_fp64_pieces(h, working, n)) return run_gram_fp64(h, A, m, n, lda, G, G_lo, ldg, part_off);
+    if (h->opts.fixed_scale) {
+        // every column's exponent over the whole of A first, then the Gram on those fixed scales
+        GramPlan plan = gram_tc_plan(m, n, h->sm_count, h->opts.split_k);
+        plan.wait_cycles = h->opts.timeout_cycles;
+        char* ex = base(h) + part_off + align_up(gram_partials_bytes(plan));
+        int* E = reinterpret_cast<int*>(ex + 256);
+        e = launch_colexp(static_cast<const float*>(A), m, n, lda, reinterpret_cast<unsigned*>(ex), E, h->dinfo,
+                          h->sm_count, h->stream);
+        if (e != cudaSuccess) return from_cuda(e);
+        plan.E_fixed = E;
+        e = launch_gram_tc(A, m, n, lda, plan, base(h) + part_off, h->dinfo, h->stream);
+        if (e != cudaSuccess) return from_cuda(e);
+        return from_cuda(launch_gram_combine(plan, base(h) + part_off, n, G, G_lo, ldg, h->stream));
+    }
     const bool tc = use_tc(h, A, working, n, lda);
     if (tc && n > 64) {
         // 32-column blocks b1 < b2, one launch per pair: the cross tile always, block b1's
@@ -184,6 +207,8 @@ size_t part_bytes_for(tsvd_ctx* h, const void* A, int working, int64_t m, int n,
     if (use_fp64_pieces(h, working, n))
         return align_up(gram_partials_bytes(gram_tc_plan(m, 64, h->sm_count, h->opts.split_k))) +
                fp64_extra_bytes(m, n);
+    if (h->opts.fixed_scale)
+        return align_up(gram_partials_bytes(gram_tc_plan(m, n, h->sm_count, h->opts.split_k))) + FIXED_EXTRA;
     if (use_tc(h, A, working, n, lda)) return gram_partials_bytes(gram_tc_plan(m, n, h->sm_count, h->opts.split_k));
     return gram_partials_bytes(gram_plan(m, n, h->sm_count, h->opts.split_k));
 }
@@ -308,6 +333,8 @@ tsvd_status tsvd_create(tsvd_handle* out, int device, void* stream, const tsvd_o
         if (opts->gram_variant < 0 || opts->gram_variant > 2) return TSVD_ERR_ARG;
         if (opts->u_variant < 0 || opts->u_variant > 1) return TSVD_ERR_ARG;
         if (opts->timing < 0 || opts->timeout_cycles < 0) return TSVD_ERR_ARG;
+        if (opts->fixed_scale < 0 || opts->fixed_scale > 1) return TSVD_ERR_ARG;
+        if (opts->fixed_scale && opts->gram_variant != 0) return TSVD_ERR_UNSUPPORTED;
     }
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
@@ -367,6 +394,10 @@ tsvd_status tsvd_gram(tsvd_handle h, const void* A, int64_t m, int64_t n, int64_
         return TSVD_ERR_ARG;
     if (!gram_supported(h, A, working, n, lda)) return TSVD_ERR_UNSUPPORTED;
     if (higher == TSVD_DD && h->opts.gram_variant == 1) return TSVD_ERR_UNSUPPORTED;
+    if (h->opts.fixed_scale) {
+        const tsvd_status fs = fixed_scale_check(A, working, n, lda);
+        if (fs != TSVD_OK) return fs;
+    }
     DeviceGuard g(h->device);
     const size_t pb = part_bytes_for(h, A, working, m, (int)n, lda);
     tsvd_status st = ensure_ws(h, align_up(pb));
@@ -416,6 +447,10 @@ tsvd_status tsvd_solve(tsvd_handle h, const void* A, int64_t m, int64_t n, int64
     if (h->opts.eig_variant == EIG_ALG2 && (working != TSVD_FP32 || n > 64)) return TSVD_ERR_UNSUPPORTED;
     if (higher == TSVD_DD && h->opts.gram_variant == 1) return TSVD_ERR_UNSUPPORTED;
     if (!gram_supported(h, A, working, n, lda)) return TSVD_ERR_UNSUPPORTED;
+    if (h->opts.fixed_scale) {
+        const tsvd_status fs = fixed_scale_check(A, working, n, lda);
+        if (fs != TSVD_OK) return fs;
+    }
     DeviceGuard g(h->device);
     const Layout L = layout_for(n, part_bytes_for(h, A, working, m, (int)n, lda), working);
     tsvd_status st = ensure_ws(h, L.total);
@@ -607,6 +642,7 @@ tsvd_status tsvd_batch_solve(tsvd_handle h, int32_t count, const void* const* A,
         return TSVD_ERR_ARG;
     if (!valid_prec_pair(working, higher)) return TSVD_ERR_ARG;
     if (!(working == TSVD_FP32 && higher == TSVD_FP64)) return TSVD_ERR_UNSUPPORTED;
+    if (h->opts.fixed_scale) return TSVD_ERR_UNSUPPORTED;
     size_t need = 0;
     for (int32_t i = 0; i < count; ++i) {
         const bool want_u = U && U[i];
@@ -679,3 +715,127 @@ tsvd_status tsvd_stage_ms_mean(tsvd_handle h, int last, float ms[4]) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- row-sharded Gram (Sec. 4.2.1)
+extern "C" {
+
+tsvd_status tsvd_gram_colexp(tsvd_handle h, const void* A, int64_t m, int64_t n, int64_t lda, tsvd_prec working,
+                             int32_t* E) {
+    if (!h || !A || !E || m < 0 || n < 1 || lda < (m > 1 ? m : 1) || (working != TSVD_FP32 && working != TSVD_FP64))
+        return TSVD_ERR_ARG;
+    if (working != TSVD_FP32 || n > 64) return TSVD_ERR_UNSUPPORTED;
+    DeviceGuard g(h->device);
+    tsvd_status st = ensure_ws(h, 256);
+    if (st != TSVD_OK) return st;
+    cudaError_t e = cudaMemsetAsync(h->dinfo, 0, sizeof(DevInfo), h->stream);
+    if (e == cudaSuccess)
+        e = launch_colexp(static_cast<const float*>(A), m, (int)n, lda, reinterpret_cast<unsigned*>(h->ws), E,
+                          h->dinfo, h->sm_count, h->stream);
+    if (e == cudaSuccess) e = launch_finalize_info(h->dinfo, h->stream);
+    return from_cuda(e);
+}
+
+tsvd_status tsvd_gram_partial(tsvd_handle h, const void* A, int64_t m, int64_t n, int64_t lda, tsvd_prec working,
+                              const int32_t* E, int64_t* limbs) {
+    if (!h || !A || !E || !limbs || m < 0 || n < 1 || lda < (m > 1 ? m : 1) ||
+        (working != TSVD_FP32 && working != TSVD_FP64))
+        return TSVD_ERR_ARG;
+    const tsvd_status fs = fixed_scale_check(A, working, n, lda);
+    if (fs != TSVD_OK) return fs;
+    DeviceGuard g(h->device);
+    cudaError_t e = cudaMemsetAsync(h->dinfo, 0, sizeof(DevInfo), h->stream);
+    if (e != cudaSuccess) return from_cuda(e);
+    if (m == 0) {  // a rank without rows contributes zero
+        e = cudaMemsetAsync(limbs, 0, sizeof(int64_t) * 4 * (size_t)n * n, h->stream);
+        if (e == cudaSuccess) e = launch_finalize_info(h->dinfo, h->stream);
+        return from_cuda(e);
+    }
+    GramPlan plan = gram_tc_plan(m, (int)n, h->sm_count, h->opts.split_k);
+    plan.wait_cycles = h->opts.timeout_cycles;
+    plan.E_fixed = E;
+    tsvd_status st = ensure_ws(h, align_up(gram_partials_bytes(plan)));
+    if (st != TSVD_OK) return st;
+    e = launch_gram_tc(A, m, (int)n, lda, plan, h->ws, h->dinfo, h->stream);
+    if (e == cudaSuccess) e = launch_gram_limbs(plan, h->ws, (int)n, E, reinterpret_cast<long long*>(limbs), h->stream);
+    if (e == cudaSuccess) e = launch_finalize_info(h->dinfo, h->stream);
+    return from_cuda(e);
+}
+
+tsvd_status tsvd_gram_finish(tsvd_handle h, const int64_t* limbs, const int32_t* E, int64_t n, tsvd_prec higher,
+                             double* G, int64_t ldg) {
+    if (!h || !limbs || !E || !G || n < 1 || ldg < n || (higher != TSVD_FP64 && higher != TSVD_DD))
+        return TSVD_ERR_ARG;
+    if (n > 64) return TSVD_ERR_UNSUPPORTED;
+    DeviceGuard g(h->device);
+    return from_cuda(launch_gram_finish(reinterpret_cast<const long long*>(limbs), (int)n, E, G,
+                                        higher == TSVD_DD ? G + ldg * n : nullptr, ldg, h->stream));
+}
+
+tsvd_status tsvd_solve_gram(tsvd_handle h, const double* G, int64_t ldg, const void* A, int64_t m, int64_t n,
+                            int64_t lda, tsvd_prec working, tsvd_prec higher, void* sigma, void* V, int64_t ldv,
+                            void* U, int64_t ldu, tsvd_info* info) {
+    if (!h || !G || !sigma || !V || n < 1 || ldg < n || m < 0 || ldv < n || (U && (!A || ldu < (m > 1 ? m : 1))) ||
+        (A && lda < (m > 1 ? m : 1)) || !valid_prec_pair(working, higher))
+        return TSVD_ERR_ARG;
+    if (working != TSVD_FP32 || higher != TSVD_FP64 || n > 256) return TSVD_ERR_UNSUPPORTED;
+    if (h->opts.eig_variant == EIG_ALG2 && n > 64) return TSVD_ERR_UNSUPPORTED;
+    DeviceGuard g(h->device);
+    const Layout L = layout_for(n, 0, working);
+    tsvd_status st = ensure_ws(h, L.total);
+    if (st != TSVD_OK) return st;
+    cudaError_t e = cudaMemsetAsync(h->dinfo, 0, sizeof(DevInfo), h->stream);
+    if (e != cudaSuccess) return from_cuda(e);
+    double* lam = reinterpret_cast<double*>(base(h) + L.lam);
+    double* Vh = reinterpret_cast<double*>(base(h) + L.Vh);
+    double* scratch = reinterpret_cast<double*>(base(h) + L.scratch);
+    void* W = base(h) + L.W;
+    e = run_eig(h, G, (int)n, ldg, scratch, lam, Vh);
+    if (e == cudaSuccess)
+        e = launch_finish(lam, Vh, (int)n, working, sigma, V, ldv, W, nullptr, nullptr, 0, h->dinfo, h->stream, U_FP64);
+    if (e == cudaSuccess && U && m > 0) {
+        if (h->opts.u_variant == 0 && compute_u_tc_ok(A, working, m, (int)n, lda))
+            e = launch_compute_u_tc(static_cast<const float*>(A), m, (int)n, lda, static_cast<const float*>(W),
+                                    static_cast<float*>(U), ldu, h->sm_count, h->dinfo, h->stream);
+        else if (compute_u_v2_ok(A, working, m, (int)n, lda, U, ldu))
+            e = launch_compute_u_v2(static_cast<const float*>(A), m, (int)n, lda, static_cast<const float*>(W),
+                                    static_cast<float*>(U), ldu, h->sm_count, h->dinfo, h->stream);
+        else
+            e = launch_compute_u(A, working, m, (int)n, lda, W, U, ldu, h->stream);
+    }
+    if (e == cudaSuccess) e = launch_finalize_info(h->dinfo, h->stream);
+    if (e == cudaSuccess && info) e = cudaMemcpyAsync(info, h->dinfo, sizeof(DevInfo), cudaMemcpyDefault, h->stream);
+    return from_cuda(e);
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- mixed precision Cholesky QR (Sec. 3.1)
+extern "C" tsvd_status tsvd_cholqr(tsvd_handle h, const void* A, int64_t m, int64_t n, int64_t lda,
+                                   tsvd_prec working, tsvd_prec higher, void* Q, int64_t ldq, double* R,
+                                   int64_t ldr, tsvd_info* info) {
+    if (!h || !A || n < 1 || m < n || lda < m || (Q && ldq < m) || (R && ldr < n) || !valid_prec_pair(working, higher))
+        return TSVD_ERR_ARG;
+    if (working != TSVD_FP32 || higher != TSVD_FP64 || n > 64) return TSVD_ERR_UNSUPPORTED;
+    if (h->opts.fixed_scale) {
+        const tsvd_status fs = fixed_scale_check(A, working, n, lda);
+        if (fs != TSVD_OK) return fs;
+    }
+    DeviceGuard g(h->device);
+    const Layout L = layout_for(n, part_bytes_for(h, A, working, m, (int)n, lda), working);
+    tsvd_status st = ensure_ws(h, L.total);
+    if (st != TSVD_OK) return st;
+    cudaError_t e = cudaMemsetAsync(h->dinfo, 0, sizeof(DevInfo), h->stream);
+    if (e != cudaSuccess) return from_cuda(e);
+    double* G = reinterpret_cast<double*>(base(h) + L.G);
+    double* X = reinterpret_cast<double*>(base(h) + L.scratch);
+    int* perm = reinterpret_cast<int*>(base(h) + L.scratch + sizeof(double) * (size_t)n * n);
+    st = run_gram(h, A, m, (int)n, lda, working, G, nullptr, n, L.part);
+    if (st != TSVD_OK) return st;
+    e = launch_cholesky(G, (int)n, n, X, perm, h->dinfo, false, h->stream);
+    if (e == cudaSuccess)
+        e = launch_cholqr_q(static_cast<const float*>(A), m, (int)n, lda, X, static_cast<float*>(Q), ldq, R, ldr,
+                            h->sm_count, h->stream);
+    if (e == cudaSuccess) e = launch_finalize_info(h->dinfo, h->stream);
+    if (e == cudaSuccess && info) e = cudaMemcpyAsync(info, h->dinfo, sizeof(DevInfo), cudaMemcpyDefault, h->stream);
+    return from_cuda(e);
+}

@@ -158,6 +158,158 @@ def test_gram_powers_of_two_and_stacking_are_exact():
     assert np.array_equal(Gs, G * np.outer(sc, sc))
 
 
+# ------------------------------------------------------------------ fixed scales and the row-sharded Gram (Sec. 4.2.1)
+def test_gram_fixed_scale_bitwise_invariant():
+    """fixed_scale = 1: every entry is digited against its column's exponent over the whole A and
+    every digit-pair product is summed exactly, so the Gram is bitwise the same for any split of the
+    rows over CTAs and any order of the rows; it stays within 2^-50 (|A|^T|A|) of the exact sum."""
+    m, n = 70004, 48
+    A, _ = workloads.small_case(m, n, kappa_sigma=1e3, logd=3.0, seed=21, device="cuda")
+    A_np = workloads.to_numpy_colmajor(A, m)
+    ref = None
+    for split in (0, 1, 7, 152, 300):
+        h = handle(fixed_scale=1, split_k=split) if split else handle(fixed_scale=1)
+        Gh, Gl, st = gpu_gram(A, m, n, m, h=h, higher=T.TSVD_DD)
+        T.tsvd_destroy(h)
+        assert st == T.TSVD_OK
+        if ref is None:
+            ref = (Gh, Gl)
+            S_hi, S_lo, Sabs = oracle.gram(A_np)
+            assert np.all(np.abs((Gh - S_hi) + (Gl - S_lo)) <= 2.0 ** -50 * Sabs)
+        assert np.array_equal(Gh, ref[0]) and np.array_equal(Gl, ref[1]), split
+    perm = torch.randperm(m, generator=torch.Generator().manual_seed(3)).cuda()
+    Ap = A[:m][perm].T.contiguous().T
+    h = handle(fixed_scale=1)
+    Gh, Gl, st = gpu_gram(Ap, m, n, m, h=h, higher=T.TSVD_DD)
+    T.tsvd_destroy(h)
+    assert st == T.TSVD_OK and np.array_equal(Gh, ref[0]) and np.array_equal(Gl, ref[1])
+    # unaligned input is refused with TSVD_ERR_ALIGN
+    h = handle(fixed_scale=1)
+    G = torch.zeros(n * n, dtype=torch.float64, device="cuda")
+    assert T.tsvd_gram(h, A, m - 1, n, m - 1, T.TSVD_FP32, T.TSVD_FP64, G, n, check=False) == T.TSVD_ERR_ALIGN
+    T.tsvd_destroy(h)
+
+
+@pytest.mark.parametrize("bounds", [[0, 70004], [0, 30000, 70004], [0, 4, 40000, 40000, 70004],
+                                    [0, 12000, 24000, 36000, 48000, 70004]])
+def test_row_sharded_gram_emulated_ranks(bounds):
+    """The row-sharded entry points with the ranks emulated in one process (their all-reduces done
+    by hand on the device tensors): for one to five shards, empty shards included, the finished
+    Gram is bitwise the fixed-scale Gram of the whole A, and tsvd_solve_gram on it gives bitwise the
+    sigma and V of tsvd_solve with fixed scales, and every shard's U rows."""
+    m, n = bounds[-1], 40
+    A, _ = workloads.small_case(m, n, kappa_sigma=1e3, logd=3.0, seed=77, device="cuda")
+    # two shards on few CTAs: many 1024-row periods per CTA
+    h = handle(split_k=3) if len(bounds) == 3 else handle()
+    shards = [(bounds[k], bounds[k + 1]) for k in range(len(bounds) - 1)]
+    Es = []
+    for r0, r1 in shards:
+        E = torch.zeros(n, dtype=torch.int32, device="cuda")
+        T.tsvd_gram_colexp(h, A[r0:], r1 - r0, n, m, T.TSVD_FP32, E)
+        Es.append(E)
+    E = torch.stack(Es).max(dim=0).values.contiguous()   # the all-reduce MAX
+    limbs = torch.zeros(4, n, n, dtype=torch.int64, device="cuda")
+    for r0, r1 in shards:
+        part = torch.zeros(4, n, n, dtype=torch.int64, device="cuda")
+        T.tsvd_gram_partial(h, A[r0:], r1 - r0, n, m, T.TSVD_FP32, E, part)
+        assert T.tsvd_sync_status(h) == T.TSVD_OK
+        limbs += part                                       # the all-reduce SUM
+    G = torch.zeros(2 * n * n, dtype=torch.float64, device="cuda")
+    T.tsvd_gram_finish(h, limbs, E, n, T.TSVD_DD, G, n)
+    hf = handle(fixed_scale=1)
+    Gref, Glref, st = gpu_gram(A, m, n, m, h=hf, higher=T.TSVD_DD)
+    assert st == T.TSVD_OK
+    g = G.cpu().numpy()
+    assert np.array_equal(g[: n * n].reshape(n, n).T, Gref) and np.array_equal(g[n * n:].reshape(n, n).T, Glref)
+    # the n x n stage on every "rank" and each shard's rows of U
+    sig_ref, V_ref, U_ref, st, _ = gpu_solve(A, m, n, m, h=hf)
+    T.tsvd_destroy(hf)
+    assert st == T.TSVD_OK
+    for r0, r1 in shards:
+        sig = torch.zeros(n, device="cuda")
+        V = colmajor(n, n, torch.float32)
+        U = colmajor(max(r1 - r0, 1), n, torch.float32)
+        info = torch.zeros(6, dtype=torch.int32, device="cuda")
+        T.tsvd_solve_gram(h, G, n, A[r0:], r1 - r0, n, m, T.TSVD_FP32, T.TSVD_FP64, sig, V, n, U, max(r1 - r0, 1),
+                          info)
+        torch.cuda.synchronize()
+        assert int(info[0].item()) == T.TSVD_OK
+        assert np.array_equal(sig.cpu().numpy().astype(np.float64), sig_ref)
+        assert np.array_equal(V.cpu().numpy().astype(np.float64), V_ref)
+        if r1 > r0:
+            assert np.array_equal(U[: r1 - r0].cpu().numpy().astype(np.float64), U_ref[r0:r1])
+    # exponents that do not bound a column are reported; misaligned shards are refused
+    Ebad = E.clone()
+    Ebad[3] -= 1
+    part = torch.zeros(4, n, n, dtype=torch.int64, device="cuda")
+    T.tsvd_gram_partial(h, A, m, n, m, T.TSVD_FP32, Ebad, part)
+    assert T.tsvd_sync_status(h) == T.TSVD_ERR_ARG
+    assert T.tsvd_gram_partial(h, A[1:], m - 1, n, m, T.TSVD_FP32, E, part, check=False) == T.TSVD_ERR_ALIGN
+    T.tsvd_destroy(h)
+
+
+# ------------------------------------------------------------------ mixed precision Cholesky QR (Sec. 3.1, Theorem 3)
+@pytest.mark.parametrize("m,n,kappa,logd", [(20000, 16, 1e3, 3.0), (65537, 33, 1e2, 2.0), (131076, 64, 1e3, 3.0),
+                                            (300, 64, 10.0, 1.0)])
+def test_cholqr_matches_oracle(m, n, kappa, logd):
+    """tsvd_cholqr: R is the plain FP64 Cholesky factor of the Gram tsvd_gram returns (backward
+    error |R^T R - M| <= (n + 1) u_h |R|^T |R| componentwise); sampled rows of Q solve q R_w = a
+    for R_w = RN_32(R) with the FP32 forward substitution's backward error
+    |q R_w - a| <= n u_32 |q| |R_w| (and agree with the oracle's exactly rounded solution within the
+    matching forward bound); Q is orthogonal to O(u) kappa(B) (Theorem 3, constant 2n)."""
+    A, _ = workloads.small_case(m, n, kappa_sigma=kappa, logd=logd, seed=23 * m + n, device="cuda")
+    h = handle()
+    Q = colmajor(m, n, torch.float32)
+    R = colmajor(n, n, torch.float64)
+    info = torch.zeros(6, dtype=torch.int32, device="cuda")
+    T.tsvd_cholqr(h, A, m, n, m, T.TSVD_FP32, T.TSVD_FP64, Q, m, R, n, info)
+    torch.cuda.synchronize()
+    assert int(info[0].item()) == T.TSVD_OK
+    M, _, st = gpu_gram(A, m, n, m, h=h)
+    T.tsvd_destroy(h)
+    assert st == T.TSVD_OK
+    Rn = R.cpu().numpy()
+    assert np.array_equal(Rn, np.triu(Rn))
+    # Cholesky backward error on the same M
+    assert np.all(np.abs(Rn.T @ Rn - M) <= (n + 1) * UH * 4 * (np.abs(Rn).T @ np.abs(Rn)))
+    Ro, st_o = oracle.cholesky(M)
+    assert st_o == 0
+    d = np.sqrt(np.diag(M))
+    kC = np.linalg.cond(M / np.outer(d, d))
+    assert np.all(np.abs(Rn - Ro) <= 64 * n * UH * kC * d[None, :])  # |r_ij| <= d_j = (M_jj)^(1/2)
+    # rows of Q
+    A_np = workloads.to_numpy_colmajor(A, m)
+    Rw = Rn.astype(np.float32).astype(np.float64)
+    rows = np.unique(np.concatenate([[0, m - 1], np.linspace(0, m - 1, 40).astype(np.int64)]))
+    Qn = Q[:m].cpu().numpy().astype(np.float64)
+    resid = np.abs(Qn[rows] @ Rw - A_np[rows].astype(np.float64))
+    assert np.all(resid <= n * U32 * (np.abs(Qn[rows]) @ np.abs(Rw)) + 1e-38)
+    Qo = oracle.cholqr_rows(A_np, Rw, rows, 24)
+    # q - q_exact = q dR R_w^-1 with |dR| <= n u |R_w|, plus the rounding of q_exact
+    fwd = (n + 2) * U32 * ((np.abs(Qn[rows]) @ np.abs(Rw)) @ np.abs(np.linalg.inv(Rw))) + U32 * np.abs(Qo) + 1e-38
+    assert np.all(np.abs(Qn[rows] - Qo) <= fwd)
+    kB = math.sqrt(kC)
+    Qt = Q[:m].double()
+    orth = torch.linalg.matrix_norm(Qt.T @ Qt - torch.eye(n, dtype=torch.float64, device="cuda"), ord=2).item()
+    assert orth <= 2 * n * U32 * kB, (orth, kB)
+
+
+def test_cholqr_rank_deficient_and_args():
+    m, n = 4096, 12
+    A, _ = workloads.small_case(m, n, seed=3, device="cuda")
+    A[:, 7] = 0.0
+    h = handle()
+    Q = colmajor(m, n, torch.float32)
+    info = torch.zeros(6, dtype=torch.int32, device="cuda")
+    T.tsvd_cholqr(h, A, m, n, m, T.TSVD_FP32, T.TSVD_FP64, Q, m, None, 0, info)
+    torch.cuda.synchronize()
+    assert int(info[0].item()) == T.TSVD_ERR_NOT_FULL_RANK
+    assert T.tsvd_cholqr(h, A, n - 1, n, m, T.TSVD_FP32, T.TSVD_FP64, Q, m, check=False) == T.TSVD_ERR_ARG
+    assert T.tsvd_cholqr(h, A, m, 65, m, T.TSVD_FP32, T.TSVD_FP64, Q, m, check=False) in (T.TSVD_ERR_UNSUPPORTED,
+                                                                                            T.TSVD_ERR_ARG)
+    T.tsvd_destroy(h)
+
+
 # ------------------------------------------------------------------ Jacobi (a4-a6)
 @pytest.mark.parametrize("variant", [1, 2])
 @pytest.mark.parametrize("n,kappa,logd", [(1, 1.0, 0.0), (2, 10.0, 1.0), (7, 1e2, 2.0), (16, 1e3, 3.0),
