@@ -18,20 +18,21 @@
 //   3. The pairs are scheduled by the round-robin ("circle") tournament over
 //      a thread-block cluster.
 //
-// GB300 sets the shape of step 3.  Its FP64 unit issues one warp
-// instruction per ~64 cycles per SM sub-partition whatever the number of
-// active lanes, with a dependent latency of ~64 cycles; FP32 is ~60x faster.
+// GB300 sets the shape of step 3.  Its FP64 pipe takes one instruction of a
+// warp per ~64 cycles (independent or not, whatever the number of active
+// lanes) and about one per 19 cycles from a whole SM; FP32 is ~60x faster.
 // So (i) the pairs are spread over the 16 SMs of a (non-portable) cluster,
-// two per SM, one warp per pair, and a warp issues only the FP64
-// instructions that carry the result: 2 for its part of x_p^T x_q, 1 for the
-// norm difference, 5 for the orthogonality correction, 8 for the rotation, 3
-// for the norm updates; (ii) the reduction of the dot product (exact 64-bit
-// fixed point), the angle and the scaled test (FP32) run on the integer and
-// FP32 pipes; (iii) a column that leaves an SM is written
-// straight from registers into the neighbour's shared memory by st.async,
-// into a ring of receive buffers that the tournament maps in place, each
-// store completing a transaction on the neighbour's mbarrier: no copy, no
-// fence, no cluster-wide barrier within a sweep.
+// two per SM, two warps per pair (one row per lane), and a warp issues only
+// the FP64 instructions that carry the result: 1 for its part of x_p^T x_q,
+// 1 for the norm difference, 4 for the rotation of its rows, and either the 6
+// of the orthogonality correction or the 3 of the norm updates; (ii) the
+// reduction of the dot product (exact 64-bit fixed point), the angle and the
+// scaled test (FP32) run on the integer and FP32 pipes; (iii) a column that
+// leaves an SM is written straight from registers into the neighbour's shared
+// memory by st.async, into a ring of receive buffers whose slot of every
+// column follows from the step count in closed form, each store completing a
+// transaction on the neighbour's mbarrier: no copy, no fence, no shared map
+// and no cluster-wide barrier within a sweep.
 //
 // The rotation angle and (c0, s0) are computed in FP32 while the applied
 // rotation is made orthogonal to FP64 precision by one correction factor:
@@ -274,16 +275,49 @@ __device__ __forceinline__ long long os_to_fixed(double x, int S) {
 // CTA's barrier of step K - 2: so a ring of D = 2P + 2 buffers per side keeps every store
 // causally after the last read of the column it overwrites.
 //
-// One warp per pair, lane l holding rows l and l + 32.  Per step a warp issues 19 FP64
-// instructions: 2 for its part of g = x_p^T x_q, 1 for a_qq - a_pp, 5 for the orthogonality
-// correction, 8 for the rotation, 3 for the norm updates.  The reduction of g is an exact
-// sum of 64-bit fixed-point integers (units 2^(S - 62), 2^S above ||x_p|| ||x_q|| from the
-// exponents of the norms) on the integer pipes and the angle is FP32.  (Measured per step:
-// the FP64 correction's dependent chain is shorter than the same correction in integer
-// arithmetic, whose 64-bit multiplies run one warp deep per SM sub-partition.)  A leaving column is written from registers with st.async
-// into the neighbour's ring buffer, each 8-byte store completing a transaction on the
-// neighbour's mbarrier, which its owner arms (one arrival expecting a column's bytes) for
-// every use.
+// os_buf gives the buffer of a slot at step K in closed form (ring = K mod D): a column
+// that entered the CTA from a neighbour sits in the ring slot of the step it arrived,
+// which is a fixed number of steps back along its path through the CTA; before any
+// arrival the slot still holds an initial column.  A single-CTA cluster only rotates its
+// 2P - 1 moving columns round the circle.
+__device__ __forceinline__ int os_wrap(int v, int D) { return v < 0 ? v + D : v; }
+__device__ __forceinline__ int os_buf(int c, int C, int P, int D, int K, int ring, int u, bool top) {
+    if (C == 1) {
+        if (top && u == 0) return 0;
+        const int L = 2 * P - 1;
+        const int x = top ? u - 1 : 2 * P - 2 - u;  // position on the circle
+        const int y = ((x - K) % L + L) % L;         // where its column started
+        return y <= P - 2 ? y + 1 : 3 * P - 2 - y;
+    }
+    const int RL0 = 2 * P, RR0 = 2 * P + D;
+    if (top) {
+        if (c > 0) return K > u ? RL0 + os_wrap(ring - u - 1, D) : u - K;
+        if (u == 0) return 0;
+        if (K < u) return u - K;  // first CTA: top[u] came from bot[0] u steps back
+        return K - u > P - 1 ? RR0 + os_wrap(ring - u - P, D) : P + K - u;
+    }
+    if (c < C - 1) return K > P - 1 - u ? RR0 + os_wrap(ring - P + u, D) : P + u + K;
+    // last CTA: bot[u] came from top[P-1] P - u steps back
+    if (K <= P - 1 - u) return P + u + K;
+    if (K < 2 * P - u) return 2 * P - 1 - K - u;
+    return RL0 + os_wrap(ring - 2 * P + u, D);
+}
+__device__ __forceinline__ void os_pair_bar(int a) {
+    asm volatile("bar.sync %0, 64;" ::"r"(1 + a) : "memory");
+}
+
+// Two warps per pair (half h holds rows 32 h .. 32 h + 31, one per lane): GB300's FP64 pipe
+// takes one instruction of a warp per ~64 cycles, independent or not, and about one per 19
+// cycles from the whole SM, so the FP64 work of a step is spread over the pair's two warps.
+// Per step a warp issues 1 FP64 instruction for its part of g = x_p^T x_q, 1 for a_qq - a_pp
+// and 4 for the rotation of its rows; half 0 also the 6 of the orthogonality correction,
+// half 1 the 3 of the norm updates (they exchange their results through shared memory at a
+// 64-thread barrier).  The reduction of g is an exact sum of 64-bit fixed-point integers
+// (units 2^(S - 62), 2^S above 4 ||x_p|| ||x_q|| from the exponents of the norms) on the
+// integer pipes, over the lanes and then the two halves, and the angle is FP32.  A leaving
+// column is written from registers with st.async into the neighbour's ring buffer, each
+// 8-byte store completing a transaction on the neighbour's mbarrier, which its owner arms
+// (one arrival expecting a column's bytes) for every use.
 __global__ void __launch_bounds__(512) onesided_jacobi_kernel(OsParams prm) {
     cg::cluster_group cluster = cg::this_cluster();
     const int C = (int)cluster.num_blocks();
@@ -294,7 +328,11 @@ __global__ void __launch_bounds__(512) onesided_jacobi_kernel(OsParams prm) {
     double* bufs = sm;  // [2P + 2D][OS_LD]
     const int RL0 = 2 * P, RR0 = 2 * P + D;
     __shared__ uint64_t rbar[2][OS_MAXRING];  // [0]: from the left, [1]: from the right
-    __shared__ int map_top[2][OS_MAXP], map_bot[2][OS_MAXP];  // slot -> buffer, by step parity
+    __shared__ long long s_g[OS_MAXP][2];     // per pair: each half's part of g (fixed point)
+    __shared__ double s_rot2[OS_MAXP][2];     // per pair: the applied (cs, sn)
+    __shared__ double s_nrm[OS_MAXP][2];      // per pair: the updated squared norms
+    __shared__ double s_rc[OS_MAXP][2][2];    // per pair: recomputed squared norms, by column and half
+    __shared__ int s_rcf[OS_MAXP];            // per pair: which norms are recomputed
     __shared__ int s_rot;
     __shared__ int s_cnt[2];                // used in CTA 0: per-sweep cluster totals
     __shared__ int s_total;
@@ -307,7 +345,9 @@ __global__ void __launch_bounds__(512) onesided_jacobi_kernel(OsParams prm) {
     __shared__ float s_off[16];             // per warp: the largest scaled |g| left in the sweep
     __shared__ float s_off_cta;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int nwarps = (int)(blockDim.x >> 5);
+    const int nwarps = (int)(blockDim.x >> 5);  // 2P
+    const int a = warp >> 1, h = warp & 1;      // this warp's pair and half
+    const int row = 32 * h + lane;
     const int N = np - 1;
     const double tol2 = prm.tol * prm.tol;
     const float tol_f = (float)prm.tol;
@@ -340,12 +380,11 @@ __global__ void __launch_bounds__(512) onesided_jacobi_kernel(OsParams prm) {
         s2 = warp_sum(s2);
         if (lane == 0) { b[64] = s2; b[65] = __longlong_as_double((long long)col); }
     }
-    if (tid < P) { map_top[0][tid] = tid; map_bot[0][tid] = P + tid; }
     cluster.sync();
 
     int sweep = 0;
     bool converged = false;
-    unsigned K = 0;  // global step counter: map parity, ring slot, mbarrier phase
+    int K = 0;               // global step counter
     float best_off = 0.0f;
     float sweep_mx = 0.0f;  // the largest scaled |g| met in the sweep
     int checks = 0;
@@ -357,120 +396,133 @@ __global__ void __launch_bounds__(512) onesided_jacobi_kernel(OsParams prm) {
         if (tid == 0) { s_rot = 0; s_lmax = 0; }
         best_off = 0.0f;
         sweep_mx = 0.0f;
-        {   // exact squared norms at the start of the sweep
-            const int par = (int)(K & 1u);
-            for (int u = warp; u < 2 * P; u += nwarps) {
-                double* b = bufs + (size_t)(u < P ? map_top[par][u] : map_bot[par][u - P]) * OS_LD;
-                double s2 = warp_sum(fma(b[lane], b[lane], b[lane + 32] * b[lane + 32]));
-                if (lane == 0) b[64] = s2;
-            }
+        // exact squared norms at the start of the sweep
+        for (int u = warp; u < 2 * P; u += nwarps) {
+            double* b = bufs + (size_t)(u < P ? os_buf(c, C, P, D, K, ring, u, true)
+                                              : os_buf(c, C, P, D, K, ring, u - P, false)) * OS_LD;
+            double s2 = warp_sum(fma(b[lane], b[lane], b[lane + 32] * b[lane + 32]));
+            if (lane == 0) b[64] = s2;
         }
         __syncthreads();
         for (int k = 0; k < N; ++k, ++K) {
-            const int par = (int)(K & 1u);
-            if (warp < P) {
-                const int a = warp;
-                double* xp = bufs + (size_t)map_top[par][a] * OS_LD;
-                double* xq = bufs + (size_t)map_bot[par][a] * OS_LD;
-                const double p0 = xp[lane], p1 = xp[lane + 32], q0 = xq[lane], q1 = xq[lane + 32];
-                const double app = xp[64], aqq = xq[64];
-                const long long idp = __double_as_longlong(xp[65]), idq = __double_as_longlong(xq[65]);
-                const double dpq = aqq - app;
-                // g = x_p^T x_q: one FP64 partial per lane, summed exactly as 64-bit fixed-point
-                // integers in units 2^(S - 62), with 2^S >= 4 (a_pp a_qq)^(1/2) >= 4 sum |x_p x_q|
-                const int ea = (int)((__double_as_longlong(app) >> 52) & 0x7ff) - 1023;
-                const int eb = (int)((__double_as_longlong(aqq) >> 52) & 0x7ff) - 1023;
-                const int S = ((ea + eb + 3) >> 1) + 2;
-                long long G = os_to_fixed(fma(p0, q0, p1 * q1), S);
+            double* xp = bufs + (size_t)os_buf(c, C, P, D, K, ring, a, true) * OS_LD;
+            double* xq = bufs + (size_t)os_buf(c, C, P, D, K, ring, a, false) * OS_LD;
+            const double p0 = xp[row], q0 = xq[row];
+            const double app = xp[64], aqq = xq[64];
+            const long long idp = __double_as_longlong(xp[65]), idq = __double_as_longlong(xq[65]);
+            // g = x_p^T x_q: one FP64 product per lane, summed exactly as 64-bit fixed-point
+            // integers in units 2^(S - 62), with 2^S >= 4 (a_pp a_qq)^(1/2) >= 4 sum |x_p x_q|
+            const int ea = (int)((__double_as_longlong(app) >> 52) & 0x7ff) - 1023;
+            const int eb = (int)((__double_as_longlong(aqq) >> 52) & 0x7ff) - 1023;
+            const int S = ((ea + eb + 3) >> 1) + 2;
+            long long G = os_to_fixed(p0 * q0, S);
+            const double dpq = aqq - app;
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) G += __shfl_xor_sync(0xffffffffu, G, o);
-                const double g = os_u64_to_double((unsigned long long)(G < 0 ? -G : G), S - 62, G < 0);
-                // column ids are integer bit patterns; positive doubles have positive patterns
-                const bool live = idp < n && idq < n && __double_as_longlong(app) > 0 && __double_as_longlong(aqq) > 0;
-                // the scaled test |g| > tol sqrt(a_pp a_qq): decided in FP32 when the FP32 ratio
-                // is clearly on one side (factor 2), exactly in FP64 otherwise
-                bool rot = false;
-                if (live && G != 0) {
-                    const float gf = fabsf(os_to_float(g)), af = os_to_float(app), bf = os_to_float(aqq);
-                    const bool in_range =
-                        af > 1e-30f && af < 1e30f && bf > 1e-30f && bf < 1e30f && gf > 1e-30f && gf < 1e30f;
-                    const float rr = in_range ? gf * rsqrtf(af) * rsqrtf(bf) : 0.0f;
-                    if (in_range && rr > 2.0f * tol_f) rot = true;
-                    else if (!in_range || rr > 0.5f * tol_f) rot = g * g > tol2 * (app * aqq);
-                    if (!rot) best_off = fmaxf(best_off, rr);
-                    sweep_mx = fmaxf(sweep_mx, in_range ? rr : (rot ? 1.0f : 0.0f));
+            for (int o = 16; o > 0; o >>= 1) G += __shfl_xor_sync(0xffffffffu, G, o);
+            if (lane == 0) s_g[a][h] = G;
+            os_pair_bar(a);
+            G = s_g[a][0] + s_g[a][1];
+            const double g = os_u64_to_double((unsigned long long)(G < 0 ? -G : G), S - 62, G < 0);
+            // both halves take every decision below from the same values, so they agree.
+            // Column ids are integer bit patterns; positive doubles have positive patterns.
+            const bool live = idp < n && idq < n && __double_as_longlong(app) > 0 && __double_as_longlong(aqq) > 0;
+            // the scaled test |g| > tol sqrt(a_pp a_qq): decided in FP32 when the FP32 ratio
+            // is clearly on one side (factor 2), exactly in FP64 otherwise
+            bool rot = false;
+            if (live && G != 0) {
+                const float gf = fabsf(os_to_float(g)), af = os_to_float(app), bf = os_to_float(aqq);
+                const bool in_range =
+                    af > 1e-30f && af < 1e30f && bf > 1e-30f && bf < 1e30f && gf > 1e-30f && gf < 1e30f;
+                const float rr = in_range ? gf * rsqrtf(af) * rsqrtf(bf) : 0.0f;
+                if (in_range && rr > 2.0f * tol_f) rot = true;
+                else if (!in_range || rr > 0.5f * tol_f) rot = g * g > tol2 * (app * aqq);
+                if (!rot) best_off = fmaxf(best_off, rr);
+                sweep_mx = fmaxf(sweep_mx, in_range ? rr : (rot ? 1.0f : 0.0f));
+            }
+            double n0 = p0, m0 = q0, np2 = app, nq2 = aqq;
+            if (rot) {
+                // Rutishauser's t = sgn(zeta)/(|zeta| + sqrt(1 + zeta^2)), zeta = (a_qq - a_pp)/2g,
+                // sgn(0) = +1, in FP32 from ratios <= 1 (its accuracy only sets how far g is
+                // reduced; a_qq - a_pp comes from FP64: for clustered sigma the difference of two
+                // FP32 roundings would be noise); c0 = 1/sqrt(1 + t^2), s0 = t c0; the applied
+                // rotation is (c0, s0) scaled to unit length in FP64.
+                const float df = os_to_float(dpq);
+                const float hf = 2.0f * os_to_float(g);
+                const float adf = fabsf(df), ahf = fabsf(hf);
+                const float sz = (df == 0.0f || (df > 0.0f) == (hf > 0.0f)) ? 1.0f : -1.0f;
+                float tf;
+                if (adf >= ahf) {
+                    const float z = __fdividef(ahf, adf), w = fmaf(z, z, 1.0f);
+                    tf = sz * __fdividef(z, 1.0f + w * rsqrtf(w));
+                } else {
+                    const float z = __fdividef(adf, ahf), w = fmaf(z, z, 1.0f);
+                    tf = sz * __fdividef(1.0f, z + w * rsqrtf(w));
                 }
-                double n0 = p0, n1 = p1, m0 = q0, m1 = q1, np2 = app, nq2 = aqq;
-                if (rot) {
-                    // Rutishauser's t = sgn(zeta)/(|zeta| + sqrt(1 + zeta^2)), zeta = (a_qq - a_pp)/2g,
-                    // sgn(0) = +1, in FP32 from ratios <= 1 (its accuracy only sets how far g is
-                    // reduced; a_qq - a_pp comes from FP64: for clustered sigma the difference of two
-                    // FP32 roundings would be noise); c0 = 1/sqrt(1 + t^2), s0 = t c0; the applied
-                    // rotation is (c0, s0) scaled to unit length in FP64.
-                    const float df = os_to_float(dpq);
-                    const float hf = 2.0f * os_to_float(g);
-                    const float adf = fabsf(df), ahf = fabsf(hf);
-                    const float sz = (df == 0.0f || (df > 0.0f) == (hf > 0.0f)) ? 1.0f : -1.0f;
-                    float tf;
-                    if (adf >= ahf) {
-                        const float z = __fdividef(ahf, adf), w = fmaf(z, z, 1.0f);
-                        tf = sz * __fdividef(z, 1.0f + w * rsqrtf(w));
-                    } else {
-                        const float z = __fdividef(adf, ahf), w = fmaf(z, z, 1.0f);
-                        tf = sz * __fdividef(1.0f, z + w * rsqrtf(w));
-                    }
-                    const float cf = rsqrtf(fmaf(tf, tf, 1.0f));
-                    // (c0, s0) scaled to unit length to FP64 precision: e = c0^2 + s0^2 - 1 (exact in
-                    // FP64, |e| ~ 2^-24), f = 1 - e/2 + 3e^2/8 = (1 + e)^(-1/2) + O(e^3)
+                const float cf = rsqrtf(fmaf(tf, tf, 1.0f));
+                if (h == 0) {
+                    // (c0, s0) scaled to unit length to FP64 precision: e = c0^2 + s0^2 - 1 (exact
+                    // in FP64, |e| ~ 2^-24), f = 1 - e/2 + 3e^2/8 = (1 + e)^(-1/2) + O(e^3)
                     const double c0 = os_to_double(cf), s0 = os_to_double(tf * cf);
                     const double ee = fma(c0, c0, fma(s0, s0, -1.0));
                     const double f = fma(ee, fma(ee, 0.375, -0.5), 1.0);
-                    const double cs = c0 * f, sn = s0 * f;
-                    n0 = fma(cs, p0, -sn * q0);
-                    n1 = fma(cs, p1, -sn * q1);
-                    m0 = fma(sn, p0, cs * q0);
-                    m1 = fma(sn, p1, cs * q1);
+                    if (lane == 0) { s_rot2[a][0] = c0 * f; s_rot2[a][1] = s0 * f; }
+                } else {
                     // Within a sweep the squared norms only steer later angles and tests; they
                     // follow the exact-angle update a_pp - t g, a_qq + t g.  Every sweep starts
-                    // from exact norms, and the final sweep (no rotation) uses only those.
+                    // from exact norms, and the final sweep (no rotation) uses only those.  A
+                    // norm that dropped by 16x is recomputed (cancellation in the update).
                     const double tg = os_to_double(tf) * g;
-                    np2 = app - tg;
-                    nq2 = aqq + tg;
-                    // a norm that dropped by 16x is recomputed (cancellation in the update)
-                    if (os_hi(np2) < os_hi(app) - (4 << 20)) np2 = warp_sum(fma(n0, n0, n1 * n1));
-                    if (os_hi(nq2) < os_hi(aqq) - (4 << 20)) nq2 = warp_sum(fma(m0, m0, m1 * m1));
-                    if (lane == 0) atomicAdd(&s_rot, 1);
-                }
-                // top[P-1] leaves to the right, bot[0] to the left, from registers with its norm
-                // and id; every other column is written back in place
-                if (a == P - 1 && c < C - 1) {
-                    const uint32_t dst = os_mapa(bufs + (size_t)(RL0 + ring) * OS_LD, c + 1);
-                    const uint32_t rb = os_mapa(&rbar[0][ring], c + 1);
-                    os_st_async(dst + 8u * (unsigned)lane, n0, rb);
-                    os_st_async(dst + 8u * (unsigned)(lane + 32), n1, rb);
+                    const double u2 = app - tg, v2 = aqq + tg;
                     if (lane == 0) {
-                        os_st_async(dst + 8u * 64u, np2, rb);
-                        os_st_async(dst + 8u * 65u, __longlong_as_double(idp), rb);
+                        s_nrm[a][0] = u2;
+                        s_nrm[a][1] = v2;
+                        s_rcf[a] = (os_hi(u2) < os_hi(app) - (4 << 20) ? 1 : 0) |
+                                   (os_hi(v2) < os_hi(aqq) - (4 << 20) ? 2 : 0);
                     }
-                } else {
-                    xp[lane] = n0;
-                    xp[lane + 32] = n1;
-                    if (lane == 0) xp[64] = np2;
                 }
-                if (a == 0 && c > 0) {
-                    const uint32_t dst = os_mapa(bufs + (size_t)(RR0 + ring) * OS_LD, c - 1);
-                    const uint32_t rb = os_mapa(&rbar[1][ring], c - 1);
-                    os_st_async(dst + 8u * (unsigned)lane, m0, rb);
-                    os_st_async(dst + 8u * (unsigned)(lane + 32), m1, rb);
-                    if (lane == 0) {
-                        os_st_async(dst + 8u * 64u, nq2, rb);
-                        os_st_async(dst + 8u * 65u, __longlong_as_double(idq), rb);
-                    }
-                } else {
-                    xq[lane] = m0;
-                    xq[lane + 32] = m1;
-                    if (lane == 0) xq[64] = nq2;
+                os_pair_bar(a);
+                const double cs = s_rot2[a][0], sn = s_rot2[a][1];
+                n0 = fma(cs, p0, -sn * q0);
+                m0 = fma(sn, p0, cs * q0);
+                np2 = s_nrm[a][0];
+                nq2 = s_nrm[a][1];
+                const int rc = s_rcf[a];
+                if (rc) {
+                    const double r1 = (rc & 1) ? warp_sum(n0 * n0) : 0.0;
+                    const double r2 = (rc & 2) ? warp_sum(m0 * m0) : 0.0;
+                    if (lane == 0) { s_rc[a][0][h] = r1; s_rc[a][1][h] = r2; }
+                    os_pair_bar(a);
+                    if (rc & 1) np2 = s_rc[a][0][0] + s_rc[a][0][1];
+                    if (rc & 2) nq2 = s_rc[a][1][0] + s_rc[a][1][1];
                 }
+                if (h == 0 && lane == 0) atomicAdd(&s_rot, 1);
+            }
+            // top[P-1] leaves to the right, bot[0] to the left, from registers with its norm
+            // and id (half 1 sends those); every other column is written back in place
+            const bool lead = h == 1 && lane == 0;
+            if (a == P - 1 && c < C - 1) {
+                const uint32_t dst = os_mapa(bufs + (size_t)(RL0 + ring) * OS_LD, c + 1);
+                const uint32_t rb = os_mapa(&rbar[0][ring], c + 1);
+                os_st_async(dst + 8u * (unsigned)row, n0, rb);
+                if (lead) {
+                    os_st_async(dst + 8u * 64u, np2, rb);
+                    os_st_async(dst + 8u * 65u, __longlong_as_double(idp), rb);
+                }
+            } else {
+                xp[row] = n0;
+                if (lead) xp[64] = np2;
+            }
+            if (a == 0 && c > 0) {
+                const uint32_t dst = os_mapa(bufs + (size_t)(RR0 + ring) * OS_LD, c - 1);
+                const uint32_t rb = os_mapa(&rbar[1][ring], c - 1);
+                os_st_async(dst + 8u * (unsigned)row, m0, rb);
+                if (lead) {
+                    os_st_async(dst + 8u * 64u, nq2, rb);
+                    os_st_async(dst + 8u * 65u, __longlong_as_double(idq), rb);
+                }
+            } else {
+                xq[row] = m0;
+                if (lead) xq[64] = nq2;
             }
             // the columns arriving in this step (every thread acquires them itself); after one
             // wait has run out the rest fail at once, so a lost neighbour costs one limit
@@ -483,22 +535,13 @@ __global__ void __launch_bounds__(512) onesided_jacobi_kernel(OsParams prm) {
                 // phase has completed: an arrival on an incomplete phase would be one too many)
                 if (got_l) os_arm(&rbar[0][ring], colbytes);
                 if (got_r) os_arm(&rbar[1][ring], colbytes);
-                const int* top = map_top[par];
-                const int* bot = map_bot[par];
-                int* nt = map_top[par ^ 1];
-                int* nb_ = map_bot[par ^ 1];
-                nt[0] = (c == 0) ? top[0] : RL0 + ring;
-                nt[1] = (c == 0) ? bot[0] : top[0];
-                for (int u = 2; u < P; ++u) nt[u] = top[u - 1];
-                for (int u = 0; u < P - 1; ++u) nb_[u] = bot[u + 1];
-                nb_[P - 1] = (c == C - 1) ? top[P - 1] : RR0 + ring;
             }
             if (++ring == D) { ring = 0; phase ^= 1u; }
             __syncthreads();
         }
         // cluster-wide rotation count and largest scaled |g| of this sweep
         const int sp = sweep & 1;
-        if (lane == 0 && warp < P) atomicMax(&s_lmax, __float_as_int(sweep_mx));
+        if (lane == 0) atomicMax(&s_lmax, __float_as_int(sweep_mx));
         __syncthreads();
         if (tid == 0) {
             atomicAdd(&cluster.map_shared_rank(s_cnt, 0)[sp], s_rot);
@@ -519,9 +562,9 @@ __global__ void __launch_bounds__(512) onesided_jacobi_kernel(OsParams prm) {
         // pair of the current columns is tested at once (the same scaled test, exact norms);
         // the sweep runs only if some pair fails.
         if (mx < 0x1p-20f && sweep < prm.max_sweeps) {
-            const int par = (int)(K & 1u);
             for (int u = warp; u < 2 * P; u += nwarps) {
-                double* b = bufs + (size_t)(u < P ? map_top[par][u] : map_bot[par][u - P]) * OS_LD;
+                double* b = bufs + (size_t)(u < P ? os_buf(c, C, P, D, K, ring, u, true)
+                                                  : os_buf(c, C, P, D, K, ring, u - P, false)) * OS_LD;
                 double s2 = 0.0;
                 for (int r = lane; r < 64; r += 32) s2 = fma(b[r], b[r], s2);
                 s2 = warp_sum(s2);
@@ -533,10 +576,11 @@ __global__ void __launch_bounds__(512) onesided_jacobi_kernel(OsParams prm) {
             const int items = slots * slots * C;
             for (int it = tid; it < items; it += blockDim.x) {
                 const int u = it % slots, w = (it / slots) % slots, rk = it / (slots * slots);
-                const double* bu = bufs + (size_t)(u < P ? map_top[par][u] : map_bot[par][u - P]) * OS_LD;
-                const int* rt = cluster.map_shared_rank(&map_top[par][0], rk);
-                const int* rb = cluster.map_shared_rank(&map_bot[par][0], rk);
-                const double* bv = cluster.map_shared_rank(bufs, rk) + (size_t)(w < P ? rt[w] : rb[w - P]) * OS_LD;
+                const double* bu = bufs + (size_t)(u < P ? os_buf(c, C, P, D, K, ring, u, true)
+                                                         : os_buf(c, C, P, D, K, ring, u - P, false)) * OS_LD;
+                const double* bv = cluster.map_shared_rank(bufs, rk) +
+                                   (size_t)(w < P ? os_buf(rk, C, P, D, K, ring, w, true)
+                                                  : os_buf(rk, C, P, D, K, ring, w - P, false)) * OS_LD;
                 const long long iu = __double_as_longlong(bu[65]), iv = __double_as_longlong(bv[65]);
                 if (!(iu < iv && iv < n)) continue;
                 const double au = bu[64], av = bv[64];
@@ -563,20 +607,18 @@ __global__ void __launch_bounds__(512) onesided_jacobi_kernel(OsParams prm) {
         }
     }
     // outputs: lambda_j = ||x_j||^2, v_j = P^T x_j / ||x_j||
-    {
-        const int par = (int)(K & 1u);
-        for (int u = warp; u < 2 * P; u += nwarps) {
-            const double* b = bufs + (size_t)(u < P ? map_top[par][u] : map_bot[par][u - P]) * OS_LD;
-            const int j = (int)__double_as_longlong(b[65]);
-            if (j >= n) continue;
-            double s2 = 0.0;
-            for (int r = lane; r < 64; r += 32) s2 = fma(b[r], b[r], s2);
-            s2 = warp_sum(s2);
-            const double nrm = sqrt(s2);
-            const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
-            for (int r = lane; r < n; r += 32) prm.V[prm.perm[r] + (size_t)j * n] = b[r] * inv;
-            if (lane == 0) prm.lam[j] = s2;
-        }
+    for (int u = warp; u < 2 * P; u += nwarps) {
+        const double* b = bufs + (size_t)(u < P ? os_buf(c, C, P, D, K, ring, u, true)
+                                                : os_buf(c, C, P, D, K, ring, u - P, false)) * OS_LD;
+        const int j = (int)__double_as_longlong(b[65]);
+        if (j >= n) continue;
+        double s2 = 0.0;
+        for (int r = lane; r < 64; r += 32) s2 = fma(b[r], b[r], s2);
+        s2 = warp_sum(s2);
+        const double nrm = sqrt(s2);
+        const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+        for (int r = lane; r < n; r += 32) prm.V[prm.perm[r] + (size_t)j * n] = b[r] * inv;
+        if (lane == 0) prm.lam[j] = s2;
     }
     // info: sweeps and the largest scaled |g| seen in the last sweep
     if (lane == 0 && warp < 16) s_off[warp] = best_off;
@@ -721,7 +763,7 @@ cudaError_t launch_cluster_jacobi(OsParams prm, int C, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(C, 1, 1);
-    cfg.blockDim = dim3(32 * prm.P, 1, 1);
+    cfg.blockDim = dim3(64 * prm.P, 1, 1);  // two warps per pair
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
