@@ -164,15 +164,15 @@ __global__ void __launch_bounds__(256)
 
 // ---------------------------------------------------------------- cluster one-sided Jacobi
 constexpr int OS_LD = 66;    // a column: 64 rows (zero padded), squared norm, column id (integer bits)
-constexpr int OS_MAXRING = 18;  // receive buffers per side: 2P + 2 for P <= 8
-constexpr int OS_MAXP = 8;   // pairs per CTA
+constexpr int OS_MAXRING = 10;  // receive buffers per side: 2P + 2 for P <= 4
+constexpr int OS_MAXP = 4;   // pairs per CTA (cluster_size_for keeps P <= 4: two warps each)
 
 struct OsParams {
     const double* X;  // n x n (ld n): columns to orthogonalise (X = R^T)
     const int* perm;
     int n;            // true size
     int np;           // padded column count (multiple of 4 * clusterSize)
-    int P;            // pairs per CTA (2 <= P <= 8)
+    int P;            // pairs per CTA (2 <= P <= OS_MAXP)
     double tol;
     int max_sweeps;
     long long wait_limit;
@@ -318,7 +318,7 @@ __device__ __forceinline__ void os_pair_bar(int a) {
 // column is written from registers with st.async into the neighbour's ring buffer, each
 // 8-byte store completing a transaction on the neighbour's mbarrier, which its owner arms
 // (one arrival expecting a column's bytes) for every use.
-__global__ void __launch_bounds__(512) onesided_jacobi_kernel(OsParams prm) {
+__global__ void __launch_bounds__(64 * OS_MAXP, 1) onesided_jacobi_kernel(OsParams prm) {
     cg::cluster_group cluster = cg::this_cluster();
     const int C = (int)cluster.num_blocks();
     const int c = (int)cluster.block_rank();
@@ -350,7 +350,7 @@ __global__ void __launch_bounds__(512) onesided_jacobi_kernel(OsParams prm) {
     const int row = 32 * h + lane;
     const int N = np - 1;
     const double tol2 = prm.tol * prm.tol;
-    const float tol_f = (float)prm.tol;
+    const int T2 = (int)((__double_as_longlong(tol2) >> 52) & 0x7ff) - 1023;  // tol^2 in [2^T2, 2^(T2+1))
     const unsigned colbytes = (unsigned)(sizeof(double) * OS_LD);
 
     if (tid == 0) {
@@ -404,9 +404,10 @@ __global__ void __launch_bounds__(512) onesided_jacobi_kernel(OsParams prm) {
             if (lane == 0) b[64] = s2;
         }
         __syncthreads();
+        int bt = os_buf(c, C, P, D, K, ring, a, true), bb = os_buf(c, C, P, D, K, ring, a, false);
         for (int k = 0; k < N; ++k, ++K) {
-            double* xp = bufs + (size_t)os_buf(c, C, P, D, K, ring, a, true) * OS_LD;
-            double* xq = bufs + (size_t)os_buf(c, C, P, D, K, ring, a, false) * OS_LD;
+            double* xp = bufs + (size_t)bt * OS_LD;
+            double* xq = bufs + (size_t)bb * OS_LD;
             const double p0 = xp[row], q0 = xq[row];
             const double app = xp[64], aqq = xq[64];
             const long long idp = __double_as_longlong(xp[65]), idq = __double_as_longlong(xq[65]);
@@ -426,16 +427,21 @@ __global__ void __launch_bounds__(512) onesided_jacobi_kernel(OsParams prm) {
             // both halves take every decision below from the same values, so they agree.
             // Column ids are integer bit patterns; positive doubles have positive patterns.
             const bool live = idp < n && idq < n && __double_as_longlong(app) > 0 && __double_as_longlong(aqq) > 0;
-            // the scaled test |g| > tol sqrt(a_pp a_qq): decided in FP32 when the FP32 ratio
-            // is clearly on one side (factor 2), exactly in FP64 otherwise
+            // the scaled test |g| > tol sqrt(a_pp a_qq), decided on the exponents when they are
+            // clearly on one side: with normal g, a_pp, a_qq, g^2 / (a_pp a_qq) lies in
+            // (2^(d-2), 2^(d+2)) for d = 2 e_g - e_p - e_q, and tol^2 in [2^T, 2^(T+1)); exactly in
+            // FP64 otherwise.  The FP32 ratio only feeds the sweep statistics.
             bool rot = false;
             if (live && G != 0) {
+                const int bg = (os_hi(g) >> 20) & 0x7ff, ba = ea + 1023, bb = eb + 1023;
+                const int d = 2 * bg - ba - bb;
+                const bool normal = bg > 0 && ba > 0 && bb > 0 && bg < 0x7ff && ba < 0x7ff && bb < 0x7ff;
+                if (normal && d >= T2 + 3) rot = true;
+                else if (!normal || d >= T2 - 1) rot = g * g > tol2 * (app * aqq);
                 const float gf = fabsf(os_to_float(g)), af = os_to_float(app), bf = os_to_float(aqq);
                 const bool in_range =
                     af > 1e-30f && af < 1e30f && bf > 1e-30f && bf < 1e30f && gf > 1e-30f && gf < 1e30f;
                 const float rr = in_range ? gf * rsqrtf(af) * rsqrtf(bf) : 0.0f;
-                if (in_range && rr > 2.0f * tol_f) rot = true;
-                else if (!in_range || rr > 0.5f * tol_f) rot = g * g > tol2 * (app * aqq);
                 if (!rot) best_off = fmaxf(best_off, rr);
                 sweep_mx = fmaxf(sweep_mx, in_range ? rr : (rot ? 1.0f : 0.0f));
             }
@@ -446,23 +452,26 @@ __global__ void __launch_bounds__(512) onesided_jacobi_kernel(OsParams prm) {
                 // reduced; a_qq - a_pp comes from FP64: for clustered sigma the difference of two
                 // FP32 roundings would be noise); c0 = 1/sqrt(1 + t^2), s0 = t c0; the applied
                 // rotation is (c0, s0) scaled to unit length in FP64.
+                // Taken by half angles: tan 2theta = |2g| / |a_qq - a_pp|, theta in [0, pi/4];
+                // cos 2theta and sin 2theta from the ratio (<= 1) of the smaller to the larger,
+                // then c0 = (1 + cos 2theta) / (2 (1 + cos 2theta))^(1/2) = cos theta and
+                // |s0| = sin 2theta / (2 (1 + cos 2theta))^(1/2) = sin theta (1 + cos 2theta >= 1:
+                // no cancellation); t = tan theta = sin 2theta / (1 + cos 2theta).
                 const float df = os_to_float(dpq);
                 const float hf = 2.0f * os_to_float(g);
                 const float adf = fabsf(df), ahf = fabsf(hf);
                 const float sz = (df == 0.0f || (df > 0.0f) == (hf > 0.0f)) ? 1.0f : -1.0f;
-                float tf;
-                if (adf >= ahf) {
-                    const float z = __fdividef(ahf, adf), w = fmaf(z, z, 1.0f);
-                    tf = sz * __fdividef(z, 1.0f + w * rsqrtf(w));
-                } else {
-                    const float z = __fdividef(adf, ahf), w = fmaf(z, z, 1.0f);
-                    tf = sz * __fdividef(1.0f, z + w * rsqrtf(w));
-                }
-                const float cf = rsqrtf(fmaf(tf, tf, 1.0f));
+                const bool dbig = adf >= ahf;
+                const float z = ahf == 0.0f ? 0.0f : (dbig ? __fdividef(ahf, adf) : __fdividef(adf, ahf));
+                const float r2 = rsqrtf(fmaf(z, z, 1.0f));
+                const float c2 = dbig ? r2 : z * r2, s2 = dbig ? z * r2 : r2;
+                const float u2 = 1.0f + c2;
+                const float q2 = rsqrtf(2.0f * u2);
+                const float cf = u2 * q2, sf = sz * (s2 * q2);
                 if (h == 0) {
                     // (c0, s0) scaled to unit length to FP64 precision: e = c0^2 + s0^2 - 1 (exact
                     // in FP64, |e| ~ 2^-24), f = 1 - e/2 + 3e^2/8 = (1 + e)^(-1/2) + O(e^3)
-                    const double c0 = os_to_double(cf), s0 = os_to_double(tf * cf);
+                    const double c0 = os_to_double(cf), s0 = os_to_double(sf);
                     const double ee = fma(c0, c0, fma(s0, s0, -1.0));
                     const double f = fma(ee, fma(ee, 0.375, -0.5), 1.0);
                     if (lane == 0) { s_rot2[a][0] = c0 * f; s_rot2[a][1] = s0 * f; }
@@ -471,7 +480,7 @@ __global__ void __launch_bounds__(512) onesided_jacobi_kernel(OsParams prm) {
                     // follow the exact-angle update a_pp - t g, a_qq + t g.  Every sweep starts
                     // from exact norms, and the final sweep (no rotation) uses only those.  A
                     // norm that dropped by 16x is recomputed (cancellation in the update).
-                    const double tg = os_to_double(tf) * g;
+                    const double tg = os_to_double(sz * __fdividef(s2, u2)) * g;
                     const double u2 = app - tg, v2 = aqq + tg;
                     if (lane == 0) {
                         s_nrm[a][0] = u2;
@@ -537,6 +546,9 @@ __global__ void __launch_bounds__(512) onesided_jacobi_kernel(OsParams prm) {
                 if (got_r) os_arm(&rbar[1][ring], colbytes);
             }
             if (++ring == D) { ring = 0; phase ^= 1u; }
+            // the next step's slots, off the path that follows the barrier
+            bt = os_buf(c, C, P, D, K + 1, ring, a, true);
+            bb = os_buf(c, C, P, D, K + 1, ring, a, false);
             __syncthreads();
         }
         // cluster-wide rotation count and largest scaled |g| of this sweep
@@ -757,6 +769,7 @@ int cluster_size_for(int n, bool allow16) {
 cudaError_t launch_cluster_jacobi(OsParams prm, int C, cudaStream_t s) {
     prm.np = ((prm.n < 4 ? 4 : prm.n) + 4 * C - 1) / (4 * C) * (4 * C);
     prm.P = prm.np / (2 * C);
+    if (prm.P > OS_MAXP) return cudaErrorNotSupported;
     const size_t smem = sizeof(double) * (size_t)(2 * prm.P + 2 * (2 * prm.P + 2)) * OS_LD;
     cudaError_t e =
         cudaFuncSetAttribute(onesided_jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
