@@ -396,8 +396,9 @@ def test_solve_matches_oracle(m, n, kappa, logd, variant):
 
 
 def test_batch_matches_single_solves_and_exact_u():
-    """The batched launches (Gram work items on the CUDA-core Ozaki kernel, one CTA per instance for
-    the n x n stage) against single solves (tensor-core Gram, cluster Jacobi): both are the same
+    """The batched launches (Gram work items on the tcgen05 kernel for instances whose A is 16-byte
+    aligned with lda a multiple of 4, on the mma.sync Ozaki kernel otherwise; one CTA per instance
+    for the n x n stage) against single solves (tensor-core Gram, cluster Jacobi): both are the same
     exact Gram and FP64 Jacobi up to rounding, so sigma agrees to 2 FP32 ulps and V to 1e-4 (well
     separated spectra); U against the exact product with the batch's own W, (n + 1) u_32 (|A| |W|)."""
     cases = [(3000, 8), (1024, 16), (7777, 24), (2048, 64), (4096, 1), (40000, 48), (16385, 33), (130, 8), (200, 32),
