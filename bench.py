@@ -6,10 +6,15 @@ FP64 Jacobi, sort/cast, U) on one resident synthetic instance of the
 quoted on).  Prints ONE JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload NAME] [--no-cpu-baseline] [--no-plain]
+                  [--workload NAME] [--no-cpu-baseline] [--no-plain] [--sharded | --replicas]
 
-With torchrun (N > 1) every rank runs its own replica (independent
-instances, no data-path collective): weak scaling.
+With torchrun (N > 1) the FP32 workloads run row-sharded (Sec. 4.2.1): every
+rank holds its own m rows of an (N m) x n matrix, the Gram is formed with one
+all-reduce MAX of the column exponents and one all-reduce SUM of the exact
+integer limbs (NCCL), and every rank runs the n x n stage and its rows of U:
+weak scaling.  --replicas runs independent instances instead; --sharded takes
+the sharded path at N = 1 too (under torchrun with a one-rank NCCL group, so
+the collectives run).
 """
 from __future__ import annotations
 
@@ -157,11 +162,13 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def dist_setup(n_gpus):
+def dist_setup(n_gpus, force=False):
+    """RANK/LOCAL_RANK/WORLD_SIZE from the launcher; a process group for several ranks, or for one
+    rank under a launcher when `force` (the row-sharded path then runs its collectives)."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
+    if world > 1 or (force and "MASTER_ADDR" in os.environ):
         import torch
         import torch.distributed as dist
         backend = "nccl" if torch.cuda.is_available() else "gloo"
@@ -402,6 +409,10 @@ def main():
     ap.add_argument("--cpu-rows", type=int, default=32768)
     ap.add_argument("--ref-rows", type=int, default=16384)
     ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--sharded", action="store_true",
+                    help="row-sharded solve (each rank's rows; one all-reduce of the exact Gram limbs); "
+                         "the default with several ranks")
+    ap.add_argument("--replicas", action="store_true", help="several ranks: independent replicas instead")
     ap.add_argument("--rows", type=int, default=0,
                     help="smaller m of the same workload (profiling captures); 0 = the workload's m")
     args = ap.parse_args()
@@ -416,7 +427,7 @@ def main():
     import paper_2603_11953_gb300 as T
     from paper_2603_11953_gb300 import workloads
 
-    world, rank, local = dist_setup(args.gpus)
+    world, rank, local = dist_setup(args.gpus, force=args.sharded)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     spec = workloads.CONFIGS[args.workload]
@@ -434,8 +445,25 @@ def main():
     U = torch.zeros(n, m, dtype=wdt, device=dev)
     info = torch.zeros(6, dtype=torch.int32, device=dev)
 
-    def step():
-        T.tsvd_solve(h, A, m, n, m, working, higher, sigma, V, n, U, m, info)
+    # Row-sharded (Sec. 4.2.1): every rank holds its own m rows (seeded by rank) of a (world m) x n
+    # matrix; the Gram is formed from one all-reduce MAX of the column exponents and one all-reduce
+    # SUM of the exact integer limbs, every rank runs the n x n stage and its own rows of U.
+    use_shard = (args.sharded or (world > 1 and not args.replicas)) and working == T.TSVD_FP32 and n <= 64
+    gram_ev = []
+    if use_shard:
+        from paper_2603_11953_gb300 import sharded
+        ops = sharded.LibraryOps(h, check=False)
+
+        def step():
+            g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            g0.record(stream)
+            G = sharded.sharded_gram(A, m, n, m, ops)
+            g1.record(stream)
+            ops.solve(G, A, m, n, m, sigma, V, U, m, info)
+            gram_ev.append((g0, g1))
+    else:
+        def step():
+            T.tsvd_solve(h, A, m, n, m, working, higher, sigma, V, n, U, m, info)
 
     for _ in range(args.warmup):
         step()
@@ -456,6 +484,10 @@ def main():
     # per-stage device times averaged over the timed steps (events the library recorded on
     # its stream around each stage of each call)
     stage_ms = T.tsvd_stage_ms_mean(h, min(args.steps, 1024))
+    if use_shard:
+        # the Gram stage (exponents, partial, both all-reduces, finish) from this loop's events
+        gms = sum(a.elapsed_time(b) for a, b in gram_ev[-args.steps:]) / args.steps
+        stage_ms = [gms, stage_ms[1], stage_ms[2], gms + stage_ms[3]]
     ms_total = max_over_ranks(ms_total, world, dev)
     ms_step = ms_total / args.steps
     bytes_A = m * n * esize
@@ -475,7 +507,8 @@ def main():
         for _ in range(2):
             st_ = torch.cuda.Stream(dev)
             hh, _ = T.tsvd_create(local, st_.cuda_stream, T.tsvd_opts())
-            lanes.append(dict(s=st_, h=hh, c=[torch.cuda.Stream(dev) for _ in range(NCS)],
+            lanes.append(dict(s=st_, h=hh, ops=sharded.LibraryOps(hh, check=False) if use_shard else None,
+                              c=[torch.cuda.Stream(dev) for _ in range(NCS)],
                               A=torch.empty((n, m), dtype=wdt, device=dev),
                               U=torch.empty((n, m), dtype=wdt, device=dev), sig=torch.empty(n, dtype=wdt, device=dev),
                               V=torch.empty((n, n), dtype=wdt, device=dev),
@@ -495,7 +528,11 @@ def main():
             for c in L["c"]:
                 L["s"].wait_stream(c)
             with torch.cuda.stream(L["s"]):
-                T.tsvd_solve(L["h"], L["A"], m, n, m, working, higher, L["sig"], L["V"], n, L["U"], m, L["info"])
+                if use_shard:
+                    sharded.sharded_solve(L["A"].T, m, n, m, L["sig"], L["V"], L["ops"], L["U"], m, L["info"])
+                else:
+                    T.tsvd_solve(L["h"], L["A"], m, n, m, working, higher, L["sig"], L["V"], n, L["U"], m,
+                                 L["info"])
             for c in L["c"]:
                 c.wait_stream(L["s"])
             for i in range(NCH):
@@ -595,7 +632,8 @@ def main():
         if n <= 64:
             # pivoted Cholesky n^3/3, then per sweep every pair's dot product (2n) and rotation (6n)
             eig_flops = n ** 3 / 3.0 + sweeps * (n * (n - 1) // 2) * 8 * n
-            launches = KERNELS_PER_STEP
+            # row-sharded: column maxima, exponents, limbs and finish instead of the combine
+            launches = KERNELS_PER_STEP + (3 if use_shard else 0)
         else:
             # two-sided: per pair, rows and columns p, q of M (8n) and of V (6n)
             eig_flops = sweeps * (n * (n - 1) // 2) * 14.0 * n
@@ -648,7 +686,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "fp32" if working == T.TSVD_FP32 else "fp64", "data": "synthetic",
             "config": {"workload": spec.name, "m": m, "n": n, "working": "fp32" if working == 0 else "fp64",
-                       "higher": "fp64" if higher == 1 else "dd", "parallelism": f"replicas{world}",
+                       "higher": "fp64" if higher == 1 else "dd",
+                       "parallelism": f"rowshard{world}" if use_shard else f"replicas{world}",
                        "eig": "pivoted Cholesky + one-sided Jacobi (FP64, 16-CTA cluster)" if n <= 64 and
                               working == T.TSVD_FP32 else "default for this shape",
                        "u": "tcgen05 3-term TF32 split" if working == T.TSVD_FP32 and n <= 64 else "CUDA cores",
@@ -660,8 +699,8 @@ def main():
     T.tsvd_destroy(h)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    if world > 1:
-        import torch.distributed as dist
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
         dist.destroy_process_group()
     return 0
 

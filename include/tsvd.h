@@ -211,9 +211,10 @@ TSVD_API tsvd_status tsvd_batch_solve(tsvd_handle h, int32_t count, const void* 
  * TSVD_ERR_NO_CONVERGENCE) or TSVD_ERR_CUDA. */
 TSVD_API tsvd_status tsvd_sync_status(tsvd_handle h);
 
-/* Per-stage device times of the last tsvd_solve (requires opts.timing = 1):
- * ms[0] Gram (split + MMA + combine), ms[1] eigensolver (scaling, Jacobi,
- * sort, cast), ms[2] compute U, ms[3] total.  Synchronises the stream.
+/* Per-stage device times of the last tsvd_solve or tsvd_solve_gram (requires
+ * opts.timing >= 1): ms[0] Gram (split + MMA + combine; 0 for tsvd_solve_gram,
+ * whose caller formed G), ms[1] eigensolver (scaling, Jacobi, sort, cast),
+ * ms[2] compute U, ms[3] total.  Synchronises the stream.
  * These are the components of the paper's time breakdown (Sec. 4.1.2). */
 TSVD_API tsvd_status tsvd_last_stage_ms(tsvd_handle h, float ms[4]);
 

@@ -789,9 +789,13 @@ tsvd_status tsvd_solve_gram(tsvd_handle h, const double* G, int64_t ldg, const v
     double* Vh = reinterpret_cast<double*>(base(h) + L.Vh);
     double* scratch = reinterpret_cast<double*>(base(h) + L.scratch);
     void* W = base(h) + L.W;
+    // stage events as tsvd_solve records them; the Gram stage is empty here (the caller formed G)
+    record(h, 0);
+    record(h, 1);
     e = run_eig(h, G, (int)n, ldg, scratch, lam, Vh);
     if (e == cudaSuccess)
         e = launch_finish(lam, Vh, (int)n, working, sigma, V, ldv, W, nullptr, nullptr, 0, h->dinfo, h->stream, U_FP64);
+    if (e == cudaSuccess) record(h, 2);
     if (e == cudaSuccess && U && m > 0) {
         if (h->opts.u_variant == 0 && compute_u_tc_ok(A, working, m, (int)n, lda))
             e = launch_compute_u_tc(static_cast<const float*>(A), m, (int)n, lda, static_cast<const float*>(W),
@@ -801,6 +805,11 @@ tsvd_status tsvd_solve_gram(tsvd_handle h, const double* G, int64_t ldg, const v
                                     static_cast<float*>(U), ldu, h->sm_count, h->dinfo, h->stream);
         else
             e = launch_compute_u(A, working, m, (int)n, lda, W, U, ldu, h->stream);
+    }
+    if (e == cudaSuccess && h->opts.timing) {
+        record(h, 3);
+        h->have_times = true;
+        ++h->calls;
     }
     if (e == cudaSuccess) e = launch_finalize_info(h->dinfo, h->stream);
     if (e == cudaSuccess && info) e = cudaMemcpyAsync(info, h->dinfo, sizeof(DevInfo), cudaMemcpyDefault, h->stream);

@@ -22,12 +22,17 @@ from . import (TSVD_FP32, TSVD_FP64, tsvd_gram_colexp, tsvd_gram_finish, tsvd_gr
 
 
 class LibraryOps:
-    """The per-rank steps on the library's kernels (handle h, FP32 working precision)."""
+    """The per-rank steps on the library's kernels (handle h, FP32 working precision).  With
+    check=False nothing synchronises the host: numeric outcomes are read from `info` after the
+    solve (a timing loop runs this way)."""
 
-    def __init__(self, h):
+    def __init__(self, h, check=True):
         self.h = h
+        self.check = check
 
     def _sync(self, name):
+        if not self.check:
+            return
         st = tsvd_sync_status(self.h)
         if st != TSVD_OK:
             raise TsvdError(name, st)
@@ -53,17 +58,18 @@ class LibraryOps:
         tsvd_solve_gram(self.h, G, n, A, m, n, lda, TSVD_FP32, TSVD_FP64, sigma, V, n, U, ldu, info)
 
 
-def _world(group):
-    return dist.get_world_size(group) if dist.is_available() and dist.is_initialized() else 1
+def _distributed():
+    # any initialised process group takes part, a one-rank group included
+    return dist.is_available() and dist.is_initialized()
 
 
 def sharded_gram(A, m, n, lda, ops, group=None):
     """G = A^T A over all ranks' rows (this rank holds A: m x n, leading dimension lda)."""
     E = ops.colexp(A, m, n, lda)
-    if _world(group) > 1:
+    if _distributed():
         dist.all_reduce(E, op=dist.ReduceOp.MAX, group=group)   # the exponents must bound every rank's rows
     limbs = ops.partial(A, m, n, lda, E)
-    if _world(group) > 1:
+    if _distributed():
         dist.all_reduce(limbs, op=dist.ReduceOp.SUM, group=group)  # integer sums: exact in any order
     return ops.finish(limbs, E, n)
 
