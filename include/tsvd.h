@@ -7,10 +7,10 @@
  * u_h:
  *   1. M_h = A^T A formed in the higher precision          (Alg. 1 lines 1-2)
  *   2. M_h = V_h Sigma_h^2 V_h^T in the higher precision   (Alg. 1 line 3): by
- *      default (n <= 64) a pivoted Cholesky M_h = R^T R followed by a
+ *      default (n <= 256) a pivoted Cholesky M_h = R^T R followed by a
  *      one-sided Jacobi SVD of R^T (the factor-then-SVD structure of Alg. 2,
- *      all in the higher precision); two-sided Jacobi on M_h (Sec. 2.1) for
- *      n > 64 or on request (tsvd_opts.eig_variant)
+ *      all in the higher precision); two-sided Jacobi on M_h (Sec. 2.1) on
+ *      request (tsvd_opts.eig_variant); Algorithm 2 as written on request
  *   3. Sigma, V rounded to working precision               (Alg. 1 lines 4-5)
  *   4. U = A (V Sigma^{-1}) in working precision           (Alg. 1 line 6)
  *
@@ -78,9 +78,10 @@ typedef struct {
     double jacobi_tol;     /* skip test |m_pq| <= tol*sqrt(m_pp m_qq) (default n * 2^-53; n * 2^-104
                               for the double-double n x n stage of FP64 working precision) */
     int max_sweeps;        /* Jacobi sweep limit (default 40) */
-    int eig_variant;       /* 0 = default (2 for n <= 64, else 1); 1 = two-sided
+    int eig_variant;       /* 0 = default (2 for n <= 256, else 1); 1 = two-sided
                               Jacobi on M_h (Sec. 2.1); 2 = pivoted Cholesky of M_h
-                              + one-sided Jacobi on R^T, both in FP64 (n <= 64);
+                              + one-sided Jacobi on R^T over a thread-block cluster,
+                              both in FP64 (n <= 256);
                               3 = Algorithm 2 as the paper writes it: plain FP64
                               Cholesky M_h = R_h^T R_h, R = RN_32(R_h), SVD of R in
                               FP32 by one-sided Jacobi (skip threshold n 2^-24 unless
@@ -124,7 +125,8 @@ typedef struct {
                          iterations on the pivoted Cholesky factor of C (an
                          under-estimate, typically within a few per cent); +Inf when
                          M_h is not positive definite; 0 where not computed (the
-                         two-sided n x n stage, the double-double stage, batches) */
+                         two-sided n x n stage, the double-double stage, batches,
+                         n > 64) */
 } tsvd_info;
 
 /* Create a handle bound to `device` and `stream` (a cudaStream_t; NULL = the

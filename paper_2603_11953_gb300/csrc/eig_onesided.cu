@@ -162,10 +162,116 @@ __global__ void __launch_bounds__(256)
     if (tid == 0 && deficient) atomicOr(&info->flags, FLAG_NOT_FULL_RANK);
 }
 
+// 64 < n <= 256: the same factorization with the Schur complement S (lower triangle by original
+// index) and the rows of R in global scratch (2 n^2 doubles, L2-resident), one CTA of 1024
+// threads.  Thread o < n owns index o for the pivot search and the ascending list of the
+// remaining indices, which a ballot per warp and the warps' counts build without a serial pass.
+__global__ void __launch_bounds__(1024, 1)
+    chol_piv_gm_kernel(const double* __restrict__ M, int n, int64_t ldm, double* __restrict__ S,
+                       double* __restrict__ Rr, double* __restrict__ X, int* __restrict__ perm_out, DevInfo* info,
+                       int pivot) {
+    __shared__ int s_list[256];
+    __shared__ int s_perm[256];
+    __shared__ unsigned char s_rem[256];
+    __shared__ long long s_key[32];
+    __shared__ int s_idx[32];
+    __shared__ int s_cnt[8];
+    __shared__ int s_ok;
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    for (int idx = tid; idx < n * n; idx += nt) {
+        const int r = idx % n, c = idx / n;
+        S[idx] = r >= c ? M[r + (size_t)c * ldm] : 0.0;
+        Rr[idx] = 0.0;
+    }
+    for (int i = tid; i < 256; i += nt) s_rem[i] = i < n ? 1 : 0;
+    __syncthreads();
+    bool deficient = false;
+    int kend = n;
+    for (int k = 0; k < n; ++k) {
+        // pivot: the largest remaining diagonal, lowest original index on ties (non-negative doubles
+        // order like their bit patterns; every negative value sorts below them); without
+        // pivoting the remaining indices are k..n-1 in order
+        if (pivot) {
+            long long key = LLONG_MIN;
+            int bo = n;
+            if (tid < n && s_rem[tid]) {
+                const long long dd = __double_as_longlong(S[tid + (size_t)tid * n]);
+                key = dd < 0 ? LLONG_MIN + 1 : dd;
+                bo = tid;
+            }
+            for (int off = 16; off > 0; off >>= 1) {
+                const long long ob = __shfl_xor_sync(0xffffffffu, key, off);
+                const int oo = __shfl_xor_sync(0xffffffffu, bo, off);
+                if (ob > key || (ob == key && oo < bo)) { key = ob; bo = oo; }
+            }
+            if (lane == 0) { s_key[warp] = key; s_idx[warp] = bo; }
+            __syncthreads();
+            if (warp == 0) {
+                key = lane < nw ? s_key[lane] : LLONG_MIN;
+                bo = lane < nw ? s_idx[lane] : n;
+                for (int off = 16; off > 0; off >>= 1) {
+                    const long long ob = __shfl_xor_sync(0xffffffffu, key, off);
+                    const int oo = __shfl_xor_sync(0xffffffffu, bo, off);
+                    if (ob > key || (ob == key && oo < bo)) { key = ob; bo = oo; }
+                }
+                if (lane == 0) s_ok = bo;
+            }
+            __syncthreads();
+        }
+        const int ok = pivot ? s_ok : k;
+        const double d = S[ok + (size_t)ok * n];
+        if (!(d > 0.0)) { deficient = true; kend = k; break; }
+        const double rinv = chol_rsqrt(d);  // 1 / r_kk
+        // row k of R over the remaining indices and their ascending list (without ok)
+        bool keep = false;
+        if (tid < n) {
+            keep = s_rem[tid] && tid != ok;
+            if (tid == ok) Rr[(size_t)k * n + tid] = d * rinv;
+            else if (keep) Rr[(size_t)k * n + tid] = chol_S(S, n, tid, ok) * rinv;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        if (lane == 0 && warp < 8) s_cnt[warp] = __popc(bal);
+        __syncthreads();
+        if (keep) {
+            int pos = __popc(bal & ((1u << lane) - 1u));
+            for (int w = 0; w < warp; ++w) pos += s_cnt[w];
+            s_list[pos] = tid;
+        }
+        if (tid == 0) { s_perm[k] = ok; s_rem[ok] = 0; }
+        __syncthreads();
+        // trailing update S(a, b) -= R[k][a] R[k][b] over the remaining lower triangle: the warps
+        // take its columns b (round robin), the lanes its rows a >= b
+        const int rc = n - 1 - k;
+        const double* rk = Rr + (size_t)k * n;
+        for (int jb = warp; jb < rc; jb += nw) {
+            const int b = s_list[jb];
+            const double rb = rk[b];
+            for (int ia = jb + lane; ia < rc; ia += 32) {
+                const int a = s_list[ia];
+                S[a + (size_t)b * n] -= rk[a] * rb;
+            }
+        }
+        __syncthreads();
+    }
+    // X = R^T with rows in pivot order; past a rank deficiency the remaining positions take the
+    // remaining indices in ascending order
+    if (tid == 0) {
+        int pos = kend;
+        for (int o = 0; o < n; ++o)
+            if (s_rem[o]) s_perm[pos++] = o;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < n * n; idx += nt) {
+        const int pos = idx % n, c = idx / n;
+        X[idx] = (pos >= c && c < kend) ? Rr[(size_t)c * n + s_perm[pos]] : 0.0;
+    }
+    for (int i = tid; i < n; i += nt) perm_out[i] = s_perm[i];
+    if (tid == 0 && deficient) atomicOr(&info->flags, FLAG_NOT_FULL_RANK);
+}
+
 // ---------------------------------------------------------------- cluster one-sided Jacobi
-constexpr int OS_LD = 66;    // a column: 64 rows (zero padded), squared norm, column id (integer bits)
-constexpr int OS_MAXRING = 10;  // receive buffers per side: 2P + 2 for P <= 4
-constexpr int OS_MAXP = 4;   // pairs per CTA (cluster_size_for keeps P <= 4: two warps each)
+constexpr int OS_MAXRING = 18;  // receive buffers per side: 2P + 2 for P <= 8
+constexpr int OS_MAXP = 8;   // pairs per CTA (n <= 256 on 16 CTAs: two warps each)
 
 struct OsParams {
     const double* X;  // n x n (ld n): columns to orthogonalise (X = R^T)
@@ -318,14 +424,18 @@ __device__ __forceinline__ void os_pair_bar(int a) {
 // column is written from registers with st.async into the neighbour's ring buffer, each
 // 8-byte store completing a transaction on the neighbour's mbarrier, which its owner arms
 // (one arrival expecting a column's bytes) for every use.
+// RPL rows per lane and half: columns of 64 RPL rows (n <= 64 RPL); lane l of half h holds rows
+// 32 h + l + 64 i, i < RPL.
+template <int RPL>
 __global__ void __launch_bounds__(64 * OS_MAXP, 1) onesided_jacobi_kernel(OsParams prm) {
+    constexpr int ROWS = 64 * RPL, LD = ROWS + 2;  // a column: its rows, squared norm, id (integer bits)
     cg::cluster_group cluster = cg::this_cluster();
     const int C = (int)cluster.num_blocks();
     const int c = (int)cluster.block_rank();
     const int n = prm.n, np = prm.np, P = prm.P;
     const int D = 2 * P + 2;  // receive ring depth per side
     extern __shared__ __align__(16) double sm[];
-    double* bufs = sm;  // [2P + 2D][OS_LD]
+    double* bufs = sm;  // [2P + 2D][LD]
     const int RL0 = 2 * P, RR0 = 2 * P + D;
     __shared__ uint64_t rbar[2][OS_MAXRING];  // [0]: from the left, [1]: from the right
     __shared__ long long s_g[OS_MAXP][2];     // per pair: each half's part of g (fixed point)
@@ -351,7 +461,7 @@ __global__ void __launch_bounds__(64 * OS_MAXP, 1) onesided_jacobi_kernel(OsPara
     const int N = np - 1;
     const double tol2 = prm.tol * prm.tol;
     const int T2 = (int)((__double_as_longlong(tol2) >> 52) & 0x7ff) - 1023;  // tol^2 in [2^T2, 2^(T2+1))
-    const unsigned colbytes = (unsigned)(sizeof(double) * OS_LD);
+    const unsigned colbytes = (unsigned)(sizeof(double) * LD);
 
     if (tid == 0) {
         for (int s = 0; s < 2; ++s)
@@ -370,15 +480,15 @@ __global__ void __launch_bounds__(64 * OS_MAXP, 1) onesided_jacobi_kernel(OsPara
     // initial placement: local top u <- column cP+u, bottom u <- column np-1-cP-u
     for (int u = warp; u < 2 * P; u += nwarps) {
         const int col = (u < P) ? c * P + u : np - 1 - c * P - (u - P);
-        double* b = bufs + (size_t)u * OS_LD;
+        double* b = bufs + (size_t)u * LD;
         double s2 = 0.0;
-        for (int r = lane; r < 64; r += 32) {
+        for (int r = lane; r < ROWS; r += 32) {
             const double v = (col < n && r < n) ? prm.X[r + (size_t)col * n] : 0.0;
             b[r] = v;
             s2 = fma(v, v, s2);
         }
         s2 = warp_sum(s2);
-        if (lane == 0) { b[64] = s2; b[65] = __longlong_as_double((long long)col); }
+        if (lane == 0) { b[ROWS] = s2; b[ROWS + 1] = __longlong_as_double((long long)col); }
     }
     cluster.sync();
 
@@ -399,24 +509,31 @@ __global__ void __launch_bounds__(64 * OS_MAXP, 1) onesided_jacobi_kernel(OsPara
         // exact squared norms at the start of the sweep
         for (int u = warp; u < 2 * P; u += nwarps) {
             double* b = bufs + (size_t)(u < P ? os_buf(c, C, P, D, K, ring, u, true)
-                                              : os_buf(c, C, P, D, K, ring, u - P, false)) * OS_LD;
-            double s2 = warp_sum(fma(b[lane], b[lane], b[lane + 32] * b[lane + 32]));
-            if (lane == 0) b[64] = s2;
+                                              : os_buf(c, C, P, D, K, ring, u - P, false)) * LD;
+            double s2 = 0.0;
+#pragma unroll
+            for (int i = 0; i < 2 * RPL; ++i) s2 = fma(b[lane + 32 * i], b[lane + 32 * i], s2);
+            s2 = warp_sum(s2);
+            if (lane == 0) b[ROWS] = s2;
         }
         __syncthreads();
         int bt = os_buf(c, C, P, D, K, ring, a, true), bb = os_buf(c, C, P, D, K, ring, a, false);
         for (int k = 0; k < N; ++k, ++K) {
-            double* xp = bufs + (size_t)bt * OS_LD;
-            double* xq = bufs + (size_t)bb * OS_LD;
-            const double p0 = xp[row], q0 = xq[row];
-            const double app = xp[64], aqq = xq[64];
-            const long long idp = __double_as_longlong(xp[65]), idq = __double_as_longlong(xq[65]);
+            double* xp = bufs + (size_t)bt * LD;
+            double* xq = bufs + (size_t)bb * LD;
+            double pr[RPL], qr[RPL];
+#pragma unroll
+            for (int i = 0; i < RPL; ++i) { pr[i] = xp[row + 64 * i]; qr[i] = xq[row + 64 * i]; }
+            const double app = xp[ROWS], aqq = xq[ROWS];
+            const long long idp = __double_as_longlong(xp[ROWS + 1]), idq = __double_as_longlong(xq[ROWS + 1]);
             // g = x_p^T x_q: one FP64 product per lane, summed exactly as 64-bit fixed-point
             // integers in units 2^(S - 62), with 2^S >= 4 (a_pp a_qq)^(1/2) >= 4 sum |x_p x_q|
             const int ea = (int)((__double_as_longlong(app) >> 52) & 0x7ff) - 1023;
             const int eb = (int)((__double_as_longlong(aqq) >> 52) & 0x7ff) - 1023;
             const int S = ((ea + eb + 3) >> 1) + 2;
-            long long G = os_to_fixed(p0 * q0, S);
+            long long G = 0;
+#pragma unroll
+            for (int i = 0; i < RPL; ++i) G += os_to_fixed(pr[i] * qr[i], S);
             const double dpq = aqq - app;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) G += __shfl_xor_sync(0xffffffffu, G, o);
@@ -445,7 +562,10 @@ __global__ void __launch_bounds__(64 * OS_MAXP, 1) onesided_jacobi_kernel(OsPara
                 if (!rot) best_off = fmaxf(best_off, rr);
                 sweep_mx = fmaxf(sweep_mx, in_range ? rr : (rot ? 1.0f : 0.0f));
             }
-            double n0 = p0, m0 = q0, np2 = app, nq2 = aqq;
+            double nr[RPL], mr[RPL];
+#pragma unroll
+            for (int i = 0; i < RPL; ++i) { nr[i] = pr[i]; mr[i] = qr[i]; }
+            double np2 = app, nq2 = aqq;
             if (rot) {
                 // Rutishauser's t = sgn(zeta)/(|zeta| + sqrt(1 + zeta^2)), zeta = (a_qq - a_pp)/2g,
                 // sgn(0) = +1, in FP32 from ratios <= 1 (its accuracy only sets how far g is
@@ -491,14 +611,20 @@ __global__ void __launch_bounds__(64 * OS_MAXP, 1) onesided_jacobi_kernel(OsPara
                 }
                 os_pair_bar(a);
                 const double cs = s_rot2[a][0], sn = s_rot2[a][1];
-                n0 = fma(cs, p0, -sn * q0);
-                m0 = fma(sn, p0, cs * q0);
+#pragma unroll
+                for (int i = 0; i < RPL; ++i) {
+                    nr[i] = fma(cs, pr[i], -sn * qr[i]);
+                    mr[i] = fma(sn, pr[i], cs * qr[i]);
+                }
                 np2 = s_nrm[a][0];
                 nq2 = s_nrm[a][1];
                 const int rc = s_rcf[a];
                 if (rc) {
-                    const double r1 = (rc & 1) ? warp_sum(n0 * n0) : 0.0;
-                    const double r2 = (rc & 2) ? warp_sum(m0 * m0) : 0.0;
+                    double r1 = 0.0, r2 = 0.0;
+#pragma unroll
+                    for (int i = 0; i < RPL; ++i) { r1 = fma(nr[i], nr[i], r1); r2 = fma(mr[i], mr[i], r2); }
+                    r1 = (rc & 1) ? warp_sum(r1) : 0.0;
+                    r2 = (rc & 2) ? warp_sum(r2) : 0.0;
                     if (lane == 0) { s_rc[a][0][h] = r1; s_rc[a][1][h] = r2; }
                     os_pair_bar(a);
                     if (rc & 1) np2 = s_rc[a][0][0] + s_rc[a][0][1];
@@ -510,28 +636,32 @@ __global__ void __launch_bounds__(64 * OS_MAXP, 1) onesided_jacobi_kernel(OsPara
             // and id (half 1 sends those); every other column is written back in place
             const bool lead = h == 1 && lane == 0;
             if (a == P - 1 && c < C - 1) {
-                const uint32_t dst = os_mapa(bufs + (size_t)(RL0 + ring) * OS_LD, c + 1);
+                const uint32_t dst = os_mapa(bufs + (size_t)(RL0 + ring) * LD, c + 1);
                 const uint32_t rb = os_mapa(&rbar[0][ring], c + 1);
-                os_st_async(dst + 8u * (unsigned)row, n0, rb);
+#pragma unroll
+                for (int i = 0; i < RPL; ++i) os_st_async(dst + 8u * (unsigned)(row + 64 * i), nr[i], rb);
                 if (lead) {
-                    os_st_async(dst + 8u * 64u, np2, rb);
-                    os_st_async(dst + 8u * 65u, __longlong_as_double(idp), rb);
+                    os_st_async(dst + 8u * (unsigned)ROWS, np2, rb);
+                    os_st_async(dst + 8u * (unsigned)(ROWS + 1), __longlong_as_double(idp), rb);
                 }
             } else {
-                xp[row] = n0;
-                if (lead) xp[64] = np2;
+#pragma unroll
+                for (int i = 0; i < RPL; ++i) xp[row + 64 * i] = nr[i];
+                if (lead) xp[ROWS] = np2;
             }
             if (a == 0 && c > 0) {
-                const uint32_t dst = os_mapa(bufs + (size_t)(RR0 + ring) * OS_LD, c - 1);
+                const uint32_t dst = os_mapa(bufs + (size_t)(RR0 + ring) * LD, c - 1);
                 const uint32_t rb = os_mapa(&rbar[1][ring], c - 1);
-                os_st_async(dst + 8u * (unsigned)row, m0, rb);
+#pragma unroll
+                for (int i = 0; i < RPL; ++i) os_st_async(dst + 8u * (unsigned)(row + 64 * i), mr[i], rb);
                 if (lead) {
-                    os_st_async(dst + 8u * 64u, nq2, rb);
-                    os_st_async(dst + 8u * 65u, __longlong_as_double(idq), rb);
+                    os_st_async(dst + 8u * (unsigned)ROWS, nq2, rb);
+                    os_st_async(dst + 8u * (unsigned)(ROWS + 1), __longlong_as_double(idq), rb);
                 }
             } else {
-                xq[row] = m0;
-                if (lead) xq[64] = nq2;
+#pragma unroll
+                for (int i = 0; i < RPL; ++i) xq[row + 64 * i] = mr[i];
+                if (lead) xq[ROWS] = nq2;
             }
             // the columns arriving in this step (every thread acquires them itself); after one
             // wait has run out the rest fail at once, so a lost neighbour costs one limit
@@ -576,11 +706,11 @@ __global__ void __launch_bounds__(64 * OS_MAXP, 1) onesided_jacobi_kernel(OsPara
         if (mx < 0x1p-20f && sweep < prm.max_sweeps) {
             for (int u = warp; u < 2 * P; u += nwarps) {
                 double* b = bufs + (size_t)(u < P ? os_buf(c, C, P, D, K, ring, u, true)
-                                                  : os_buf(c, C, P, D, K, ring, u - P, false)) * OS_LD;
+                                                  : os_buf(c, C, P, D, K, ring, u - P, false)) * LD;
                 double s2 = 0.0;
-                for (int r = lane; r < 64; r += 32) s2 = fma(b[r], b[r], s2);
+                for (int r = lane; r < ROWS; r += 32) s2 = fma(b[r], b[r], s2);
                 s2 = warp_sum(s2);
-                if (lane == 0) b[64] = s2;
+                if (lane == 0) b[ROWS] = s2;
             }
             cluster.sync();
             int fails = 0;
@@ -589,16 +719,16 @@ __global__ void __launch_bounds__(64 * OS_MAXP, 1) onesided_jacobi_kernel(OsPara
             for (int it = tid; it < items; it += blockDim.x) {
                 const int u = it % slots, w = (it / slots) % slots, rk = it / (slots * slots);
                 const double* bu = bufs + (size_t)(u < P ? os_buf(c, C, P, D, K, ring, u, true)
-                                                         : os_buf(c, C, P, D, K, ring, u - P, false)) * OS_LD;
+                                                         : os_buf(c, C, P, D, K, ring, u - P, false)) * LD;
                 const double* bv = cluster.map_shared_rank(bufs, rk) +
                                    (size_t)(w < P ? os_buf(rk, C, P, D, K, ring, w, true)
-                                                  : os_buf(rk, C, P, D, K, ring, w - P, false)) * OS_LD;
-                const long long iu = __double_as_longlong(bu[65]), iv = __double_as_longlong(bv[65]);
+                                                  : os_buf(rk, C, P, D, K, ring, w - P, false)) * LD;
+                const long long iu = __double_as_longlong(bu[ROWS + 1]), iv = __double_as_longlong(bv[ROWS + 1]);
                 if (!(iu < iv && iv < n)) continue;
-                const double au = bu[64], av = bv[64];
+                const double au = bu[ROWS], av = bv[ROWS];
                 if (!(au > 0.0 && av > 0.0)) continue;
                 double g0 = 0.0, g1 = 0.0, g2 = 0.0, g3 = 0.0;
-                for (int r = 0; r < 64; r += 4) {
+                for (int r = 0; r < ROWS; r += 4) {
                     g0 = fma(bu[r], bv[r], g0);
                     g1 = fma(bu[r + 1], bv[r + 1], g1);
                     g2 = fma(bu[r + 2], bv[r + 2], g2);
@@ -621,11 +751,11 @@ __global__ void __launch_bounds__(64 * OS_MAXP, 1) onesided_jacobi_kernel(OsPara
     // outputs: lambda_j = ||x_j||^2, v_j = P^T x_j / ||x_j||
     for (int u = warp; u < 2 * P; u += nwarps) {
         const double* b = bufs + (size_t)(u < P ? os_buf(c, C, P, D, K, ring, u, true)
-                                                : os_buf(c, C, P, D, K, ring, u - P, false)) * OS_LD;
-        const int j = (int)__double_as_longlong(b[65]);
+                                                : os_buf(c, C, P, D, K, ring, u - P, false)) * LD;
+        const int j = (int)__double_as_longlong(b[ROWS + 1]);
         if (j >= n) continue;
         double s2 = 0.0;
-        for (int r = lane; r < 64; r += 32) s2 = fma(b[r], b[r], s2);
+        for (int r = lane; r < ROWS; r += 32) s2 = fma(b[r], b[r], s2);
         s2 = warp_sum(s2);
         const double nrm = sqrt(s2);
         const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
@@ -766,13 +896,17 @@ int cluster_size_for(int n, bool allow16) {
     return allow16 ? 16 : 8;
 }
 
-cudaError_t launch_cluster_jacobi(OsParams prm, int C, cudaStream_t s) {
+// rows per lane and half of the column buffers: n <= 64, 128 or 256
+int rows_per_lane(int n) { return n <= 64 ? 1 : (n <= 128 ? 2 : 4); }
+
+template <int RPL>
+cudaError_t launch_cluster_jacobi_t(OsParams prm, int C, cudaStream_t s) {
     prm.np = ((prm.n < 4 ? 4 : prm.n) + 4 * C - 1) / (4 * C) * (4 * C);
     prm.P = prm.np / (2 * C);
     if (prm.P > OS_MAXP) return cudaErrorNotSupported;
-    const size_t smem = sizeof(double) * (size_t)(2 * prm.P + 2 * (2 * prm.P + 2)) * OS_LD;
+    const size_t smem = sizeof(double) * (size_t)(2 * prm.P + 2 * (2 * prm.P + 2)) * (64 * RPL + 2);
     cudaError_t e =
-        cudaFuncSetAttribute(onesided_jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(onesided_jacobi_kernel<RPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(C, 1, 1);
@@ -786,14 +920,39 @@ cudaError_t launch_cluster_jacobi(OsParams prm, int C, cudaStream_t s) {
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, onesided_jacobi_kernel, prm);
+    return cudaLaunchKernelEx(&cfg, onesided_jacobi_kernel<RPL>, prm);
+}
+
+template <int RPL>
+bool allow_cluster16() {
+    const bool ok = cudaFuncSetAttribute(onesided_jacobi_kernel<RPL>, cudaFuncAttributeNonPortableClusterSizeAllowed,
+                                         1) == cudaSuccess;
+    if (!ok) (void)cudaGetLastError();
+    return ok;
+}
+
+template <int RPL>
+cudaError_t launch_cluster_jacobi(OsParams prm, cudaStream_t s) {
+    const int C = cluster_size_for(prm.n, allow_cluster16<RPL>());
+    cudaError_t e = launch_cluster_jacobi_t<RPL>(prm, C, s);
+    if (e != cudaSuccess && C == 16) {
+        // the device may not schedule a 16-CTA cluster: the portable size instead
+        (void)cudaGetLastError();
+        e = launch_cluster_jacobi_t<RPL>(prm, 8, s);
+    }
+    return e;
 }
 
 }  // namespace
 
 cudaError_t launch_cholesky(const double* M, int n, int64_t ldm, double* X, int* perm, DevInfo* info, bool pivot,
-                            cudaStream_t s) {
-    if (n > 64) return cudaErrorNotSupported;
+                            cudaStream_t s, double* gm_scratch) {
+    if (n > 256 || (n > 64 && gm_scratch == nullptr)) return cudaErrorNotSupported;
+    if (n > 64) {
+        chol_piv_gm_kernel<<<1, 1024, 0, s>>>(M, n, ldm, gm_scratch, gm_scratch + (size_t)n * n, X, perm, info,
+                                              pivot ? 1 : 0);
+        return cudaGetLastError();
+    }
     cudaError_t e = cudaFuncSetAttribute(chol_piv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)(2 * sizeof(double) * 64 * 64));
     if (e != cudaSuccess) return e;
@@ -801,45 +960,38 @@ cudaError_t launch_cholesky(const double* M, int n, int64_t ldm, double* X, int*
     return cudaGetLastError();
 }
 
+// scratch: X (n^2 doubles), perm (n ints in n doubles' room), and for n > 64 the Cholesky's
+// global Schur complement and rows of R (2 n^2 doubles): (3 n^2 + n) doubles in all
 cudaError_t launch_eig_onesided(const double* M, int n, int64_t ldm, double tol, int max_sweeps,
                                 void* scratch, double* lam_ws, double* V_ws, DevInfo* info,
                                 cudaStream_t s, const EigSide* side, long long wait_cycles) {
-    if (n > 64) return cudaErrorNotSupported;
+    if (n > 256) return cudaErrorNotSupported;
     double* X = reinterpret_cast<double*>(scratch);
-    int* perm = reinterpret_cast<int*>(reinterpret_cast<char*>(scratch) + sizeof(double) * (size_t)n * n);
-    const size_t chol_smem = 2 * sizeof(double) * (size_t)n * n;
-    cudaError_t e = cudaFuncSetAttribute(chol_piv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(2 * sizeof(double) * 64 * 64));
+    int* perm = reinterpret_cast<int*>(X + (size_t)n * n);
+    double* gm = X + (size_t)n * n + n;
+    cudaError_t e = launch_cholesky(M, n, ldm, X, perm, info, true, s, gm);
     if (e != cudaSuccess) return e;
-    chol_piv_kernel<<<1, 256, chol_smem, s>>>(M, n, ldm, X, perm, info, 1);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    // kappa(B) on the side stream, beside the Jacobi (joined before the caller's next launch)
-    const bool fork = side != nullptr && side->stream != nullptr;
+    // kappa(B) on the side stream, beside the Jacobi (joined before the caller's next launch);
+    // estimated for n <= 64
+    const bool fork = n <= 64 && side != nullptr && side->stream != nullptr;
     if (fork) {
         e = cudaEventRecord(side->fork, s);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(side->stream, side->fork, 0);
         if (e != cudaSuccess) return e;
     }
-    kappa_kernel<<<1, 32, 0, fork ? side->stream : s>>>(X, perm, M, ldm, n, info);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    if (n <= 64) {
+        kappa_kernel<<<1, 32, 0, fork ? side->stream : s>>>(X, perm, M, ldm, n, info);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     if (fork) {
         e = cudaEventRecord(side->join, side->stream);
         if (e != cudaSuccess) return e;
     }
-
-    const bool allow16 =
-        cudaFuncSetAttribute(onesided_jacobi_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess;
-    if (!allow16) (void)cudaGetLastError();
     OsParams prm{X, perm, n, 0, 0, tol, max_sweeps, wait_limit_of(wait_cycles), lam_ws, V_ws, info};
-    int C = cluster_size_for(n, allow16);
-    e = launch_cluster_jacobi(prm, C, s);
-    if (e != cudaSuccess && C == 16) {
-        // the device may not schedule a 16-CTA cluster: the portable size instead
-        (void)cudaGetLastError();
-        e = launch_cluster_jacobi(prm, 8, s);
-    }
+    const int rpl = rows_per_lane(n);
+    e = rpl == 1 ? launch_cluster_jacobi<1>(prm, s) : rpl == 2 ? launch_cluster_jacobi<2>(prm, s)
+                                                                : launch_cluster_jacobi<4>(prm, s);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e == cudaSuccess && fork) e = cudaStreamWaitEvent(s, side->join, 0);
     return e;

@@ -173,11 +173,12 @@ cudaError_t launch_eig_onesided(const double* M, int n, int64_t ldm, double tol,
                                 void* scratch, double* lam_ws, double* V_ws, DevInfo* info,
                                 cudaStream_t s, const EigSide* side = nullptr, long long wait_cycles = 0);
 
-// Cholesky of M (n <= 64, FP64, one CTA) into X = R^T (n x n, ld n, rows in pivot
-// order) and perm (position -> original index); pivot = false is the plain
-// factorization (perm = identity).  A non-positive pivot flags rank deficiency.
+// Cholesky of M (FP64, one CTA) into X = R^T (n x n, ld n, rows in pivot order) and
+// perm (position -> original index); pivot = false is the plain factorization (perm =
+// identity).  A non-positive pivot flags rank deficiency.  n <= 64 in shared memory;
+// 64 < n <= 256 needs gm_scratch (2 n^2 doubles) for the Schur complement and R.
 cudaError_t launch_cholesky(const double* M, int n, int64_t ldm, double* X, int* perm, DevInfo* info, bool pivot,
-                            cudaStream_t s);
+                            cudaStream_t s, double* gm_scratch = nullptr);
 
 // Algorithm 2 (n <= 64): the plain FP64 Cholesky M = R^T R, R cast to FP32, and
 // the SVD of that R by a one-CTA one-sided Jacobi in FP32 (tol: the scaled skip

@@ -87,7 +87,7 @@ Layout layout_for(int64_t n, size_t part_bytes, int working) {
     L.Glo = off; off += align_up(sizeof(double) * n * n);
     L.lam = off; off += align_up(sizeof(double) * n);
     L.Vh = off; off += align_up(sizeof(double) * n * n);
-    L.scratch = off; off += align_up(sizeof(double) * 2 * n * n);
+    L.scratch = off; off += align_up(sizeof(double) * (3 * n * n + n));  // X, perm, Cholesky scratch (n > 64)
     L.W = off; off += align_up(wsize(working) * n * n);
     L.total = off;
     return L;
@@ -238,8 +238,7 @@ cudaError_t run_eig(tsvd_ctx* h, const double* M, int n, int64_t ldm, double* sc
         const float tol = h->opts.jacobi_tol > 0.0 ? (float)h->opts.jacobi_tol : (float)n * 5.9604644775390625e-8f;
         return launch_eig_alg2(M, n, ldm, tol, max_sweeps(h), scratch, lam, Vh, h->dinfo, h->stream);
     }
-    const bool one_sided = h->opts.eig_variant == EIG_ONE_SIDED ||
-                           (h->opts.eig_variant == EIG_DEFAULT && n <= 64);
+    const bool one_sided = n <= 256 && (h->opts.eig_variant == EIG_ONE_SIDED || h->opts.eig_variant == EIG_DEFAULT);
     if (one_sided)
         return launch_eig_onesided(M, n, ldm, jacobi_tol(h, n), max_sweeps(h), scratch, lam, Vh, h->dinfo,
                                    h->stream, &h->side, h->opts.timeout_cycles);

@@ -313,8 +313,12 @@ def test_cholqr_rank_deficient_and_args():
 # ------------------------------------------------------------------ Jacobi (a4-a6)
 @pytest.mark.parametrize("variant", [1, 2])
 @pytest.mark.parametrize("n,kappa,logd", [(1, 1.0, 0.0), (2, 10.0, 1.0), (7, 1e2, 2.0), (16, 1e3, 3.0),
-                                          (33, 1e3, 3.0), (64, 1e4, 4.0)])
+                                          (33, 1e3, 3.0), (64, 1e4, 4.0), (65, 1e3, 3.0), (100, 1e3, 3.0),
+                                          (128, 1e3, 3.0), (200, 1e2, 2.0), (256, 1e3, 3.0)])
 def test_eig_matches_oracle_jacobi(n, kappa, logd, variant):
+    """Both FP64 eigen routes on the oracle's exact Gram against the oracle's two-sided Jacobi: the
+    two-sided tournament kernel (variant 1) and the pivoted Cholesky + cluster one-sided Jacobi
+    (variant 2; 1, 2 and 4 rows per lane for n <= 64, 128, 256)."""
     m = max(4 * n, 200)
     A, _ = workloads.small_case(m, n, kappa_sigma=kappa, logd=logd, seed=11 * n)
     S_hi, _, _ = oracle.gram(workloads.to_numpy_colmajor(A, m))
@@ -823,7 +827,8 @@ def test_full_size_sampled(name):
 def test_full_size_sampled_wide():
     """The 1,048,576 x 256 FP32 workload (sigma log-uniform in [1e-5, 1], D = 10^U(-3, 3)) at full
     size in the launch configuration the benchmark would time (28 tensor-core passes over pairs of
-    32-column blocks, the two-sided Jacobi for n > 64, U in a second pass): sampled Gram entries
+    32-column blocks, the pivoted Cholesky in global scratch and the cluster one-sided Jacobi with 4
+    rows per lane, U in a second pass): sampled Gram entries
     against the exact oracle (column pairs one by one), the eigen stage on the GPU's own Gram
     against the oracle's FP64 Jacobi, sampled U rows against the exactly rounded product."""
     spec = workloads.CONFIGS["wide_1048576x256_fp32"]
