@@ -601,7 +601,8 @@ def main():
     # each with everything else at its default, on the same resident A
     variants = {}
     if not args.no_variants and n <= 64 and working == T.TSVD_FP32:
-        for name, kw in (("eig_two_sided", dict(eig_variant=1)), ("u_cuda_core_fp32", dict(u_variant=1))):
+        for name, kw in (("eig_two_sided", dict(eig_variant=1)), ("u_cuda_core_fp32", dict(u_variant=1)),
+                         ("eig_alg2_fp32_svd_of_R", dict(eig_variant=3))):
             hv, _ = T.tsvd_create(local, stream.cuda_stream, T.tsvd_opts(timing=5, **kw))
             for _ in range(7):
                 T.tsvd_solve(hv, A, m, n, m, working, higher, sigma, V, n, U, m, info)
@@ -610,6 +611,23 @@ def main():
             variants[name] = {"gram_ms": vst[0], "eig_ms": vst[1], "u_ms": vst[2], "total_ms": vst[3],
                               "status": T.tsvd_status_string(int(info[0].item()))}
             T.tsvd_destroy(hv)
+        # the mixed precision Cholesky QR (Sec. 3.1) on the same A: Gram, FP64 Cholesky, Q by FP32
+        # substitution (Q into U's buffer); it reads A twice and writes Q once
+        hq, _ = T.tsvd_create(local, stream.cuda_stream, T.tsvd_opts())
+        Rq = torch.zeros(n * n, dtype=torch.float64, device=dev)
+        for _ in range(3):
+            T.tsvd_cholqr(hq, A, m, n, m, working, T.TSVD_FP64, U, m, Rq, n, info)
+        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        q0.record(stream)
+        for _ in range(5):
+            T.tsvd_cholqr(hq, A, m, n, m, working, T.TSVD_FP64, U, m, Rq, n, info)
+        q1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms_q = q0.elapsed_time(q1) / 5
+        variants["cholqr_mixed"] = {"ms": ms_q, "value_GBps": bytes_A / (ms_q * 1e-3) / 1e9,
+                                    "hbm_frac_of_traffic": 3 * bytes_A / (ms_q * 1e-3) / 1e9 / peaks()["hbm"],
+                                    "status": T.tsvd_status_string(int(info[0].item()))}
+        T.tsvd_destroy(hq)
     pk = peaks()
     arp = arith_peaks(args.no_probe)
     gram_ms, eig_ms, u_ms = stage_ms[0], stage_ms[1], stage_ms[2]

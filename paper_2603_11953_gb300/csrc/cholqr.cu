@@ -7,12 +7,14 @@
 // With u_h = 2^-53 <= u^2 (u = 2^-24), Theorem 3 bounds ||Q^T Q - I|| by
 // O(u) kappa(B) instead of the O(u) kappa(B)^2 of a same-precision Cholesky QR.
 //
-// cholqr_q_kernel: one thread per row, the row's n solutions in registers; R_w
-// is in shared memory with its columns contiguous (entry (i, j) at Rt[j][i]),
-// so the 16-byte shared loads of q_j's sum broadcast four entries of column j
-// to the warp.  A is read once and Q written once (coalesced: consecutive
-// threads hold consecutive rows of the column-major arrays).  The n^2 / 2 FMAs
-// per row cost about 0.7 of the time A and Q take over HBM at n = 64.
+// cholqr_q_kernel: one thread per row, the row's n running values in registers, R_w in shared
+// memory with its rows contiguous (entry (j, k) at Rw[j][k]).  Right-looking order: once q_j =
+// s_j / r_jj is known, every s_k (k > j) takes its term -q_j r_jk, so a step's FMAs are
+// independent of each other and the dependent chain is n divisions long instead of n^2 / 2
+// FMAs.  Each s_k still receives its terms in the order of j, so the result is bitwise that of
+// the left-looking substitution.  16-byte shared loads broadcast four entries of row j to the
+// warp.  A is read once and Q written once (coalesced: consecutive threads hold consecutive rows
+// of the column-major arrays).
 #include "internal.cuh"
 
 namespace tsvd {
@@ -22,38 +24,41 @@ template <int NP>
 __global__ void __launch_bounds__(256)
     cholqr_q_kernel(const float* __restrict__ A, int64_t m, int n, int64_t lda, const double* __restrict__ X,
                     float* __restrict__ Q, int64_t ldq) {
-    __shared__ __align__(16) float Rt[NP][NP];  // Rt[j][i] = RN_32(R[i][j]), i <= j; zero elsewhere
+    __shared__ __align__(16) float Rw[NP][NP];  // Rw[j][k] = RN_32(R[j][k]), j <= k < n; zero elsewhere
     __shared__ float Rd[NP];                     // the diagonal
     for (int idx = threadIdx.x; idx < NP * NP; idx += blockDim.x) {
-        const int j = idx / NP, i = idx % NP;
-        // X = R^T with ld n: R[i][j] = X[j + i n]
-        Rt[j][i] = (i <= j && j < n) ? (float)X[j + (size_t)i * n] : 0.0f;
+        const int j = idx / NP, k = idx % NP;
+        // X = R^T with ld n: R[j][k] = X[k + j n]
+        Rw[j][k] = (j <= k && k < n) ? (float)X[k + (size_t)j * n] : 0.0f;
     }
     __syncthreads();
-    for (int j = threadIdx.x; j < NP; j += blockDim.x) Rd[j] = j < n ? Rt[j][j] : 1.0f;
+    for (int j = threadIdx.x; j < NP; j += blockDim.x) Rd[j] = j < n ? Rw[j][j] : 1.0f;
     __syncthreads();
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < m; r += (int64_t)gridDim.x * blockDim.x) {
-        float a[NP], q[NP];
+        float s[NP];
 #pragma unroll
-        for (int j = 0; j < NP; ++j) a[j] = j < n ? A[r + (size_t)j * lda] : 0.0f;
+        for (int j = 0; j < NP; ++j) s[j] = j < n ? A[r + (size_t)j * lda] : 0.0f;
 #pragma unroll
         for (int j = 0; j < NP; ++j) {
             // q_j = (a_j - sum_{i<j} q_i r_ij) / r_jj, the sum in FP32 in the order of i
-            float s = a[j];
-            const float4* col = reinterpret_cast<const float4*>(Rt[j]);
+            s[j] = s[j] / Rd[j];
+            // one row of R_w at a time in registers (the compiler would otherwise hoist the loads
+            // of all rows)
+            asm volatile("" ::: "memory");
+            const float4* row = reinterpret_cast<const float4*>(Rw[j]);
 #pragma unroll
-            for (int i4 = 0; i4 < (j + 3) / 4; ++i4) {
-                const float4 c = col[i4];
-                if (4 * i4 + 0 < j) s = fmaf(-q[4 * i4 + 0], c.x, s);
-                if (4 * i4 + 1 < j) s = fmaf(-q[4 * i4 + 1], c.y, s);
-                if (4 * i4 + 2 < j) s = fmaf(-q[4 * i4 + 2], c.z, s);
-                if (4 * i4 + 3 < j) s = fmaf(-q[4 * i4 + 3], c.w, s);
+            for (int k4 = (j + 1) / 4; k4 < NP / 4; ++k4) {
+                if ((k4 & 3) == 0) asm volatile("" ::: "memory");  // at most four loads ahead
+                const float4 c = row[k4];
+                if (4 * k4 + 0 > j) s[4 * k4 + 0] = fmaf(-s[j], c.x, s[4 * k4 + 0]);
+                if (4 * k4 + 1 > j) s[4 * k4 + 1] = fmaf(-s[j], c.y, s[4 * k4 + 1]);
+                if (4 * k4 + 2 > j) s[4 * k4 + 2] = fmaf(-s[j], c.z, s[4 * k4 + 2]);
+                if (4 * k4 + 3 > j) s[4 * k4 + 3] = fmaf(-s[j], c.w, s[4 * k4 + 3]);
             }
-            q[j] = s / Rd[j];
         }
 #pragma unroll
         for (int j = 0; j < NP; ++j)
-            if (j < n) Q[r + (size_t)j * ldq] = q[j];
+            if (j < n) Q[r + (size_t)j * ldq] = s[j];
     }
 }
 

@@ -14,7 +14,8 @@
 // factor in shared memory and needs no cluster.
 //
 // One CTA, one warp per column pair (round-robin "circle" tournament over the
-// n rounded up to even columns, column 0 fixed), lane l holds rows l and l + 32;
+// n rounded up to even columns, column 0 fixed; every warp finds its pair's columns
+// from the step count), lane l holds rows l and l + 32;
 // per step: g = x_p^T x_q and both squared norms in FP32 (one reduction of three
 // values), the scaled skip test |g| <= tol ||x_p|| ||x_q||, Rutishauser's angle,
 // the rotation of the two columns and of the same two columns of V.  A sweep
@@ -38,7 +39,6 @@ __global__ void __launch_bounds__(1024)
                        int max_sweeps, double* __restrict__ lam, double* __restrict__ V, DevInfo* info) {
     __shared__ float col[64][A2_ROWS];  // column c of R, cast to FP32
     __shared__ float vcol[64][A2_ROWS]; // column c of V = J (the accumulated rotations)
-    __shared__ int slot[2][64];         // tournament position -> column, by step parity
     __shared__ int s_rot;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int P = np / 2;
@@ -48,9 +48,8 @@ __global__ void __launch_bounds__(1024)
         col[c][r] = (c < n && r < n) ? (float)X[c + (size_t)r * n] : 0.0f;
         vcol[c][r] = (c == r) ? 1.0f : 0.0f;
     }
-    if (tid < np) slot[0][tid] = tid;
     __syncthreads();
-    int sweep = 0, par = 0;
+    int sweep = 0;
     bool converged = false;
     while (sweep < max_sweeps) {
         ++sweep;
@@ -58,7 +57,11 @@ __global__ void __launch_bounds__(1024)
         __syncthreads();
         for (int k = 0; k < np - 1; ++k) {
             if (warp < P) {
-                const int cp = slot[par][warp], cq = slot[par][np - 1 - warp];
+                // circle tournament in closed form: position 0 keeps column 0, position p >= 1
+                // holds after k steps the column that started at 1 + ((p - 1 - k) mod (np - 1))
+                const int L = np - 1;
+                const int cp = warp == 0 ? 0 : 1 + ((warp - 1 - k) % L + L) % L;
+                const int cq = 1 + ((np - 2 - warp - k) % L + L) % L;
                 float* xp = col[cp];
                 float* xq = col[cq];
                 const float p0 = xp[lane], p1 = xp[lane + 32], q0 = xq[lane], q1 = xq[lane + 32];
@@ -94,14 +97,6 @@ __global__ void __launch_bounds__(1024)
                     if (lane == 0) atomicAdd(&s_rot, 1);
                 }
             }
-            if (tid == 0) {  // position 0 fixed, the others move one place round the circle
-                const int* s = slot[par];
-                int* ns = slot[par ^ 1];
-                ns[0] = s[0];
-                ns[1] = s[np - 1];
-                for (int u = 2; u < np; ++u) ns[u] = s[u - 1];
-            }
-            par ^= 1;
             __syncthreads();
         }
         if (s_rot == 0) { converged = true; break; }
