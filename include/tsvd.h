@@ -87,7 +87,15 @@ typedef struct {
                               FP32 by one-sided Jacobi (skip threshold n 2^-24 unless
                               jacobi_tol is set); FP32 working, n <= 64; accuracy
                               O(u) kappa(B) + O(u_h) kappa(B)^2 (Remark 2) */
-    int autotune;          /* reserved (0) */
+    int autotune;          /* 1: the first tsvd_gram / tsvd_solve of a shape (m, n, working,
+                              TMA-loadable input) times the Gram with split_k = one CTA per
+                              SM, half, twice and three times that, and for an FP32 U
+                              (n <= 64) the tensor-core and the CUDA-core U kernel, keeps
+                              the fastest for the handle's later calls of that shape
+                              (tsvd_autotune_choice).  Synchronises the stream once per
+                              shape; not while the stream is being captured, and not when
+                              split_k, u_variant, fixed_scale or gram_variant is set.
+                              Results stay within every bound stated here. */
     long long timeout_cycles; /* limit, in GPU clock cycles, of each steady-state mbarrier
                                  wait of the tcgen05 Gram kernel and of the cluster Jacobi
                                  (0 = default, 2^31, about a second); a wait that runs out
@@ -212,6 +220,13 @@ TSVD_API tsvd_status tsvd_batch_solve(tsvd_handle h, int32_t count, const void* 
  * call (TSVD_OK, TSVD_ERR_NONFINITE, TSVD_ERR_NOT_FULL_RANK,
  * TSVD_ERR_NO_CONVERGENCE) or TSVD_ERR_CUDA. */
 TSVD_API tsvd_status tsvd_sync_status(tsvd_handle h);
+
+/* The autotuner's choice for a shape (opts.autotune): split_k (0 = one CTA per SM),
+ * u_variant, and the measured milliseconds of the chosen Gram and U (u_ms = 0 when U was
+ * not tuned); any of u_variant, gram_ms, u_ms may be NULL.  TSVD_ERR_ARG when the handle
+ * has not tuned that shape. */
+TSVD_API tsvd_status tsvd_autotune_choice(tsvd_handle h, int64_t m, int64_t n, tsvd_prec working, int32_t* split_k,
+                                          int32_t* u_variant, float* gram_ms, float* u_ms);
 
 /* Per-stage device times of the last tsvd_solve or tsvd_solve_gram (requires
  * opts.timing >= 1): ms[0] Gram (split + MMA + combine; 0 for tsvd_solve_gram,

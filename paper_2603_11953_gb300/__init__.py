@@ -26,7 +26,7 @@ TSVD_FP32, TSVD_FP64, TSVD_DD = 0, 1, 2
 EXPORTED = ["tsvd_create", "tsvd_destroy", "tsvd_status_string", "tsvd_gram", "tsvd_eig",
             "tsvd_solve", "tsvd_batch_solve", "tsvd_sync_status", "tsvd_last_stage_ms",
             "tsvd_stage_ms_mean", "tsvd_gram_static", "tsvd_gram_colexp", "tsvd_gram_partial",
-            "tsvd_gram_finish", "tsvd_solve_gram", "tsvd_cholqr"]
+            "tsvd_gram_finish", "tsvd_solve_gram", "tsvd_cholqr", "tsvd_autotune_choice"]
 
 
 class tsvd_opts(ctypes.Structure):
@@ -211,3 +211,12 @@ def tsvd_cholqr(h, A, m, n, lda, working, higher, Q, ldq, R=None, ldr=0, info=No
     st = load_library().tsvd_cholqr(h, _p(A), int(m), int(n), int(lda), int(working), int(higher), _p(Q), int(ldq),
                                     _p(R), int(ldr), _p(info))
     return _check("tsvd_cholqr", st) if check else st
+
+
+def tsvd_autotune_choice(h, m, n, working):
+    """The autotuner's choice for a shape: (split_k, u_variant, gram_ms, u_ms), or None."""
+    sk, uv = ctypes.c_int32(0), ctypes.c_int32(0)
+    gm, um = ctypes.c_float(0.0), ctypes.c_float(0.0)
+    st = load_library().tsvd_autotune_choice(h, int(m), int(n), int(working), ctypes.byref(sk), ctypes.byref(uv),
+                                             ctypes.byref(gm), ctypes.byref(um))
+    return (sk.value, uv.value, gm.value, um.value) if st == TSVD_OK else None

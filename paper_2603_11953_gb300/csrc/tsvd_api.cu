@@ -5,12 +5,23 @@
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
+#include <map>
 #include <new>
+#include <tuple>
 #include <vector>
 
 #include "internal.cuh"
 
 using namespace tsvd;
+
+// the autotuner's choice for one shape (opts.autotune)
+struct TuneChoice {
+    int split_k;    // Gram CTAs (0: one per SM)
+    int u_variant;  // 0 tensor-core U, 1 CUDA-core U
+    float gram_ms;  // the chosen Gram's time
+    float u_ms;     // the chosen U's time (0: U not tuned)
+};
 
 struct tsvd_ctx {
     int device = 0;
@@ -30,6 +41,8 @@ struct tsvd_ctx {
     cudaEvent_t stage_ev = nullptr;
     // second stream for small kernels that run beside the main sequence (the kappa(B) estimate)
     EigSide side{nullptr, nullptr, nullptr};
+    // autotuner choices by (m, n, working, TMA-loadable input)
+    std::map<std::tuple<long long, int, int, int>, TuneChoice> tuned;
 };
 
 namespace {
@@ -245,6 +258,106 @@ cudaError_t run_eig(tsvd_ctx* h, const double* M, int n, int64_t ldm, double* sc
     return launch_jacobi(M, n, ldm, jacobi_tol(h, n), max_sweeps(h), scratch, lam, Vh, h->dinfo, h->stream);
 }
 
+// ---------------------------------------------------------------- autotuner (opts.autotune = 1)
+// The first tsvd_gram or tsvd_solve of a shape (m, n, working precision, TMA-loadable input) on a
+// handle times the Gram with the candidate split-K CTA counts (one per SM, half, twice, three
+// times that) and, when the call asks for an FP32 U of n <= 64 that both U kernels accept, the
+// tensor-core and the CUDA-core U; each candidate runs three times (the first untimed) into the
+// handle's workspace, and the fastest are kept for the handle's later calls of that shape.
+// This synchronises the stream once per shape; while the stream is being captured, or when the
+// caller fixed split_k or u_variant, the defaults apply.
+float time_once(tsvd_ctx* h, cudaEvent_t e0, cudaEvent_t e1, const std::function<cudaError_t()>& run) {
+    float best = -1.0f;
+    for (int rep = 0; rep < 3; ++rep) {
+        if (cudaEventRecord(e0, h->stream) != cudaSuccess) return -1.0f;
+        if (run() != cudaSuccess) return -1.0f;
+        if (cudaEventRecord(e1, h->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) return -1.0f;
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) return -1.0f;
+        if (rep > 0 && (best < 0.0f || ms < best)) best = ms;
+    }
+    return best;
+}
+
+const TuneChoice* autotune(tsvd_ctx* h, const void* A, int64_t m, int n, int64_t lda, int working, void* U,
+                           int64_t ldu) {
+    if (!h->opts.autotune || h->opts.gram_variant != 0 || h->opts.fixed_scale || h->opts.split_k > 0) return nullptr;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(h->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    const int tc = use_tc(h, A, working, n, lda) ? 1 : 0;
+    const auto key = std::make_tuple((long long)m, n, working, tc);
+    const auto it = h->tuned.find(key);
+    if (it != h->tuned.end()) return &it->second;
+    const int cand[4] = {0, h->sm_count / 2, 2 * h->sm_count, 3 * h->sm_count};
+    size_t need = 0;
+    for (int c : cand) {
+        h->opts.split_k = c;
+        need = std::max(need, layout_for(n, part_bytes_for(h, A, working, m, n, lda), working).total);
+    }
+    h->opts.split_k = 0;
+    if (ensure_ws(h, need) != TSVD_OK) return nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    TuneChoice ch{0, 0, -1.0f, 0.0f};
+    for (int c : cand) {
+        h->opts.split_k = c;
+        const Layout L = layout_for(n, part_bytes_for(h, A, working, m, n, lda), working);
+        double* G = reinterpret_cast<double*>(base(h) + L.G);
+        double* G_lo = working == TSVD_FP64 ? reinterpret_cast<double*>(base(h) + L.Glo) : nullptr;
+        const float ms = time_once(h, e0, e1, [&]() {
+            const tsvd_status st = run_gram(h, A, m, n, lda, working, G, G_lo, n, L.part);
+            return st == TSVD_OK ? cudaSuccess : cudaErrorUnknown;
+        });
+        if (ms > 0.0f && (ch.gram_ms < 0.0f || ms < ch.gram_ms)) { ch.gram_ms = ms; ch.split_k = c; }
+    }
+    h->opts.split_k = 0;
+    if (U && working == TSVD_FP32 && h->opts.u_variant == 0 && compute_u_tc_ok(A, working, m, n, lda) &&
+        compute_u_v2_ok(A, working, m, n, lda, U, ldu)) {
+        const Layout L = layout_for(n, part_bytes_for(h, A, working, m, n, lda), working);
+        const float* W = reinterpret_cast<const float*>(base(h) + L.W);
+        const float t_tc = time_once(h, e0, e1, [&]() {
+            return launch_compute_u_tc(static_cast<const float*>(A), m, n, lda, W, static_cast<float*>(U), ldu,
+                                       h->sm_count, h->dinfo, h->stream);
+        });
+        const float t_cc = time_once(h, e0, e1, [&]() {
+            return launch_compute_u_v2(static_cast<const float*>(A), m, n, lda, W, static_cast<float*>(U), ldu,
+                                       h->sm_count, h->dinfo, h->stream);
+        });
+        if (t_tc > 0.0f && t_cc > 0.0f) {
+            ch.u_variant = t_cc < t_tc ? 1 : 0;
+            ch.u_ms = t_cc < t_tc ? t_cc : t_tc;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    (void)cudaGetLastError();
+    if (ch.gram_ms < 0.0f) return nullptr;
+    return &(h->tuned[key] = ch);
+}
+
+// the tuned options for one call, put back when it returns
+struct TunedOpts {
+    tsvd_ctx* h;
+    int split_k, u_variant;
+    TunedOpts(tsvd_ctx* hh, const TuneChoice* c) : h(hh), split_k(hh->opts.split_k), u_variant(hh->opts.u_variant) {
+        if (c) {
+            h->opts.split_k = c->split_k;
+            h->opts.u_variant = c->u_variant;
+        }
+    }
+    ~TunedOpts() {
+        h->opts.split_k = split_k;
+        h->opts.u_variant = u_variant;
+    }
+};
+
 int ring(const tsvd_ctx* h) { return (int)(h->ev.size() / 4); }
 void record(tsvd_ctx* h, int k) {
     if (h->opts.timing) cudaEventRecord(h->ev[4 * (size_t)(h->calls % ring(h)) + k], h->stream);
@@ -398,6 +511,7 @@ tsvd_status tsvd_gram(tsvd_handle h, const void* A, int64_t m, int64_t n, int64_
         if (fs != TSVD_OK) return fs;
     }
     DeviceGuard g(h->device);
+    const TunedOpts tuned(h, autotune(h, A, m, (int)n, lda, working, nullptr, 0));
     const size_t pb = part_bytes_for(h, A, working, m, (int)n, lda);
     tsvd_status st = ensure_ws(h, align_up(pb));
     if (st != TSVD_OK) return st;
@@ -451,11 +565,27 @@ tsvd_status tsvd_solve(tsvd_handle h, const void* A, int64_t m, int64_t n, int64
         if (fs != TSVD_OK) return fs;
     }
     DeviceGuard g(h->device);
+    const TunedOpts tuned(h, autotune(h, A, m, (int)n, lda, working, U, ldu));
     const Layout L = layout_for(n, part_bytes_for(h, A, working, m, (int)n, lda), working);
     tsvd_status st = ensure_ws(h, L.total);
     if (st != TSVD_OK) return st;
     h->have_times = false;
     return solve_one(h, A, m, (int)n, lda, working, higher, sigma, V, ldv, U, ldu, info, true);
+}
+
+tsvd_status tsvd_autotune_choice(tsvd_handle h, int64_t m, int64_t n, tsvd_prec working, int32_t* split_k,
+                                 int32_t* u_variant, float* gram_ms, float* u_ms) {
+    if (!h || !split_k) return TSVD_ERR_ARG;
+    for (int tc = 1; tc >= 0; --tc) {
+        const auto it = h->tuned.find(std::make_tuple((long long)m, (int)n, (int)working, tc));
+        if (it == h->tuned.end()) continue;
+        *split_k = it->second.split_k;
+        if (u_variant) *u_variant = it->second.u_variant;
+        if (gram_ms) *gram_ms = it->second.gram_ms;
+        if (u_ms) *u_ms = it->second.u_ms;
+        return TSVD_OK;
+    }
+    return TSVD_ERR_ARG;
 }
 
 }  // extern "C"

@@ -399,6 +399,39 @@ def test_solve_matches_oracle(m, n, kappa, logd, variant):
     assert orth <= 1e-4, orth
 
 
+def test_autotune_choice_and_results():
+    """opts.autotune = 1: the first solve of a shape times the Gram's split-K candidates and both FP32 U
+    kernels and keeps the fastest; the choice is reported for the shape and reused (a second solve is
+    bitwise the first), the Gram stays within 2^-50 (|A|^T|A|) of the exact sum, sigma within 2 u_32 of
+    the oracle and U within the tensor-core U's bound (n + 13) u_32 (|A||W|)."""
+    m, n = 300000, 48
+    A, _ = workloads.small_case(m, n, kappa_sigma=1e3, logd=3.0, seed=909, device="cuda")
+    A_np = workloads.to_numpy_colmajor(A, m)
+    h = handle(autotune=1)
+    sig, V, U, st, _ = gpu_solve(A, m, n, m, h=h)
+    assert st == T.TSVD_OK
+    ch = T.tsvd_autotune_choice(h, m, n, T.TSVD_FP32)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert ch is not None and ch[0] in (0, sms // 2, 2 * sms, 3 * sms) and ch[1] in (0, 1)
+    assert ch[2] > 0.0 and ch[3] > 0.0
+    assert T.tsvd_autotune_choice(h, m + 1, n, T.TSVD_FP32) is None
+    sig2, V2, U2, st2, _ = gpu_solve(A, m, n, m, h=h)
+    assert st2 == T.TSVD_OK and T.tsvd_autotune_choice(h, m, n, T.TSVD_FP32) == ch
+    assert np.array_equal(sig, sig2) and np.array_equal(V, V2) and np.array_equal(U, U2)
+    Gh, _, stg = gpu_gram(A, m, n, m, h=h)
+    assert stg == T.TSVD_OK
+    assert check_gram(A_np, Gh, m, n) <= 2.0 ** -50
+    T.tsvd_destroy(h)
+    ref = oracle.svd(A_np, higher=1)
+    assert ref["status"] == 0
+    assert (np.abs(sig - ref["sigma_h"]) / ref["sigma_h"]).max() <= 2 * U32
+    W = (V.astype(np.float32) / sig.astype(np.float32)).astype(np.float64)
+    rows = np.unique(np.concatenate([np.arange(64), np.linspace(0, m - 1, 200).astype(np.int64)]))
+    Uref = oracle.rows_times(A_np, W, rows, 24)
+    bound = (n + 13) * U32 * (np.abs(A_np[rows].astype(np.float64)) @ np.abs(W)) + 1e-38
+    assert np.all(np.abs(U[rows] - Uref) <= bound)
+
+
 def test_batch_matches_single_solves_and_exact_u():
     """The batched launches (Gram work items on the tcgen05 kernel for instances whose A is 16-byte
     aligned with lda a multiple of 4, on the mma.sync Ozaki kernel otherwise; one CTA per instance
