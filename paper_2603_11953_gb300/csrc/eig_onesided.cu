@@ -71,6 +71,26 @@ namespace {
 __device__ __forceinline__ double chol_S(const double* sa, int n, int x, int y) {
     return x >= y ? sa[x + (size_t)y * n] : sa[y + (size_t)x * n];
 }
+// Conversions by integer bit operations (the FP64 pipe is the scarce resource):
+// double -> float truncates the significand and flushes values outside the normal
+// float range to 0 / +-max (only angles and heuristics use it); float -> double is
+// exact for normal floats and gives 0 for subnormal ones.
+__device__ __forceinline__ float os_to_float(double x) {
+    const long long b = __double_as_longlong(x);
+    const int ex = (int)((b >> 52) & 0x7ff) - 1023;
+    const unsigned sgn = (unsigned)((unsigned long long)b >> 63) << 31;
+    if (ex < -126) return __uint_as_float(sgn);
+    if (ex > 127) return __uint_as_float(sgn | 0x7f7fffffu);
+    return __uint_as_float(sgn | ((unsigned)(ex + 127) << 23) | (unsigned)((b >> 29) & 0x7fffff));
+}
+__device__ __forceinline__ double os_to_double(float x) {
+    const unsigned b = __float_as_uint(x);
+    const unsigned ex = (b >> 23) & 0xff;
+    if (ex == 0) return 0.0;
+    const unsigned long long d = ((unsigned long long)(b >> 31) << 63) | ((unsigned long long)(ex + 896) << 52) |
+                                 ((unsigned long long)(b & 0x7fffff) << 29);
+    return __longlong_as_double((long long)d);
+}
 // 1 / sqrt(d) for a positive normal d: d = dm 4^k with dm in [1, 4) by an exponent shift,
 // y0 = rsqrtf(dm) (FP32), one Newton step with its second-order term in FP64,
 // y = y0 (1 + e/2 + 3e^2/8) with e = 1 - dm y0^2 (|e| ~ 2^-23, error O(e^3)), then 2^-k.
@@ -78,7 +98,7 @@ __device__ __forceinline__ double chol_rsqrt(double d) {
     const long long b = __double_as_longlong(d);
     const int k = (int)(((b >> 52) & 0x7ff) - 1023) >> 1;  // floor(exponent / 2)
     const double dm = __longlong_as_double(b - ((long long)(2 * k) << 52));
-    const double y0 = (double)rsqrtf((float)dm);
+    const double y0 = os_to_double(rsqrtf(os_to_float(dm)));  // dm in [1, 4): both conversions exact-range
     const double e = fma(-dm * y0, y0, 1.0);
     const double y = y0 * fma(e, fma(e, 0.375, 0.5), 1.0);
     return __longlong_as_double(__double_as_longlong(y) - ((long long)k << 52));
@@ -91,7 +111,7 @@ __global__ void __launch_bounds__(256)
     double* Rr = sa + (size_t)n * n;  // [n][n]: row k of R by original column index
     __shared__ int s_list[64];        // remaining original indices, ascending
     __shared__ int s_perm[64];
-    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
     for (int idx = tid; idx < n * n; idx += nt) {
         const int r = idx % n, c = idx / n;
         sa[idx] = r >= c ? M[r + (size_t)c * ldm] : 0.0;
@@ -105,31 +125,37 @@ __global__ void __launch_bounds__(256)
         // pivot: the largest remaining diagonal, lowest original index on ties.  Every warp
         // finds it itself.  Non-negative doubles order like their bit patterns; every
         // negative value (rank deficiency) sorts below them.
-        long long best = LLONG_MIN;
+        // keys: 0 for a negative value, else the bit pattern's high word + 1 and its low word (non-
+        // negative doubles order like their patterns); three warp reductions: high word, low word
+        // among the lanes at the maximum, lowest index among those
+        unsigned khi = 0u, klo = 0u;
         int bo = n;
         for (int o = lane; o < n; o += 32) {
             if (!((rem >> o) & 1ull)) continue;
             const long long dd = __double_as_longlong(sa[o + (size_t)o * n]);
-            const long long key = dd < 0 ? LLONG_MIN + 1 : dd;
-            if (key > best || (key == best && o < bo)) { best = key; bo = o; }
+            const unsigned h = dd < 0 ? 0u : (unsigned)(dd >> 32) + 1u, l = dd < 0 ? 0u : (unsigned)dd;
+            if (bo == n || h > khi || (h == khi && l > klo)) { khi = h; klo = l; bo = o; }
         }
-        for (int off = 16; off > 0; off >>= 1) {
-            const long long ob = __shfl_xor_sync(0xffffffffu, best, off);
-            const int oo = __shfl_xor_sync(0xffffffffu, bo, off);
-            if (ob > best || (ob == best && oo < bo)) { best = ob; bo = oo; }
-        }
+        const unsigned mh = __reduce_max_sync(0xffffffffu, khi);
+        const unsigned ml = __reduce_max_sync(0xffffffffu, khi == mh ? klo : 0u);
+        bo = (int)__reduce_min_sync(0xffffffffu, (khi == mh && klo == ml) ? (unsigned)bo : (unsigned)n);
         const int ok = pivot ? bo : __ffsll((long long)rem) - 1;
         const double d = sa[ok + (size_t)ok * n];
-        if (!(d > 0.0)) { deficient = true; kend = k; break; }
+        // d > 0 (finite) decided on the bit pattern: the SM's FP64 pipe takes about one
+        // instruction per 19 cycles from all its warps, so no warp repeats FP64 work here
+        const long long db = __double_as_longlong(d);
+        if (!(db > 0 && db < 0x7ff0000000000000ll)) { deficient = true; kend = k; break; }
         const unsigned long long rn = rem & ~(1ull << ok);
-        const double rinv = chol_rsqrt(d);  // 1 / r_kk
-        // row k of R over the remaining indices, and their ascending list
-        for (int o = tid; o < n; o += nt) {
-            if (o == ok) Rr[(size_t)k * n + o] = d * rinv;
-            else if ((rn >> o) & 1ull) Rr[(size_t)k * n + o] = chol_S(sa, n, o, ok) * rinv;
-            if ((rn >> o) & 1ull) s_list[__popcll(rn & ((1ull << o) - 1ull))] = o;
+        if (warp == 0) {
+            // one warp: 1 / r_kk, row k of R over the remaining indices, and their ascending list
+            const double rinv = chol_rsqrt(d);
+            for (int o = lane; o < n; o += 32) {
+                if (o == ok) Rr[(size_t)k * n + o] = d * rinv;
+                else if ((rn >> o) & 1ull) Rr[(size_t)k * n + o] = chol_S(sa, n, o, ok) * rinv;
+                if ((rn >> o) & 1ull) s_list[__popcll(rn & ((1ull << o) - 1ull))] = o;
+            }
+            if (lane == 0) s_perm[k] = ok;
         }
-        if (tid == 0) s_perm[k] = ok;
         __syncthreads();
         // trailing update S(a, b) -= R[k][a] R[k][b] over the remaining lower triangle: the
         // warps take its columns b (round robin), the lanes its rows a >= b, contiguous
@@ -177,6 +203,7 @@ __global__ void __launch_bounds__(1024, 1)
     __shared__ int s_idx[32];
     __shared__ int s_cnt[8];
     __shared__ int s_ok;
+    __shared__ double s_rinv;
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     for (int idx = tid; idx < n * n; idx += nt) {
         const int r = idx % n, c = idx / n;
@@ -220,18 +247,22 @@ __global__ void __launch_bounds__(1024, 1)
         }
         const int ok = pivot ? s_ok : k;
         const double d = S[ok + (size_t)ok * n];
-        if (!(d > 0.0)) { deficient = true; kend = k; break; }
-        const double rinv = chol_rsqrt(d);  // 1 / r_kk
-        // row k of R over the remaining indices and their ascending list (without ok)
-        bool keep = false;
-        if (tid < n) {
-            keep = s_rem[tid] && tid != ok;
-            if (tid == ok) Rr[(size_t)k * n + tid] = d * rinv;
-            else if (keep) Rr[(size_t)k * n + tid] = chol_S(S, n, tid, ok) * rinv;
-        }
+        // d > 0 (finite) decided on the bit pattern, and 1 / r_kk only by the warps that use it
+        // (the SM's FP64 pipe is shared by all 32 warps)
+        const long long db = __double_as_longlong(d);
+        if (!(db > 0 && db < 0x7ff0000000000000ll)) { deficient = true; kend = k; break; }
+        // 1 / r_kk by one thread, the row k of R over the remaining indices and their ascending
+        // list (without ok) after the barrier
+        if (tid == 0) s_rinv = chol_rsqrt(d);
+        const bool keep = tid < n && s_rem[tid] && tid != ok;
         const unsigned bal = __ballot_sync(0xffffffffu, keep);
         if (lane == 0 && warp < 8) s_cnt[warp] = __popc(bal);
         __syncthreads();
+        if (tid < n) {
+            const double rinv = s_rinv;
+            if (tid == ok) Rr[(size_t)k * n + tid] = d * rinv;
+            else if (keep) Rr[(size_t)k * n + tid] = chol_S(S, n, tid, ok) * rinv;
+        }
         if (keep) {
             int pos = __popc(bal & ((1u << lane) - 1u));
             for (int w = 0; w < warp; ++w) pos += s_cnt[w];
@@ -293,26 +324,6 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 __device__ __forceinline__ uint32_t os_smem(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-// Conversions by integer bit operations (the FP64 pipe is the scarce resource):
-// double -> float truncates the significand and flushes values outside the normal
-// float range to 0 / +-max (only angles and heuristics use it); float -> double is
-// exact for normal floats and gives 0 for subnormal ones.
-__device__ __forceinline__ float os_to_float(double x) {
-    const long long b = __double_as_longlong(x);
-    const int ex = (int)((b >> 52) & 0x7ff) - 1023;
-    const unsigned sgn = (unsigned)((unsigned long long)b >> 63) << 31;
-    if (ex < -126) return __uint_as_float(sgn);
-    if (ex > 127) return __uint_as_float(sgn | 0x7f7fffffu);
-    return __uint_as_float(sgn | ((unsigned)(ex + 127) << 23) | (unsigned)((b >> 29) & 0x7fffff));
-}
-__device__ __forceinline__ double os_to_double(float x) {
-    const unsigned b = __float_as_uint(x);
-    const unsigned ex = (b >> 23) & 0xff;
-    if (ex == 0) return 0.0;
-    const unsigned long long d = ((unsigned long long)(b >> 31) << 63) | ((unsigned long long)(ex + 896) << 52) |
-                                 ((unsigned long long)(b & 0x7fffff) << 29);
-    return __longlong_as_double((long long)d);
-}
 __device__ __forceinline__ int os_hi(double x) { return __double2hiint(x); }
 __device__ __forceinline__ uint32_t os_mapa(const void* local, int rank) {
     uint32_t raddr;
