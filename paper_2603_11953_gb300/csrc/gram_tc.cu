@@ -57,6 +57,7 @@ constexpr int TC_SUB = 64;           // rows per sub-chunk (= MMA K of one digit
 constexpr int TC_PERIOD = 16;        // sub-chunks per exact accumulation period (1024 rows)
 constexpr int TC_SF = 6;             // FP32 stages
 constexpr int TC_SD = 2;             // digit stages
+constexpr int TC_MX = 4;             // column-maxima slots (the workers publish two sub-chunks ahead)
 constexpr int TC_THREADS = 640;   // 4 control warps + 16 workers
 constexpr int TC_WORKERS = 512;
 constexpr int TC_RD = 8;              // decision records
@@ -147,12 +148,14 @@ struct TcShared {
     uint64_t fp_full[TC_SF], fp_empty[TC_SF];
     uint64_t dig_full[TC_SD], dig_empty[TC_SD];
     uint64_t dec_full[TC_RD], dec_empty[TC_RD];
+    uint64_t max_full[TC_MX];  // per sub-chunk (mod TC_MX): the workers have published its column maxima
     uint64_t acc_full, acc_empty;
     TcRecord rec[TC_RD];
     int dflags[2][2];      // decider warps: growth (soft 1, hard 2) and abort (4) bits, double-buffered
     uint32_t tmem_base;
     int abort;             // some role gave up (bounded wait expired)
     int dig_newp[TC_SD];   // the sub-chunk in this digit stage opens a new period
+    unsigned colmax[TC_MX][64];  // per sub-chunk (mod TC_MX): max |a| of each column (float bit pattern)
 };
 
 // Bit pattern of the float 1.5 * 2^e.  Adding it to a float x with |x| <= 2^(e-1)
@@ -343,6 +346,35 @@ __device__ __forceinline__ void tc_drain(const TcRecord& R, uint32_t tmem, int q
     else tc_fold_all<1>(trow, hi, lo, res);            // lanes 64..127: second digit
 }
 
+// The workers publish the column maxima of sub-chunk h for the deciders: lane l takes rows
+// 8 (l % 8) .. + 7 of column 4 w + l / 8 (the digits' layout), the column's 8 lanes combine
+// theirs by shuffles.  max |a| is taken on the bit patterns (Inf and NaN order above every
+// finite value).  False if the stage did not land (it is then not read).
+__device__ __forceinline__ bool tc_publish_max(TcShared& S, const float* fpb, int h, int n, int wq, int lane,
+                                               long long wait_limit) {
+    const int f = h % TC_SF;
+    bool ok = mbar_wait(&S.fp_full[f], (h / TC_SF) & 1, wait_limit) && !S.abort;
+    if (!__all_sync(0xffffffffu, ok)) return false;
+    const int jj = 4 * wq + (lane >> 3), rb = lane & 7;
+    unsigned mx = 0u;
+    if (jj < n) {
+        const float4* src =
+            reinterpret_cast<const float4*>(fpb + (size_t)f * 64 * TC_SUB + (size_t)jj * TC_SUB + 8 * rb);
+        const float4 a = src[0], b = src[1];
+        mx = max(max(max(__float_as_uint(a.x) & 0x7fffffffu, __float_as_uint(a.y) & 0x7fffffffu),
+                     max(__float_as_uint(a.z) & 0x7fffffffu, __float_as_uint(a.w) & 0x7fffffffu)),
+                 max(max(__float_as_uint(b.x) & 0x7fffffffu, __float_as_uint(b.y) & 0x7fffffffu),
+                     max(__float_as_uint(b.z) & 0x7fffffffu, __float_as_uint(b.w) & 0x7fffffffu)));
+    }
+    mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+    mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+    mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 4));
+    if (rb == 0) S.colmax[h % TC_MX][jj] = mx;
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&S.max_full[h % TC_MX]);
+    return true;
+}
+
 // partial slot and status block of this CTA (batched use: those of its item)
 template <bool BATCH>
 __device__ __forceinline__ int64_t tc_slot(const TcBatchItem* items) {
@@ -406,9 +438,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     (void)rows_per_cta;
 
     if (tid == 0) {
-        // an FP32 stage is free once both deciders and the MMA issuer (which sees every worker's
-        // digits of that sub-chunk) have passed it
-        for (int s = 0; s < TC_SF; ++s) { mbar_init(&S.fp_full[s], 1); mbar_init(&S.fp_empty[s], 2 + 1); }
+        // an FP32 stage is free once the MMA issuer has seen every worker's digits of that
+        // sub-chunk (the workers read it for its maxima and its digits only)
+        for (int s = 0; s < TC_SF; ++s) { mbar_init(&S.fp_full[s], 1); mbar_init(&S.fp_empty[s], 1); }
+        for (int s = 0; s < TC_MX; ++s) mbar_init(&S.max_full[s], 16);
         for (int s = 0; s < TC_SD; ++s) { mbar_init(&S.dig_full[s], 16); mbar_init(&S.dig_empty[s], 1); }
         for (int s = 0; s < TC_RD; ++s) { mbar_init(&S.dec_full[s], 2); mbar_init(&S.dec_empty[s], 16); }
         mbar_init(&S.acc_full, 1);
@@ -488,8 +521,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             (void)mbar_wait(&S.acc_full, period & 1);
         } else if (warp >= 2) {
             // ---------------- deciders (warps 2, 3; lane l owns column j = 32 (warp - 2) + l).
-            // For each sub-chunk as soon as it lands: column maxima -> growth class; the two
-            // warps agree on whether a new period starts (an entry needs more than one binade
+            // For each sub-chunk, from the column maxima the workers publish: growth class; the
+            // two warps agree on whether a new period starts (an entry needs more than one binade
             // above the running scale, or the exactness budget is spent) and publish a record.
             const int dw = warp - 2, j = 32 * dw + lane;
             int Ecur = EXP_EMPTY, Epend = EXP_EMPTY, Eacc = EXP_EMPTY, period_len = 0;
@@ -502,24 +535,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const int r = g % TC_RD;
                 int fl = 0;
                 if (g < G) {
-                    const int f = g % TC_SF;
-                    const bool landed = mbar_wait(&S.fp_full[f], (g / TC_SF) & 1, wait_limit);
-                    if (!landed) fl |= 4;
-                    // max |a| of column j on the bit patterns (Inf / NaN have the largest); the
-                    // lanes start at staggered row quads so each 16-byte load is conflict-free.
-                    // A stage whose wait gave up is not read (its contents are not the input).
-                    unsigned mine = 0;
-                    if (landed && j < n) {
-                        const float* col = fpb + (size_t)f * 64 * TC_SUB + (size_t)j * TC_SUB;
-#pragma unroll 4
-                        for (int k = 0; k < 16; ++k) {
-                            const uint4 v = *reinterpret_cast<const uint4*>(col + 4 * ((k + lane) & 15));
-                            mine = max(mine, max(max(v.x & 0x7fffffffu, v.y & 0x7fffffffu),
-                                                 max(v.z & 0x7fffffffu, v.w & 0x7fffffffu)));
-                        }
-                    }
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&S.fp_empty[f]);
+                    // the column maxima of sub-chunk g, found by the workers (8 lanes per column)
+                    const bool got = mbar_wait(&S.max_full[g % TC_MX], (g / TC_MX) & 1, wait_limit);
+                    if (!got) fl |= 4;
+                    const unsigned mine = got ? S.colmax[g % TC_MX][j] : 0u;
                     if (mine >= 0x7f800000u) bad = true;
                     const int e = (mine == 0u || mine >= 0x7f800000u) ? EXP_EMPTY : tc_exp_above(__uint_as_float(mine));
                     // one binade above the running scale is "soft" (top digit in [-256, 256], still
@@ -595,7 +614,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         for (int k = 0; k < 8; ++k) res[k] = 0u;
         int drained = 0, res_periods = 0;
         bool failed = false;
-        for (int g = 0; g <= G; ++g) {
+        // the maxima of sub-chunk g + 2 are published right after the digits of sub-chunk g, so
+        // the deciders have a whole sub-chunk's time for each record
+        for (int h = 0; h < 2 && h < G && !failed; ++h) {
+            if (!tc_publish_max(S, fpb, h, n, wq, lane, wait_limit)) {
+                failed = true;
+                if (lane == 0) atomicExch(&S.abort, 1);
+            }
+        }
+        for (int g = 0; g <= G && !failed; ++g) {
             const int r = g % TC_RD;
             bool ok = mbar_wait(&S.dec_full[r], (g / TC_RD) & 1, wait_limit) && !S.abort;
             if (!__all_sync(0xffffffffu, ok)) { failed = true; break; }
@@ -651,6 +678,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 if (lane == 0) {
                     S.dig_newp[d] = newp;  // every warp writes the same value
                     mbar_arrive(&S.dig_full[d]);
+                }
+                if (g + 2 < G && !tc_publish_max(S, fpb, g + 2, n, wq, lane, wait_limit)) {
+                    failed = true;
+                    if (lane == 0) atomicExch(&S.abort, 1);
+                    break;
                 }
             }
             if (((newp && g > 0) || g == G) && G > 0) {
