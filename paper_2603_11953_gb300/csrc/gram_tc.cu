@@ -195,13 +195,21 @@ __host__ __device__ constexpr TcFold tc_fold(int h, int cb) {
                    : cb == 6 ? TcFold{0, 32, 0, 12}    // (2,2) diagonal: 1/2
                              : TcFold{2, 48, 9, 0});   // (3,3) diagonal: 1/2
 }
+// A block of kind 0 adds y = (a << g) + b (mod 2^32) to hi, shifted by sh: a and b are the
+// bit patterns of 1.5 2^(23+g-w) + a' 2^(g-w) and 1.5 2^(23-w) + b' 2^-w, so y is the block's
+// value P = a' 2^g + b' (|P| <= 2^24) plus a constant bias that keeps y inside [0, 2^32)
+// (no data-dependent wrap), and hi gets P 2^sh plus the bias 2^sh.
+__host__ __device__ constexpr uint32_t tc_fold_bias(TcFold f) {
+    return (uint32_t)((tc_magic(23 + f.g - f.w) << f.g) + tc_magic(23 - f.w));
+}
+__host__ __device__ constexpr bool tc_fold_nowrap(TcFold f) {
+    return tc_fold_bias(f) >= (1u << 24) && tc_fold_bias(f) <= 0xffffffffu - (1u << 24);
+}
 __host__ __device__ constexpr unsigned long long tc_hi_offset(int h) {
     unsigned long long o = 0;
     for (int cb = 0; cb < 8; ++cb) {
         const TcFold f = tc_fold(h, cb);
-        if (f.kind == 0)
-            o += ((unsigned long long)tc_magic(23 + f.g - f.w) << (f.sh + f.g)) +
-                 ((unsigned long long)tc_magic(23 - f.w) << f.sh);
+        if (f.kind == 0) o += (unsigned long long)tc_fold_bias(f) << f.sh;
     }
     return o;
 }
@@ -213,18 +221,6 @@ __host__ __device__ constexpr uint32_t tc_lo_offset(int h) {
         if (f.kind == 2) o += tc_magic(23 + f.sh - f.w);
     }
     return o;
-}
-
-// Empty asm with the accumulators as operands: everything before it that updates
-// them completes first, so the next block's TMEM load does not raise the number
-// of live registers (the compiler would otherwise overlap whole blocks).
-__device__ __forceinline__ void tc_pin(unsigned long long (&hi)[16], uint32_t (&lo)[16]) {
-    asm volatile("" : "+l"(hi[0]), "+l"(hi[1]), "+l"(hi[2]), "+l"(hi[3]), "+l"(hi[4]), "+l"(hi[5]), "+l"(hi[6]),
-                      "+l"(hi[7]), "+l"(hi[8]), "+l"(hi[9]), "+l"(hi[10]), "+l"(hi[11]), "+l"(hi[12]), "+l"(hi[13]),
-                      "+l"(hi[14]), "+l"(hi[15]));
-    asm volatile("" : "+r"(lo[0]), "+r"(lo[1]), "+r"(lo[2]), "+r"(lo[3]), "+r"(lo[4]), "+r"(lo[5]), "+r"(lo[6]),
-                      "+r"(lo[7]), "+r"(lo[8]), "+r"(lo[9]), "+r"(lo[10]), "+r"(lo[11]), "+r"(lo[12]), "+r"(lo[13]),
-                      "+r"(lo[14]), "+r"(lo[15]));
 }
 
 // Residuals of the s + t = 6 blocks: kind 2 adds RN(P / 2^RS) to lo and keeps the exact
@@ -246,11 +242,10 @@ template <int H, int CB>
 __device__ __forceinline__ void tc_fold_block(uint32_t trow, unsigned long long (&hi)[16], uint32_t (&lo)[16],
                                               uint32_t (&res)[8]) {
     constexpr TcFold F = tc_fold(H, CB);
-    // two halves of 8 columns keep the temporaries few (the accumulators use 48 registers)
+    // two halves of 8 columns keep the temporaries few (the accumulators use 56 registers)
 #pragma unroll
     for (int hf = 0; hf < 2; ++hf) {
         uint32_t r[8];
-        tc_pin(hi, lo);
         tmem_ld8(trow + CB * 64 + 8 * hf, r);
         if constexpr (F.kind == 2) {
             constexpr unsigned long long C = tc_magic2(23 + F.sh - F.w), CR = tc_magic2(23 - F.w);
@@ -285,13 +280,10 @@ __device__ __forceinline__ void tc_fold_block(uint32_t trow, unsigned long long 
                 if constexpr (F.kind == 1) {
                     lo[kk] += (a0 << F.g) + b0;
                     lo[kk + 1] += (a1 << F.g) + b1;
-                } else if constexpr (F.sh >= 32) {
+                } else {
+                    static_assert(tc_fold_nowrap(F), "the combined pattern must not wrap");
                     hi[kk] += (unsigned long long)((a0 << F.g) + b0) << F.sh;
                     hi[kk + 1] += (unsigned long long)((a1 << F.g) + b1) << F.sh;
-                } else {
-                    static_assert(F.kind != 0 || F.sh >= 32 || F.sh + F.g <= 31, "multiplier must fit 32 bits");
-                    hi[kk] += (unsigned long long)a0 * (1u << (F.sh + F.g)) + (unsigned long long)b0 * (1u << F.sh);
-                    hi[kk + 1] += (unsigned long long)a1 * (1u << (F.sh + F.g)) + (unsigned long long)b1 * (1u << F.sh);
                 }
             }
         }
@@ -347,20 +339,21 @@ __device__ __forceinline__ void tc_drain(const TcRecord& R, uint32_t tmem, int q
 }
 
 // The workers publish the column maxima of sub-chunk h for the deciders: lane l takes rows
-// 8 (l % 8) .. + 7 of column 4 w + l / 8 (the digits' layout), the column's 8 lanes combine
+// 4 (l % 8) .. + 3 and 32 + 4 (l % 8) .. + 3 of column 4 w + l / 8 (the digits' layout: 8 lanes
+// read 128 contiguous bytes per 16-byte load, no bank conflict), the column's 8 lanes combine
 // theirs by shuffles.  max |a| is taken on the bit patterns (Inf and NaN order above every
 // finite value).  False if the stage did not land (it is then not read).
 __device__ __forceinline__ bool tc_publish_max(TcShared& S, const float* fpb, int h, int n, int wq, int lane,
                                                long long wait_limit) {
     const int f = h % TC_SF;
-    bool ok = mbar_wait(&S.fp_full[f], (h / TC_SF) & 1, wait_limit) && !S.abort;
+    bool ok = mbar_wait_susp(&S.fp_full[f], (h / TC_SF) & 1, wait_limit) && !S.abort;
     if (!__all_sync(0xffffffffu, ok)) return false;
     const int jj = 4 * wq + (lane >> 3), rb = lane & 7;
     unsigned mx = 0u;
     if (jj < n) {
         const float4* src =
-            reinterpret_cast<const float4*>(fpb + (size_t)f * 64 * TC_SUB + (size_t)jj * TC_SUB + 8 * rb);
-        const float4 a = src[0], b = src[1];
+            reinterpret_cast<const float4*>(fpb + (size_t)f * 64 * TC_SUB + (size_t)jj * TC_SUB + 4 * rb);
+        const float4 a = src[0], b = src[8];
         mx = max(max(max(__float_as_uint(a.x) & 0x7fffffffu, __float_as_uint(a.y) & 0x7fffffffu),
                      max(__float_as_uint(a.z) & 0x7fffffffu, __float_as_uint(a.w) & 0x7fffffffu)),
                  max(max(__float_as_uint(b.x) & 0x7fffffffu, __float_as_uint(b.y) & 0x7fffffffu),
@@ -471,7 +464,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             int issued = 0;
             for (int g = 0; g < G; ++g) {
                 const int f = g % TC_SF;
-                if (g >= TC_SF && !mbar_wait(&S.fp_empty[f], ((g / TC_SF) - 1) & 1, wait_limit)) {
+                if (g >= TC_SF && !mbar_wait_susp(&S.fp_empty[f], ((g / TC_SF) - 1) & 1, wait_limit)) {
                     atomicExch(&S.abort, 1);
                     break;
                 }
@@ -489,7 +482,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             int period = 0;
             for (int g = 0; g < G; ++g) {
                 const int d = g % TC_SD;
-                if (!mbar_wait(&S.dig_full[d], (g / TC_SD) & 1, wait_limit) || S.abort) {
+                if (!mbar_wait_susp(&S.dig_full[d], (g / TC_SD) & 1, wait_limit) || S.abort) {
                     atomicExch(&S.abort, 1);
                     break;
                 }
@@ -498,7 +491,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 if (newp && g > 0) {
                     // close the running period: the workers drain it before it is overwritten
                     mma_commit(&S.acc_full);
-                    if (!mbar_wait(&S.acc_empty, period & 1, wait_limit)) { atomicExch(&S.abort, 1); break; }
+                    if (!mbar_wait_susp(&S.acc_empty, period & 1, wait_limit)) { atomicExch(&S.abort, 1); break; }
                     tc_fence_after();
                     ++period;
                 }
@@ -518,7 +511,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             // the last period (or, after a failure, whatever was accumulated) goes to the workers;
             // every MMA issued by this thread has completed once that phase completes
             mma_commit(&S.acc_full);
-            (void)mbar_wait(&S.acc_full, period & 1);
+            (void)mbar_wait_susp(&S.acc_full, period & 1);
         } else if (warp >= 2) {
             // ---------------- deciders (warps 2, 3; lane l owns column j = 32 (warp - 2) + l).
             // For each sub-chunk, from the column maxima the workers publish: growth class; the
@@ -536,7 +529,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 int fl = 0;
                 if (g < G) {
                     // the column maxima of sub-chunk g, found by the workers (8 lanes per column)
-                    const bool got = mbar_wait(&S.max_full[g % TC_MX], (g / TC_MX) & 1, wait_limit);
+                    const bool got = mbar_wait_susp(&S.max_full[g % TC_MX], (g / TC_MX) & 1, wait_limit);
                     if (!got) fl |= 4;
                     const unsigned mine = got ? S.colmax[g % TC_MX][j] : 0u;
                     if (mine >= 0x7f800000u) bad = true;
@@ -554,7 +547,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         Epend = max(Epend, e);
                     }
                 }
-                if (g >= TC_RD && !mbar_wait(&S.dec_empty[r], ((g / TC_RD) - 1) & 1, wait_limit)) fl |= 4;
+                if (g >= TC_RD && !mbar_wait_susp(&S.dec_empty[r], ((g / TC_RD) - 1) & 1, wait_limit)) fl |= 4;
                 if (S.abort) fl |= 4;
                 fl = __reduce_or_sync(0xffffffffu, fl);
                 if (lane == 0) S.dflags[g & 1][dw] = fl;
@@ -624,7 +617,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         for (int g = 0; g <= G && !failed; ++g) {
             const int r = g % TC_RD;
-            bool ok = mbar_wait(&S.dec_full[r], (g / TC_RD) & 1, wait_limit) && !S.abort;
+            bool ok = mbar_wait_susp(&S.dec_full[r], (g / TC_RD) & 1, wait_limit) && !S.abort;
             if (!__all_sync(0xffffffffu, ok)) { failed = true; break; }
             const TcRecord& R = S.rec[r];
             const int newp = R.newp;
@@ -632,20 +625,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const int d = g % TC_SD, f = g % TC_SF;
                 // the FP32 stage has landed: the deciders waited for it before publishing the record
                 // (their release on dec_full orders it before this warp's acquire)
-                ok = g < TC_SD || mbar_wait(&S.dig_empty[d], ((g / TC_SD) - 1) & 1, wait_limit);
+                ok = g < TC_SD || mbar_wait_susp(&S.dig_empty[d], ((g / TC_SD) - 1) & 1, wait_limit);
                 if (!__all_sync(0xffffffffu, ok)) { failed = true; break; }
                 // digits of sub-chunk g: y = 128 a 2^-E (|y| < 128, < 256 after a soft growth);
                 // digit s is y's remainder rounded to the grid 2^-8s (|digit| <= 128 grid units,
                 // exact in bf16: 8 significant bits); the MMA sees digit s scaled by 2^-8s.
-                // Lane l takes rows 8 (l % 8) .. + 7 of column j = 4 w + l / 8: one 16-byte chunk
-                // of a digit slice per digit (a quarter-warp writes one slice row, 128 bytes).
+                // Lane l takes rows 4 (l % 8) .. + 3 and 32 + 4 (l % 8) .. + 3 of column
+                // j = 4 w + l / 8 and writes them as K positions 8 (l % 8) .. + 7: one 16-byte chunk
+                // of a digit slice per digit (a quarter-warp writes one slice row, 128 bytes).  Every
+                // slice holds the rows in the same order, so each block's sum over K is unchanged.
                 const int jj = 4 * wq + (lane >> 3), rb = lane & 7;
                 const int E = R.E[jj];
                 unsigned long long y[4] = {0ull, 0ull, 0ull, 0ull};
                 if (E != EXP_EMPTY) {
                     const float4* src =
-                        reinterpret_cast<const float4*>(fpb + (size_t)f * 64 * TC_SUB + (size_t)jj * TC_SUB + 8 * rb);
-                    const float4 a = src[0], b = src[1];
+                        reinterpret_cast<const float4*>(fpb + (size_t)f * 64 * TC_SUB + (size_t)jj * TC_SUB + 4 * rb);
+                    const float4 a = src[0], b = src[8];
                     const int k = 7 - E, k1 = k / 2, k2 = k - k1;
                     const float s1 = __int_as_float((k1 + 127) << 23), s2 = __int_as_float((k2 + 127) << 23);
                     const unsigned long long S1 = f2_pack(s1, s1), S2 = f2_pack(s2, s2);
@@ -688,7 +683,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             if (((newp && g > 0) || g == G) && G > 0) {
                 // the MMA issuer closes a period on seeing the first stage of the next one
                 // (or after the last sub-chunk); drain it
-                ok = mbar_wait(&S.acc_full, drained & 1, wait_limit);
+                ok = mbar_wait_susp(&S.acc_full, drained & 1, wait_limit);
                 if (!__all_sync(0xffffffffu, ok)) { failed = true; break; }
                 tc_fence_after();
                 if (res_periods == 32) {
@@ -738,7 +733,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         atomicOr(&tc_info<BATCH>(info, items)->flags, FLAG_TIMEOUT);
         // no TMA write may land after the CTA exits: wait (bounded) for the last loads
         for (int g = (tma_issued > TC_SF ? tma_issued - TC_SF : 0); g < tma_issued; ++g)
-            (void)mbar_wait(&S.fp_full[g % TC_SF], (g / TC_SF) & 1);
+            (void)mbar_wait_susp(&S.fp_full[g % TC_SF], (g / TC_SF) & 1);
     }
     if (warp == 1) {
         __syncwarp();

@@ -52,6 +52,23 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, long l
         if (clock64() - t0 > limit) return false;
     }
 }
+// As mbar_wait, with a suspend-time hint: a warp whose phase is not complete is descheduled
+// until it completes or hint_ns nanoseconds pass, and does not take issue slots meanwhile.
+__device__ __forceinline__ bool mbar_wait_susp(uint64_t* bar, unsigned parity, long long limit = TMA_WAIT_CYCLES,
+                                               unsigned hint_ns = 2000) {
+    const long long t0 = clock64();
+    for (;;) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(smem_addr(bar)), "r"(parity), "r"(hint_ns)
+            : "memory");
+        if (ok) return true;
+        if (clock64() - t0 > limit) return false;
+    }
+}
 // 2-D tiled TMA load of the box at (x = row, y = column) into dst.
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
     asm volatile(
