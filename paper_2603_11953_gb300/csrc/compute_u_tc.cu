@@ -25,8 +25,12 @@
 //   warps 4-11  convert each tile into the K-major, 128-byte-swizzled hi and
 //               lo operands (thread t: row t % 128, columns 32 (t / 128)..+31),
 //               and write the previous tile's U from TMEM (lane = row, 32
-//               columns per thread; each warp store covers 32 consecutive rows
-//               of one column, 128 bytes).
+//               columns per thread): into a shared output tile that warp 2
+//               sends to U with one TMA store (a 16-byte-aligned U), else
+//               straight to U (each warp store covers 32 consecutive rows of
+//               one column, 128 bytes).
+// With the TMA store the ring has 3 A stages, the fourth 32 KB going to the
+// output tile: loads and stores both stay in flight, as in a TMA copy.
 // W^T (the B operand, rows = columns of U) is split once per CTA.  Every
 // mbarrier wait is bounded; on timeout the kernel records TSVD_ERR_TIMEOUT,
 // waits for its own TMA loads and frees its TMEM.
@@ -41,13 +45,18 @@ constexpr int UT_THREADS = 384;
 constexpr int UT_FP_BYTES = 64 * UT_ROWS * 4;      // one A tile: [64 cols][128 rows] FP32
 constexpr int UT_OP_BYTES = 2 * UT_ROWS * 128;     // one K-major tf32 operand: [2 atoms][128 rows][128 B]
 constexpr int UT_W_BYTES = 2 * 64 * 128;           // W^T operand: [2 atoms][64 rows][128 B]
-constexpr int UT_SF = 4, UT_SO = 1;   // 4 A tiles in flight keep ~96 KB of loads outstanding per SM
-constexpr int UT_SMEM = UT_SF * UT_FP_BYTES + UT_SO * 2 * UT_OP_BYTES + 2 * UT_W_BYTES + 1024;
+constexpr int UT_SO = 1;
+// A stages: 4 (~96 KB of loads outstanding per SM) with plain stores, 3 beside the output tile
+template <bool TS> __host__ __device__ constexpr int ut_sf() { return TS ? 3 : 4; }
+template <bool TS> __host__ __device__ constexpr int ut_smem() {
+    return ut_sf<TS>() * UT_FP_BYTES + UT_SO * 2 * UT_OP_BYTES + 2 * UT_W_BYTES + (TS ? UT_FP_BYTES : 0) + 1024;
+}
 
 struct UtShared {
-    uint64_t fp_full[UT_SF], fp_empty[UT_SF];
+    uint64_t fp_full[4], fp_empty[4];
     uint64_t op_full[UT_SO], op_empty[UT_SO];
     uint64_t acc_full[2], acc_empty[2];
+    uint64_t out_full, out_free;  // output tile written by the 8 epilogue warps / read by its TMA store
     uint32_t tmem_base;
     int abort;
 };
@@ -86,25 +95,39 @@ __device__ __forceinline__ void ut_ld16(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 // Round to TF32 (10 explicit significand bits, to nearest, ties away from zero):
-// the MMA ignores the low 13 bits, so a rounded value is used exactly.
+// half a TF32 ulp (2^12 in the bit pattern) is added to the magnitude bits and
+// the 13 low bits are cleared, the rounding cvt.rna.tf32.f32 does, in two
+// integer operations (the conversion instruction made the kernel issue-bound).
+// A carry into the exponent is the correct round-up; the MMA ignores the low
+// 13 bits, so a rounded value is used exactly.
 __device__ __forceinline__ float ut_tf32(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
+    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xffffe000u);
 }
 // byte offset of element (row, k) in a [2 atoms][rows][128 B] K-major SW128 operand
 __device__ __forceinline__ uint32_t ut_off(int row, int k, int rows) {
     return (uint32_t)((k >> 5) * rows * 128 + row * 128 + ((((k & 31) >> 2) ^ (row & 7)) << 4) + ((k & 3) << 2));
 }
 
+// TMA store of the output tile (box = 128 rows x n columns) to rows x0.. of U
+__device__ __forceinline__ void ut_tma_store(const CUtensorMap* map, const void* src, int x0) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x0), "r"(0), "r"(smem_addr(src))
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+template <bool TS>
 __global__ void __launch_bounds__(UT_THREADS, 1)
-    compute_u_tc_kernel(const __grid_constant__ CUtensorMap tmapA, int64_t m, int n, const float* __restrict__ W,
-                        float* __restrict__ U, int64_t ldu, DevInfo* info) {
+    compute_u_tc_kernel(const __grid_constant__ CUtensorMap tmapA, const __grid_constant__ CUtensorMap tmapU, int64_t m,
+                        int n, const float* __restrict__ W, float* __restrict__ U, int64_t ldu, DevInfo* info) {
+    constexpr int SF = ut_sf<TS>();
     extern __shared__ unsigned char ut_dyn[];
     unsigned char* base = ut_dyn + ((1024 - (smem_addr(ut_dyn) & 1023)) & 1023);
     unsigned char* ops = base;                                        // [SO][hi, lo][UT_OP_BYTES]
     unsigned char* wop = base + UT_SO * 2 * UT_OP_BYTES;              // [hi, lo][UT_W_BYTES]
     float* fpb = reinterpret_cast<float*>(wop + 2 * UT_W_BYTES);      // [SF][64][128]
+    float* outb = fpb + (size_t)SF * 64 * UT_ROWS;                    // TS: [n][128] output tile
     __shared__ UtShared S;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -113,9 +136,11 @@ __global__ void __launch_bounds__(UT_THREADS, 1)
     const int T = (int64_t)blockIdx.x < tiles ? (int)((tiles - 1 - blockIdx.x) / P + 1) : 0;
 
     if (tid == 0) {
-        for (int s = 0; s < UT_SF; ++s) { mbar_init(&S.fp_full[s], 1); mbar_init(&S.fp_empty[s], 8); }
+        for (int s = 0; s < SF; ++s) { mbar_init(&S.fp_full[s], 1); mbar_init(&S.fp_empty[s], 8); }
         for (int s = 0; s < UT_SO; ++s) { mbar_init(&S.op_full[s], 8); mbar_init(&S.op_empty[s], 1); }
         for (int s = 0; s < 2; ++s) { mbar_init(&S.acc_full[s], 1); mbar_init(&S.acc_empty[s], 8); }
+        mbar_init(&S.out_full, 8);
+        mbar_init(&S.out_free, 1);
         mbar_fence_init();
         S.abort = 0;
     }
@@ -145,8 +170,8 @@ __global__ void __launch_bounds__(UT_THREADS, 1)
             tma_prefetch_desc(&tmapA);
             const unsigned bytes = (unsigned)(UT_ROWS * n * 4);
             for (int j = 0; j < T; ++j) {
-                const int f = j % UT_SF;
-                if (j >= UT_SF && !mbar_wait(&S.fp_empty[f], ((j / UT_SF) - 1) & 1)) { atomicExch(&S.abort, 1); break; }
+                const int f = j % SF;
+                if (j >= SF && !mbar_wait(&S.fp_empty[f], ((j / SF) - 1) & 1)) { atomicExch(&S.abort, 1); break; }
                 if (S.abort) break;
                 mbar_expect_tx(&S.fp_full[f], bytes);
                 tma_load_2d(fpb + (size_t)f * 64 * UT_ROWS, &tmapA, (int)(((int64_t)blockIdx.x + (int64_t)j * P) * UT_ROWS),
@@ -177,6 +202,19 @@ __global__ void __launch_bounds__(UT_THREADS, 1)
                 ut_commit(&S.acc_full[b]);
             }
         }
+    } else if (warp == 2) {
+        if (TS && lane == 0) {
+            // ---------------- output tile -> U (TMA store), then hand the tile back
+            tma_prefetch_desc(&tmapU);
+            for (int j = 0; j < T; ++j) {
+                if (!mbar_wait(&S.out_full, j & 1) || S.abort) { atomicExch(&S.abort, 1); break; }
+                ut_tma_store(&tmapU, outb, (int)(((int64_t)blockIdx.x + (int64_t)j * P) * UT_ROWS));
+                asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+                mbar_arrive(&S.out_free);
+            }
+            // the stores have left shared memory; wait for their writes too before the CTA exits
+            asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+        }
     } else if (warp >= 4) {
         // ---------------- converters and epilogue
         const int t = tid - 128;
@@ -187,6 +225,8 @@ __global__ void __launch_bounds__(UT_THREADS, 1)
         auto epilogue = [&](int jj) {
             const int b = jj & 1;
             if (!mbar_wait(&S.acc_full[b], (jj / 2) & 1)) ok = false;
+            // TS: the previous tile's store has read the output tile
+            if (TS && jj >= 1 && !mbar_wait(&S.out_free, (jj - 1) & 1)) ok = false;
             ut_fence_after();
             const int64_t r0 = ((int64_t)blockIdx.x + (int64_t)jj * P) * UT_ROWS + 32 * q + lane;
             const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * 64 + 32 * colh);
@@ -194,7 +234,13 @@ __global__ void __launch_bounds__(UT_THREADS, 1)
             for (int hh = 0; hh < 2; ++hh) {
                 uint32_t r[16];
                 ut_ld16(ta + 16 * hh, r);
-                if (r0 < m) {
+                if (TS) {
+                    // [column][128 rows]: a warp writes 32 consecutive rows of one column
+                    float* oc = outb + (size_t)(32 * colh + 16 * hh) * UT_ROWS + 32 * q + lane;
+#pragma unroll
+                    for (int c = 0; c < 16; ++c)
+                        if (n == 64 || 32 * colh + 16 * hh + c < n) oc[c * UT_ROWS] = __uint_as_float(r[c]);
+                } else if (r0 < m) {
                     float* ur = U + r0 + (size_t)(32 * colh + 16 * hh) * ldu;
                     if (n == 64) {
 #pragma unroll
@@ -207,12 +253,16 @@ __global__ void __launch_bounds__(UT_THREADS, 1)
                 }
             }
             ut_fence_before();
+            if (TS) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncwarp();
-            if (lane == 0) mbar_arrive(&S.acc_empty[b]);
+            if (lane == 0) {
+                mbar_arrive(&S.acc_empty[b]);
+                if (TS) mbar_arrive(&S.out_full);
+            }
         };
         for (int j = 0; j < T && ok; ++j) {
-            const int f = j % UT_SF, o = j % UT_SO;
-            if (!mbar_wait(&S.fp_full[f], (j / UT_SF) & 1)) { ok = false; break; }
+            const int f = j % SF, o = j % UT_SO;
+            if (!mbar_wait(&S.fp_full[f], (j / SF) & 1)) { ok = false; break; }
             if (j >= UT_SO && !mbar_wait(&S.op_empty[o], ((j / UT_SO) - 1) & 1)) { ok = false; break; }
             const float* fp = fpb + (size_t)f * 64 * UT_ROWS + row;
             unsigned char* oh = ops + (size_t)o * 2 * UT_OP_BYTES;
@@ -251,8 +301,8 @@ __global__ void __launch_bounds__(UT_THREADS, 1)
     __syncthreads();
     if (S.abort && tid == 0) {
         atomicOr(&info->flags, FLAG_TIMEOUT);
-        for (int j = (tma_issued > UT_SF ? tma_issued - UT_SF : 0); j < tma_issued; ++j)
-            (void)mbar_wait(&S.fp_full[j % UT_SF], (j / UT_SF) & 1);
+        for (int j = (tma_issued > SF ? tma_issued - SF : 0); j < tma_issued; ++j)
+            (void)mbar_wait(&S.fp_full[j % SF], (j / SF) & 1);
     }
     if (warp == 1) {
         __syncwarp();
@@ -270,16 +320,27 @@ bool compute_u_tc_ok(const void* A, int working, int64_t m, int n, int64_t lda) 
 
 cudaError_t launch_compute_u_tc(const float* A, int64_t m, int n, int64_t lda, const float* W, float* U,
                                 int64_t ldu, int sm_count, DevInfo* info, cudaStream_t s) {
-    CUtensorMap tmap;
+    CUtensorMap tmap, tmapU;
     cudaError_t e = make_tmap_2d(&tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, sizeof(float), A, (uint64_t)m,
                                  (uint64_t)n, (uint64_t)lda, UT_ROWS, (uint32_t)n, CU_TENSOR_MAP_SWIZZLE_NONE);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(compute_u_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, UT_SMEM);
-    if (e != cudaSuccess) return e;
+    // U written by TMA stores when its base and column stride are 16-byte aligned
+    const bool ts = ((uintptr_t)U % 16 == 0) && (ldu % 4 == 0) &&
+                    make_tmap_2d(&tmapU, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, sizeof(float), U, (uint64_t)m, (uint64_t)n,
+                                 (uint64_t)ldu, UT_ROWS, (uint32_t)n, CU_TENSOR_MAP_SWIZZLE_NONE) == cudaSuccess;
+    if (!ts) tmapU = tmap;  // unused
     const int64_t tiles = (m + UT_ROWS - 1) / UT_ROWS;
     int64_t grid = sm_count;
     if (grid > tiles) grid = tiles;
-    compute_u_tc_kernel<<<(unsigned)grid, UT_THREADS, UT_SMEM, s>>>(tmap, m, n, W, U, ldu, info);
+    if (ts) {
+        e = cudaFuncSetAttribute(compute_u_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ut_smem<true>());
+        if (e != cudaSuccess) return e;
+        compute_u_tc_kernel<true><<<(unsigned)grid, UT_THREADS, ut_smem<true>(), s>>>(tmap, tmapU, m, n, W, U, ldu, info);
+    } else {
+        e = cudaFuncSetAttribute(compute_u_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ut_smem<false>());
+        if (e != cudaSuccess) return e;
+        compute_u_tc_kernel<false><<<(unsigned)grid, UT_THREADS, ut_smem<false>(), s>>>(tmap, tmapU, m, n, W, U, ldu, info);
+    }
     return cudaGetLastError();
 }
 
