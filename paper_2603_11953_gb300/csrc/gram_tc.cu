@@ -652,6 +652,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 unsigned char* drow = dig + (size_t)d * TC_DIG_BYTES + jj * 128 + ((rb ^ (jj & 7)) << 4);
 #pragma unroll
                 for (int sdig = 0; sdig < 7; ++sdig) {
+                    // when no row of the warp has a remainder left after five digits, the last two
+                    // are +0 (what the split would give): store them without the arithmetic.  Only
+                    // an entry about 2^16 or more below its column's largest (|y| < 2^-9) has bits
+                    // below 2^-32 left, so most warps skip.
+                    if (sdig == 5 &&
+                        !__any_sync(0xffffffffu, ((y[0] | y[1] | y[2] | y[3]) & 0x7fffffff7fffffffull) != 0ull)) {
+#pragma unroll
+                        for (int z = sdig; z < 7; ++z)
+                            *reinterpret_cast<uint4*>(drow + tc_pos_of_digit(z) * 8192) = make_uint4(0u, 0u, 0u, 0u);
+                        break;
+                    }
                     const unsigned long long M2 = tc_magic2(23 - 8 * sdig);
                     uint32_t bq[4];
 #pragma unroll
