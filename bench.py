@@ -48,9 +48,9 @@ TF32_PER_BF16 = 1.1 / 2.25
 # the ncu --set full summaries in profiles/ (captured at m = 1,048,576 rows); stages whose traffic
 # grows with m are scaled by m / 1,048,576.  None where no capture covers the stage.
 NCU_TRAFFIC = {
-    "ozaki_4194304x64_fp32": {"gram": None,                           # gram_tc_kernel changed since the capture
-                              "eig": None,                           # kernels changed since the capture
-                              "compute_u": (482.525952e6, True)},    # compute_u_tc_kernel
+    "ozaki_4194304x64_fp32": {"gram": (271.798528e6, True),          # gram_tc_kernel (+ combine 10 MB)
+                              "eig": (0.09856e6, False),             # onesided_jacobi_kernel<1>
+                              "compute_u": (482.920192e6, True)},    # compute_u_tc_kernel<1>
     "stress_16777216x32_fp64": {"gram": None,
                                 "eig": (0.119296e6, False),          # eig_dd_kernel
                                 "compute_u": (491.981568e6, True)},  # compute_u_kernel<double>
