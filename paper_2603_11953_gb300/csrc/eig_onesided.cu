@@ -462,6 +462,10 @@ __global__ void __launch_bounds__(64 * OS_MAXP, 1) onesided_jacobi_kernel(OsPara
     __shared__ int s_mx_total;
     __shared__ int s_fail[2];               // used in CTA 0: failed pairs of a convergence check
     __shared__ int s_fail_total;
+    __shared__ int s_napp[2];               // used in CTA 0: columns outside the first-order range
+    __shared__ int s_napp_total;
+    __shared__ double s_coef[2 * OS_MAXP][2 * OS_MAXP * 16];  // first-order angles E(local u, column v)
+    __shared__ int s_colofs[2 * OS_MAXP * 16];   // check: offset of each column of the cluster
     __shared__ int s_timeout;
     __shared__ float s_off[16];             // per warp: the largest scaled |g| left in the sweep
     __shared__ float s_off_cta;
@@ -486,6 +490,7 @@ __global__ void __launch_bounds__(64 * OS_MAXP, 1) onesided_jacobi_kernel(OsPara
         s_cnt[0] = s_cnt[1] = 0;
         s_mx[0] = s_mx[1] = 0;
         s_fail[0] = s_fail[1] = 0;
+        s_napp[0] = s_napp[1] = 0;
         s_timeout = 0;
     }
     // initial placement: local top u <- column cP+u, bottom u <- column np-1-cP-u
@@ -710,53 +715,121 @@ __global__ void __launch_bounds__(64 * OS_MAXP, 1) onesided_jacobi_kernel(OsPara
         const float mx = __int_as_float(s_mx_total);
         if (c == 0 && tid == 0) { s_cnt[sp ^ 1] = 0; s_mx[sp ^ 1] = 0; }
         if (total == 0) { converged = true; break; }
-        // Jacobi converges quadratically: after a sweep in which every pair's scaled |g| was
-        // below 2^-20, the next sweep would normally only confirm convergence.  Instead, every
-        // pair of the current columns is tested at once (the same scaled test, exact norms);
-        // the sweep runs only if some pair fails.
-        if (mx < 0x1p-20f && sweep < prm.max_sweeps) {
-            for (int u = warp; u < 2 * P; u += nwarps) {
-                double* b = bufs + (size_t)(u < P ? os_buf(c, C, P, D, K, ring, u, true)
-                                                  : os_buf(c, C, P, D, K, ring, u - P, false)) * LD;
-                double s2 = 0.0;
-                for (int r = lane; r < ROWS; r += 32) s2 = fma(b[r], b[r], s2);
-                s2 = warp_sum(s2);
-                if (lane == 0) b[ROWS] = s2;
+        // Jacobi converges quadratically: after a sweep whose largest scaled |g| was mx the pairs
+        // are left near mx^2, and after a sweep with few rotations (at most n) the next one
+        // usually has none.  Then, instead of a sweep that would only confirm convergence, every
+        // pair of the current columns is tested at once (the same scaled test, exact norms), and
+        // a sweep runs only if some pair fails.  When the pairs that fail are all deep in the
+        // quadratic range, one simultaneous first-order step replaces the sweep: with
+        // A = X^T X = D + F (F off-diagonal), X (I + E) for the antisymmetric
+        // E_vu = g_uv / (a_u - a_v) leaves off-diagonals of order |E| |F|, and (I + E)^T (I + E)
+        // = I - E^2 is orthogonal to FP64 precision when every column of E has
+        // sum_v E_vu^2 <= 2^-53 (each |E_vu| <= 2^-27 besides).  The check then runs again.
+        // A check is one pass over the pairs (a few microseconds), a sweep n - 1 dependent steps.
+        const bool near = mx < 0x1p-20f || (double)mx * (double)mx <= prm.tol || total <= n || mx <= 0x1p-14f;
+        if (near && sweep < prm.max_sweeps) {
+            const int slots = 2 * P, cols = slots * C;
+            // where each column of the cluster sits during the check (CTA v / slots, this offset)
+            for (int v = tid; v < cols; v += blockDim.x) {
+                const int w = v % slots, rk = v / slots;
+                s_colofs[v] = (w < P ? os_buf(rk, C, P, D, K, ring, w, true) : os_buf(rk, C, P, D, K, ring, w - P, false)) * LD;
             }
-            cluster.sync();
-            int fails = 0;
-            const int slots = 2 * P;
-            const int items = slots * slots * C;
-            for (int it = tid; it < items; it += blockDim.x) {
-                const int u = it % slots, w = (it / slots) % slots, rk = it / (slots * slots);
-                const double* bu = bufs + (size_t)(u < P ? os_buf(c, C, P, D, K, ring, u, true)
-                                                         : os_buf(c, C, P, D, K, ring, u - P, false)) * LD;
-                const double* bv = cluster.map_shared_rank(bufs, rk) +
-                                   (size_t)(w < P ? os_buf(rk, C, P, D, K, ring, w, true)
-                                                  : os_buf(rk, C, P, D, K, ring, w - P, false)) * LD;
-                const long long iu = __double_as_longlong(bu[ROWS + 1]), iv = __double_as_longlong(bv[ROWS + 1]);
-                if (!(iu < iv && iv < n)) continue;
-                const double au = bu[ROWS], av = bv[ROWS];
-                if (!(au > 0.0 && av > 0.0)) continue;
-                double g0 = 0.0, g1 = 0.0, g2 = 0.0, g3 = 0.0;
-                for (int r = 0; r < ROWS; r += 4) {
-                    g0 = fma(bu[r], bv[r], g0);
-                    g1 = fma(bu[r + 1], bv[r + 1], g1);
-                    g2 = fma(bu[r + 2], bv[r + 2], g2);
-                    g3 = fma(bu[r + 3], bv[r + 3], g3);
+            // with one row per lane the whole cluster's columns are copied into this CTA (many
+            // independent remote loads at once); otherwise they are read in place
+            double* s_all = bufs + (size_t)(2 * P + 2 * D) * LD;
+            auto col = [&](int v) -> const double* {
+                if constexpr (RPL == 1) return s_all + (size_t)v * LD;
+                else return cluster.map_shared_rank(bufs, v / slots) + s_colofs[v];
+            };
+            for (int pass = 0; pass < 3; ++pass) {
+                for (int u = warp; u < slots; u += nwarps) {
+                    double* b = bufs + (size_t)(u < P ? os_buf(c, C, P, D, K, ring, u, true)
+                                                      : os_buf(c, C, P, D, K, ring, u - P, false)) * LD;
+                    double s2 = 0.0;
+                    for (int r = lane; r < ROWS; r += 32) s2 = fma(b[r], b[r], s2);
+                    s2 = warp_sum(s2);
+                    if (lane == 0) b[ROWS] = s2;
                 }
-                const double g = (g0 + g1) + (g2 + g3);
-                if (g * g > tol2 * (au * av)) ++fails;
+                cluster.sync();
+                if constexpr (RPL == 1) {
+                    for (int idx = tid; idx < cols * LD; idx += blockDim.x) {
+                        const int v = idx / LD, r = idx - v * LD;
+                        s_all[idx] = cluster.map_shared_rank(bufs, v / slots)[s_colofs[v] + r];
+                    }
+                    __syncthreads();
+                }
+                int fails = 0, napp = 0;
+                const int items = slots * cols;
+                for (int it = tid; it < items; it += blockDim.x) {
+                    const int u = it % slots, v = it / slots;
+                    const double* bu = col(c * slots + u);
+                    const double* bv = col(v);
+                    const long long iu = __double_as_longlong(bu[ROWS + 1]), iv = __double_as_longlong(bv[ROWS + 1]);
+                    const double au = bu[ROWS], av = bv[ROWS];
+                    double e = 0.0;
+                    if (iu < n && iv < n && iu != iv && au > 0.0 && av > 0.0) {
+                        double g0 = 0.0, g1 = 0.0, g2 = 0.0, g3 = 0.0;
+#pragma unroll
+                        for (int r = 0; r < ROWS; r += 4) {
+                            g0 = fma(bu[r], bv[r], g0);
+                            g1 = fma(bu[r + 1], bv[r + 1], g1);
+                            g2 = fma(bu[r + 2], bv[r + 2], g2);
+                            g3 = fma(bu[r + 3], bv[r + 3], g3);
+                        }
+                        const double g = (g0 + g1) + (g2 + g3);  // the same value in both columns' CTAs
+                        if (iu < iv && g * g > tol2 * (au * av)) ++fails;
+                        const double dd = au - av;
+                        if (fabs(g) <= 0x1p-27 * fabs(dd)) e = g / dd;
+                        else if (g * g > tol2 * (au * av)) ++napp;  // a failing pair outside the range
+                    }
+                    s_coef[u][v] = e;
+                }
+                __syncthreads();
+                // columns whose first-order step would not be orthogonal to FP64 precision
+                for (int u = warp; u < slots; u += nwarps) {
+                    double s2 = 0.0;
+                    for (int v = lane; v < cols; v += 32) s2 = fma(s_coef[u][v], s_coef[u][v], s2);
+                    s2 = warp_sum(s2);
+                    if (lane == 0 && s2 > 0x1p-53) ++napp;
+                }
+                const int cp = checks & 1;
+                ++checks;
+                if (fails) atomicAdd(&cluster.map_shared_rank(s_fail, 0)[cp], fails);
+                if (napp) atomicAdd(&cluster.map_shared_rank(s_napp, 0)[cp], napp);
+                cluster.sync();
+                if (tid == 0) {
+                    s_fail_total = cluster.map_shared_rank(s_fail, 0)[cp];
+                    s_napp_total = cluster.map_shared_rank(s_napp, 0)[cp];
+                }
+                __syncthreads();
+                const int f = s_fail_total, na = s_napp_total;
+                if (c == 0 && tid == 0) { s_fail[cp ^ 1] = 0; s_napp[cp ^ 1] = 0; }
+                if (f == 0) { converged = true; break; }
+                if (na != 0 || pass == 2) break;  // not deep in the quadratic range: sweep on
+                // the first-order step x_u <- x_u + sum_v x_v E(u, v) (E = 0 leaves x_u as it is)
+                double acc[2 * RPL];
+#pragma unroll
+                for (int i = 0; i < 2 * RPL; ++i) acc[i] = 0.0;
+                const int u = warp;  // one warp per local column (nwarps = 2P)
+#pragma unroll 4
+                for (int v = 0; v < cols; ++v) {
+                    const double e = s_coef[u][v];
+                    const double* bv = col(v);
+#pragma unroll
+                    for (int i = 0; i < 2 * RPL; ++i) acc[i] = fma(bv[lane + 32 * i], e, acc[i]);
+                }
+                // in place, once no CTA reads this CTA's columns any more (with the copies, every
+                // CTA finished copying before the counts were summed)
+                if constexpr (RPL != 1) cluster.sync();
+                {
+                    double* b = bufs + (size_t)(u < P ? os_buf(c, C, P, D, K, ring, u, true)
+                                                      : os_buf(c, C, P, D, K, ring, u - P, false)) * LD;
+#pragma unroll
+                    for (int i = 0; i < 2 * RPL; ++i) b[lane + 32 * i] += acc[i];
+                }
+                __syncthreads();
             }
-            const int cp = checks & 1;
-            ++checks;
-            if (fails) atomicAdd(&cluster.map_shared_rank(s_fail, 0)[cp], fails);
-            cluster.sync();
-            if (tid == 0) s_fail_total = cluster.map_shared_rank(s_fail, 0)[cp];
-            __syncthreads();
-            const int f = s_fail_total;
-            if (c == 0 && tid == 0) s_fail[cp ^ 1] = 0;
-            if (f == 0) { converged = true; break; }
+            if (converged) break;
         }
     }
     // outputs: lambda_j = ||x_j||^2, v_j = P^T x_j / ||x_j||
@@ -915,7 +988,9 @@ cudaError_t launch_cluster_jacobi_t(OsParams prm, int C, cudaStream_t s) {
     prm.np = ((prm.n < 4 ? 4 : prm.n) + 4 * C - 1) / (4 * C) * (4 * C);
     prm.P = prm.np / (2 * C);
     if (prm.P > OS_MAXP) return cudaErrorNotSupported;
-    const size_t smem = sizeof(double) * (size_t)(2 * prm.P + 2 * (2 * prm.P + 2)) * (64 * RPL + 2);
+    // ring slots, plus (one row per lane) room for a copy of every column of the cluster
+    const size_t smem = sizeof(double) * ((size_t)(2 * prm.P + 2 * (2 * prm.P + 2)) + (RPL == 1 ? (size_t)prm.np : 0)) *
+                        (64 * RPL + 2);
     cudaError_t e =
         cudaFuncSetAttribute(onesided_jacobi_kernel<RPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
