@@ -53,6 +53,7 @@
 #include <cooperative_groups.h>
 
 #include "internal.cuh"
+#include "tma_util.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -104,88 +105,167 @@ __device__ __forceinline__ double chol_rsqrt(double d) {
     return __longlong_as_double(__double_as_longlong(y) - ((long long)k << 52));
 }
 
-__global__ void __launch_bounds__(256)
+// n <= 64: one CTA of 16 warps with a look-ahead.  Warp 0 (the panel) runs the dependent
+// chain of each step one step ahead of the others: 1 / r_kk, row k of R from the pivot
+// column, the remaining diagonal D -= R_k^2, the next pivot, and that pivot's column brought
+// up to date (the other warps' update of the previous step has been applied to S; this
+// step's term the panel subtracts itself), and only then publishes row k.  Warps 1-15 apply
+// each published step's update S(a, b) -= R_k[a] R_k[b] to the strictly lower triangle of the
+// remaining indices, one entry per thread (a flat index table spreads the triangle evenly).
+// The two sides meet on mbarriers (row k published; every bulk warp done with step k), waited
+// on with a suspend-time hint and a bound.  Every value is computed by the same operations as
+// in a plain right-looking factorization.
+constexpr int CHL_THREADS = 512, CHL_BULK_WARPS = CHL_THREADS / 32 - 1;
+
+// pivot: the largest remaining diagonal, lowest original index on ties (keys: 0 for a
+// negative value, else the bit pattern's high word + 1 and its low word; non-negative doubles
+// order like their patterns), or the lowest remaining index without pivoting.  Whole warp.
+__device__ __forceinline__ int chol_pick(const double* D, int n, unsigned long long rem, int pivot, int lane) {
+    if (!pivot) return __ffsll((long long)rem) - 1;
+    unsigned khi = 0u, klo = 0u;
+    int bo = n;
+    for (int o = lane; o < n; o += 32) {
+        if (!((rem >> o) & 1ull)) continue;
+        const long long dd = __double_as_longlong(D[o]);
+        const unsigned h = dd < 0 ? 0u : (unsigned)(dd >> 32) + 1u, l = dd < 0 ? 0u : (unsigned)dd;
+        if (bo == n || h > khi || (h == khi && l > klo)) { khi = h; klo = l; bo = o; }
+    }
+    const unsigned mh = __reduce_max_sync(0xffffffffu, khi);
+    const unsigned ml = __reduce_max_sync(0xffffffffu, khi == mh ? klo : 0u);
+    return (int)__reduce_min_sync(0xffffffffu, (khi == mh && klo == ml) ? (unsigned)bo : (unsigned)n);
+}
+
+__global__ void __launch_bounds__(CHL_THREADS, 1)
     chol_piv_kernel(const double* __restrict__ M, int n, int64_t ldm, double* __restrict__ X,
                     int* __restrict__ perm_out, DevInfo* info, int pivot) {
-    extern __shared__ double sa[];    // [n][n] Schur complement, lower triangle by original index
+    extern __shared__ double sa[];    // [n][n] Schur complement, strictly lower triangle by original index
     double* Rr = sa + (size_t)n * n;  // [n][n]: row k of R by original column index
-    __shared__ int s_list[64];        // remaining original indices, ascending
+    __shared__ double s_D[64];        // diagonal of the Schur complement (the panel's)
+    __shared__ double s_pcol[64];     // the current pivot's column, up to date
+    __shared__ unsigned short s_tab[2016];  // flat index ia (ia - 1) / 2 + jb -> ia | jb << 8
+    __shared__ int s_list[2][64];     // per step (mod 2): remaining indices without its pivot, ascending
+    __shared__ int s_rc[2];
     __shared__ int s_perm[64];
-    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
-    for (int idx = tid; idx < n * n; idx += nt) {
+    __shared__ uint64_t s_rowbar[2];  // per step (mod 2): row k of R published (one arrival)
+    __shared__ uint64_t s_bulkbar[2]; // per step (mod 2): every bulk warp applied step k
+    __shared__ int s_stop;            // the panel is done (or gave up); steps >= s_kend are not rows
+    __shared__ int s_kend;
+    __shared__ unsigned long long s_rem;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int idx = tid; idx < n * n; idx += CHL_THREADS) {
         const int r = idx % n, c = idx / n;
         sa[idx] = r >= c ? M[r + (size_t)c * ldm] : 0.0;
         Rr[idx] = 0.0;
     }
-    __syncthreads();
-    unsigned long long rem = n == 64 ? ~0ull : ((1ull << n) - 1ull);
-    bool deficient = false;
-    int kend = n;
-    for (int k = 0; k < n; ++k) {
-        // pivot: the largest remaining diagonal, lowest original index on ties.  Every warp
-        // finds it itself.  Non-negative doubles order like their bit patterns; every
-        // negative value (rank deficiency) sorts below them.
-        // keys: 0 for a negative value, else the bit pattern's high word + 1 and its low word (non-
-        // negative doubles order like their patterns); three warp reductions: high word, low word
-        // among the lanes at the maximum, lowest index among those
-        unsigned khi = 0u, klo = 0u;
-        int bo = n;
-        for (int o = lane; o < n; o += 32) {
-            if (!((rem >> o) & 1ull)) continue;
-            const long long dd = __double_as_longlong(sa[o + (size_t)o * n]);
-            const unsigned h = dd < 0 ? 0u : (unsigned)(dd >> 32) + 1u, l = dd < 0 ? 0u : (unsigned)dd;
-            if (bo == n || h > khi || (h == khi && l > klo)) { khi = h; klo = l; bo = o; }
-        }
-        const unsigned mh = __reduce_max_sync(0xffffffffu, khi);
-        const unsigned ml = __reduce_max_sync(0xffffffffu, khi == mh ? klo : 0u);
-        bo = (int)__reduce_min_sync(0xffffffffu, (khi == mh && klo == ml) ? (unsigned)bo : (unsigned)n);
-        const int ok = pivot ? bo : __ffsll((long long)rem) - 1;
-        const double d = sa[ok + (size_t)ok * n];
-        // d > 0 (finite) decided on the bit pattern: the SM's FP64 pipe takes about one
-        // instruction per 19 cycles from all its warps, so no warp repeats FP64 work here
-        const long long db = __double_as_longlong(d);
-        if (!(db > 0 && db < 0x7ff0000000000000ll)) { deficient = true; kend = k; break; }
-        const unsigned long long rn = rem & ~(1ull << ok);
-        if (warp == 0) {
-            // one warp: 1 / r_kk, row k of R over the remaining indices, and their ascending list
-            const double rinv = chol_rsqrt(d);
-            for (int o = lane; o < n; o += 32) {
-                if (o == ok) Rr[(size_t)k * n + o] = d * rinv;
-                else if ((rn >> o) & 1ull) Rr[(size_t)k * n + o] = chol_S(sa, n, o, ok) * rinv;
-                if ((rn >> o) & 1ull) s_list[__popcll(rn & ((1ull << o) - 1ull))] = o;
-            }
-            if (lane == 0) s_perm[k] = ok;
-        }
-        __syncthreads();
-        // trailing update S(a, b) -= R[k][a] R[k][b] over the remaining lower triangle: the
-        // warps take its columns b (round robin), the lanes its rows a >= b, contiguous
-        const int rc = __popcll(rn);
-        const double* rk = Rr + (size_t)k * n;
-        for (int jb = tid >> 5; jb < rc; jb += nt >> 5) {
-            const int b = s_list[jb];
-            const double rb = rk[b];
-            for (int ia = jb + lane; ia < rc; ia += 32) {
-                const int a = s_list[ia];
-                sa[a + (size_t)b * n] -= rk[a] * rb;
-            }
-        }
-        rem = rn;
-        __syncthreads();
+    for (int t = tid; t < 2016; t += CHL_THREADS) {
+        int ia = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)t)) * 0.5f);
+        while (ia * (ia - 1) / 2 > t) --ia;
+        while ((ia + 1) * ia / 2 <= t) ++ia;
+        s_tab[t] = (unsigned short)(ia | ((t - ia * (ia - 1) / 2) << 8));
     }
+    if (tid < n) s_D[tid] = M[tid + (size_t)tid * ldm];
+    if (tid == 0) {
+        for (int i = 0; i < 2; ++i) { mbar_init(&s_rowbar[i], 1); mbar_init(&s_bulkbar[i], CHL_BULK_WARPS); }
+        mbar_fence_init();
+        s_stop = 0;
+        s_kend = n;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        // ---------------- panel
+        unsigned long long rem = n == 64 ? ~0ull : ((1ull << n) - 1ull);
+        int ok = chol_pick(s_D, n, rem, pivot, lane);
+        for (int o = lane; o < n; o += 32) s_pcol[o] = chol_S(sa, n, o, ok);
+        __syncwarp();
+        bool deficient = false, timeout = false;
+        int k = 0;
+        while (k < n) {
+            // d > 0 (finite) decided on the bit pattern
+            const double d = s_D[ok];
+            const long long db = __double_as_longlong(d);
+            if (!(db > 0 && db < 0x7ff0000000000000ll)) { deficient = true; break; }
+            const unsigned long long rn = rem & ~(1ull << ok);
+            const double rinv = chol_rsqrt(d);
+            double* rk = Rr + (size_t)k * n;
+            for (int o = lane; o < n; o += 32) {
+                if (o == ok) rk[o] = d * rinv;
+                else if ((rn >> o) & 1ull) {
+                    const double r = s_pcol[o] * rinv;
+                    rk[o] = r;
+                    s_D[o] = fma(-r, r, s_D[o]);
+                    s_list[k & 1][__popcll(rn & ((1ull << o) - 1ull))] = o;
+                }
+            }
+            if (lane == 0) { s_perm[k] = ok; s_rc[k & 1] = __popcll(rn); }
+            rem = rn;
+            __syncwarp();
+            int nok = -1;
+            if (rem != 0ull) {
+                nok = chol_pick(s_D, n, rem, pivot, lane);
+                // the next pivot's column: in S once the bulk warps finished step k - 1, minus
+                // this step's term (S itself gets it from them after row k is published)
+                if (k >= 1 && !mbar_wait_susp(&s_bulkbar[(k - 1) & 1], ((k - 1) >> 1) & 1)) timeout = true;
+                const double rkn = rk[nok];
+                for (int o = lane; o < n; o += 32)
+                    if (((rem >> o) & 1ull) && o != nok) s_pcol[o] = fma(-rk[o], rkn, chol_S(sa, n, o, nok));
+            }
+            // publish row k, its list and count
+            __threadfence_block();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&s_rowbar[k & 1]);
+            ++k;
+            if (timeout || rem == 0ull) break;
+            ok = nok;
+        }
+        if (lane == 0) {
+            s_kend = k;
+            s_rem = rem;
+            if (deficient) atomicOr(&info->flags, FLAG_NOT_FULL_RANK);
+            if (timeout) atomicOr(&info->flags, FLAG_TIMEOUT);
+            *reinterpret_cast<volatile int*>(&s_stop) = 1;
+            __threadfence_block();
+            mbar_arrive(&s_rowbar[k & 1]);  // wakes the bulk warps waiting for step k: none follows
+        }
+    } else {
+        // ---------------- bulk: the update of every published step
+        const int btid = tid - 32;
+        for (int k = 0;; ++k) {
+            if (!mbar_wait_susp(&s_rowbar[k & 1], (k >> 1) & 1)) {
+                if (lane == 0) atomicOr(&info->flags, FLAG_TIMEOUT);
+                break;
+            }
+            if (*reinterpret_cast<volatile int*>(&s_stop) && k >= *reinterpret_cast<volatile int*>(&s_kend)) break;
+            const int rc = s_rc[k & 1];
+            const int* list = s_list[k & 1];
+            const double* rk = Rr + (size_t)k * n;
+            const int T = rc * (rc - 1) / 2;
+            for (int t = btid; t < T; t += CHL_THREADS - 32) {
+                const unsigned e = s_tab[t];
+                const int a = list[e & 0xffu], b = list[e >> 8];
+                double* sp = sa + a + (size_t)b * n;
+                *sp = fma(-rk[a], rk[b], *sp);
+            }
+            __threadfence_block();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&s_bulkbar[k & 1]);
+        }
+    }
+    __syncthreads();
     // X = R^T with rows in pivot order: X[pos][c] = R[c][perm[pos]] for pos >= c.  Past a
     // rank deficiency the remaining positions take the remaining indices in ascending order.
+    const int kend = s_kend;
     if (tid == 0) {
+        const unsigned long long rem = s_rem;
         int pos = kend;
         for (int o = 0; o < n; ++o)
             if ((rem >> o) & 1ull) s_perm[pos++] = o;
     }
     __syncthreads();
-    for (int idx = tid; idx < n * n; idx += nt) {
+    for (int idx = tid; idx < n * n; idx += CHL_THREADS) {
         const int pos = idx % n, c = idx / n;
         X[idx] = (pos >= c && c < kend) ? Rr[(size_t)c * n + s_perm[pos]] : 0.0;
     }
-    for (int i = tid; i < n; i += nt) perm_out[i] = s_perm[i];
-    if (tid == 0 && deficient) atomicOr(&info->flags, FLAG_NOT_FULL_RANK);
+    for (int i = tid; i < n; i += CHL_THREADS) perm_out[i] = s_perm[i];
 }
 
 // 64 < n <= 256: the same factorization with the Schur complement S (lower triangle by original
@@ -1042,7 +1122,8 @@ cudaError_t launch_cholesky(const double* M, int n, int64_t ldm, double* X, int*
     cudaError_t e = cudaFuncSetAttribute(chol_piv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)(2 * sizeof(double) * 64 * 64));
     if (e != cudaSuccess) return e;
-    chol_piv_kernel<<<1, 256, 2 * sizeof(double) * (size_t)n * n, s>>>(M, n, ldm, X, perm, info, pivot ? 1 : 0);
+    chol_piv_kernel<<<1, CHL_THREADS, 2 * sizeof(double) * (size_t)n * n, s>>>(M, n, ldm, X, perm, info,
+                                                                       pivot ? 1 : 0);
     return cudaGetLastError();
 }
 
