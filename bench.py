@@ -49,7 +49,7 @@ TF32_PER_BF16 = 1.1 / 2.25
 # grows with m are scaled by m / 1,048,576.  None where no capture covers the stage.
 NCU_TRAFFIC = {
     "ozaki_4194304x64_fp32": {"gram": (271.798528e6, True),          # gram_tc_kernel (+ combine 10 MB)
-                              "eig": (0.09856e6, False),             # onesided_jacobi_kernel<1>
+                              "eig": (0.10368e6, False),             # onesided_jacobi_kernel<1>
                               "compute_u": (482.920192e6, True)},    # compute_u_tc_kernel<1>
     "stress_16777216x32_fp64": {"gram": None,
                                 "eig": (0.119296e6, False),          # eig_dd_kernel
