@@ -125,7 +125,8 @@ typedef struct {
 /* Per-call numeric report (written asynchronously by the device). */
 typedef struct {
     int status;       /* tsvd_status of the numeric part */
-    int sweeps;       /* Jacobi sweeps performed */
+    int sweeps;       /* Jacobi sweeps performed (eig_variant 2 may end with one first-order step
+                         in place of a last sweep, when the remaining pairs allow it; not counted) */
     double off_norm;  /* max_{p<q} |m_pq| / sqrt(m_pp m_qq) at exit */
     double kappa_B;   /* estimate of kappa(B) = (lambda_max / lambda_min)^(1/2) of the
                          column-scaled Gram C = D^-1 M_h D^-1 (A = B D, Sec. 3; the
